@@ -1,0 +1,165 @@
+/*
+ * sfft.h -- C ABI of libsfft, a GB300 (sm_103a) implementation of the aliasing-filter
+ * sparse FFT with peeling decoding (FFAST for exactly sparse spectra, R-FFAST for noisy
+ * ones), after Li, Jiang, Chen, "On Performance of Sparse Fast Fourier Transform
+ * Algorithms Using the Aliasing Filter", arXiv 2011.05749, Sec. 2-4.
+ *
+ * Problem (Sec. 2.1): a length-N signal x whose spectrum xhat (Eq. 2, normalised by 1/N)
+ * has K significant coefficients.  The library returns their positions and values.
+ *
+ * Method (Sec. 2.2, Sec. 3.2, Sec. 4.2):
+ *   1. bucketization: for every stage d (subsampling factor L_d = f[d], B_d = N / L_d
+ *      buckets, Eq. 5) and every delay tau_{d,r} (Eq. 3-4), the B_d-point DFT of the
+ *      delayed subsample (Eq. 6, Eq. 19):
+ *        Y_{d,r}[j] = sum_{m<B_d} x[(m L_d + tau_{d,r}) mod N] e^{-2 pi i j m / B_d}
+ *                   = B_d * sum_{k = j mod B_d} xhat_k e^{+2 pi i k tau_{d,r} / N};
+ *   2. classification of every bin as zero-ton, single-ton or multi-ton (Sec. 3.2,
+ *      subproblem 1) with a location (subproblem 2) and a least-squares value;
+ *   3. peeling in parallel rounds: every single-ton found in a round is subtracted from
+ *      the bins it aliases into in every stage, and the changed bins are examined again
+ *      (Sec. 3.2, subproblem 3, genie-assisted peeling, Eq. 20).
+ *
+ * Conventions:
+ *   - delays are advances: the sample is x[(m L + tau) mod N], 0 <= tau < N (the paper
+ *     writes delays, x'_i = x_{i - tau}; the paper's tau is minus this one).
+ *   - output values are the paper-normalised xhat_f (Eq. 2), sorted by frequency f.
+ *   - complex data are interleaved (re, im): SFFT_C64 = 2 x float, SFFT_C128 = 2 x double.
+ *
+ * Memory: every pointer argument may point to device memory or to host memory (pinned or
+ * pageable), unless a call says otherwise; host buffers are copied through a staging area
+ * the plan owns, and the call then waits for the stream before it returns.  With device
+ * buffers every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and returns as soon as the work is enqueued.
+ *
+ * Errors: calls return SFFT_OK (0) or a negative SFFT_E* code.  Per-signal outcomes are
+ * written by the GPU into the caller's info array (see sfft_execute).
+ */
+#ifndef SFFT_H
+#define SFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sfft_plan_s* sfft_plan_t;
+typedef struct sfft_server_s* sfft_server_t;
+
+/* return and status codes */
+#define SFFT_OK 0
+#define SFFT_PENDING 1       /* sfft_poll: request not finished */
+#define SFFT_INCOMPLETE 2    /* per-signal status: peeling ended with unresolved bins */
+#define SFFT_EINVAL (-1)     /* invalid argument (see each call) */
+#define SFFT_ENOMEM (-2)     /* device or host allocation failed */
+#define SFFT_ECUDA (-3)      /* a CUDA call failed; sfft_last_cuda_error() names it */
+#define SFFT_ETIMEDOUT (-4)  /* a bounded device-side wait ran out */
+#define SFFT_EADMIT (-5)     /* server: request can never fit the memory budget */
+#define SFFT_ENOTFOUND (-6)  /* server: unknown ticket */
+#define SFFT_EBUSY (-7)      /* server: queue full */
+
+/* element type of x and of the returned values */
+#define SFFT_C64 0
+#define SFFT_C128 1
+
+/* arithmetic of the bulk path */
+#define SFFT_PREC_FP64 0     /* plain path: everything in FP64 */
+#define SFFT_PREC_FP32 1     /* FP32 gather/DFT/peeling, FP64 location and fit */
+
+/* singleton location rule (Sec. 3.2, subproblem 2) */
+#define SFFT_LOCATE_ARG 0    /* phase of Y(tau=1) conj(Y(tau=0)), snapped to the bin's
+                                candidates; needs delays 0 and 1 in every stage (FFAST) */
+#define SFFT_LOCATE_ML 1     /* best delay-phasor correlation over the L_d candidates
+                                {j, j + B_d, ...} of the bin (random delays, R-FFAST) */
+
+typedef struct {
+    int32_t dtype;       /* SFFT_C64 or SFFT_C128 (default C64) */
+    int32_t precision;   /* SFFT_PREC_FP32 or SFFT_PREC_FP64 (default FP32) */
+    int32_t locate;      /* SFFT_LOCATE_ARG or SFFT_LOCATE_ML (default ML) */
+    int32_t max_rounds;  /* peeling rounds at most (default 64) */
+    int32_t max_batch;   /* signals per execute call at most; sizes the workspace (default 1) */
+    int32_t reserved;
+    double noise_var;    /* sigma^2 of the noise per time sample, 0 = exactly sparse */
+    double a_min;        /* smallest significant |xhat| (default 1) */
+    double eta;          /* relative numerical floor of the thresholds; 0 = default
+                            (3e-3 for FP32, 1e-6 for FP64) */
+    double c0, c1;       /* zero-ton / single-ton threshold multipliers (default 4, 2):
+                            T0_d = R (c0 B_d sigma^2 + (eta B_d a_min)^2),
+                            T1_d = R (c1 B_d sigma^2 + (eta B_d a_min)^2) */
+} sfft_opts;
+
+/* Fill *opts with the defaults above. */
+void sfft_opts_default(sfft_opts* opts);
+
+/* Create a plan for signals of length N (Sec. 3.2: N = product of co-prime factors).
+ *   f[n_stages]          subsampling factor L_d of each stage; each divides N, the f are
+ *                        pairwise co-prime, B_d = N / L_d (1 <= n_stages <= 4)
+ *   delays[n_stages * n_delays]  tau_{d,r} at [d * n_delays + r], distinct within a stage,
+ *                        0 <= tau < N (1 <= n_delays <= 16)
+ *   K                    output size: the K largest recovered coefficients (Sec. 2.1)
+ * Host arrays; the plan copies them.  N < 2^30.  The plan owns device tables (twiddles,
+ * index maps) and the workspace for opts->max_batch signals until sfft_plan_destroy.
+ * Errors: SFFT_EINVAL (bad sizes, factors, delays, ARG without delays 0 and 1),
+ * SFFT_ENOMEM, SFFT_ECUDA.                                                                */
+int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t n_stages, const int64_t* f,
+                     int32_t n_delays, const int64_t* delays, const sfft_opts* opts);
+void sfft_plan_destroy(sfft_plan_t plan);
+
+/* Bins per signal: sum_d B_d (so the bucketization output has n_delays times as many). */
+int64_t sfft_plan_num_bins(sfft_plan_t plan);
+
+/* Recover one signal.
+ *   x          N complex samples of the plan's dtype
+ *   out_idx    int64[K]: recovered frequencies, ascending
+ *   out_val    K complex values (plan dtype): xhat at out_idx
+ *   out_info   int32[4]: {count, status (SFFT_OK or SFFT_INCOMPLETE, or SFFT_ETIMEDOUT),
+ *              rounds, identifications (bins classified, over all rounds)}
+ * Entries of out_idx/out_val past count are left untouched.  Calls that share a plan use
+ * its single workspace: they must be ordered (one stream, or synchronised).              */
+int sfft_execute(sfft_plan_t plan, const void* x, int64_t* out_idx, void* out_val,
+                 int32_t* out_info, void* stream);
+
+/* Recover n signals in one set of launches.  plans[i] (may repeat), xs[i], idx[i], val[i]
+ * as in sfft_execute for signal i; infos: int32[4 * n], signal i at infos + 4 i.  The
+ * host arrays of pointers are read during the call.  Signals that share a plan are
+ * processed together, at most that plan's max_batch per launch group.  Device pointers
+ * only.                                                                                   */
+int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const void* const* xs,
+                       int64_t* const* idx, void* const* val, int32_t* infos, void* stream);
+
+/* Bucketization only (Eq. 6 / Eq. 19): writes the bins of one signal in natural order,
+ * bins[off_d + r * B_d + j] with off_d = n_delays * sum_{d'<d} B_d', as complex of the
+ * plan's arithmetic (FP32 -> C64, FP64 -> C128).  Device pointers only.                  */
+int sfft_bucketize(sfft_plan_t plan, const void* x, void* bins, void* stream);
+
+/* Peeling decoder only, on caller-supplied bins in the layout of sfft_bucketize (read,
+ * not modified).  Outputs as sfft_execute.  Device pointers only.                         */
+int sfft_decode_bins(sfft_plan_t plan, const void* bins, int64_t* out_idx, void* out_val,
+                     int32_t* out_info, void* stream);
+
+/* Serving: continuous batching of requests of any plans on one GPU.  A host thread
+ * admits requests while their workspace fits hbm_budget bytes and fewer than max_slots
+ * are in flight, launches each admitted group on its own stream (so groups overlap on
+ * the device), and retires them as their events complete.                                */
+int sfft_server_create(sfft_server_t* out, size_t hbm_budget, int32_t max_slots);
+/* Queue one request (device pointers, as sfft_execute).  The buffers must stay valid until
+ * sfft_poll reports a final status.  *ticket identifies it.                               */
+int sfft_submit(sfft_server_t srv, sfft_plan_t plan, const void* x, int64_t* out_idx,
+                void* out_val, int32_t* out_info, uint64_t* ticket);
+/* *status = SFFT_PENDING while queued or running, else SFFT_OK once the outputs are
+ * written (per-signal status in out_info).  Also reports the request's latency in
+ * microseconds from submit to completion (latency_us may be NULL).                       */
+int sfft_poll(sfft_server_t srv, uint64_t ticket, int32_t* status, double* latency_us);
+/* Wait until every queued request has finished. */
+int sfft_server_drain(sfft_server_t srv);
+void sfft_server_destroy(sfft_server_t srv);
+
+/* Text of a return code; name of the last CUDA error seen by the library. */
+const char* sfft_error_string(int code);
+const char* sfft_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFFT_H */

@@ -1,0 +1,743 @@
+// api.cu -- libsfft host library: plans (validation, prime-factor index maps, twiddles,
+// thresholds, workspace), execution entry points and error reporting.  The C ABI is
+// declared in include/sfft.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "launch.h"
+#include "sfft.h"
+#include "sfft_internal.cuh"
+#include "sfft_plan.h"
+
+using namespace sfft;
+
+namespace sfft {
+cudaError_t set_bucketize_smem_limit(int max_smem);
+cudaError_t set_compact_smem_limit(int max_smem);
+
+static thread_local char g_last_cuda[256] = "no error";
+
+int cuda_fail(cudaError_t e)
+{
+    snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return SFFT_ECUDA;
+}
+
+#define CK(call)                               \
+    do {                                       \
+        cudaError_t e_ = (call);               \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+static int64_t gcd64(int64_t a, int64_t b)
+{
+    while (b) {
+        int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+static int64_t modinv(int64_t a, int64_t m)
+{
+    // extended Euclid; a and m co-prime
+    int64_t g = m, x = 0, x1 = 1, aa = a % m;
+    if (m == 1) return 0;
+    int64_t b = aa;
+    while (b) {
+        int64_t q = g / b, t = g - q * b;
+        g = b;
+        b = t;
+        t = x - q * x1;
+        x = x1;
+        x1 = t;
+    }
+    (void)g;
+    x %= m;
+    return x < 0 ? x + m : x;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct DevInfo {
+    int sms = 0, max_smem = 0;
+    bool ok = false;
+};
+
+static int device_info(DevInfo* out)
+{
+    static std::mutex mu;
+    static DevInfo cache[64];
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) return SFFT_EINVAL;
+    if (!cache[dev].ok) {
+        DevInfo di;
+        CK(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaDeviceGetAttribute(&di.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        CK(set_bucketize_smem_limit(di.max_smem));
+        CK(set_compact_smem_limit(di.max_smem));
+        di.ok = true;
+        cache[dev] = di;
+    }
+    *out = cache[dev];
+    return SFFT_OK;
+}
+
+// factor B into (prime, power) pairs
+static std::vector<std::pair<int64_t, int>> factorize(int64_t B)
+{
+    std::vector<std::pair<int64_t, int>> out;
+    for (int64_t p = 2; p * p <= B; ++p) {
+        int e = 0;
+        while (B % p == 0) {
+            B /= p;
+            ++e;
+        }
+        if (e) out.push_back({p, e});
+    }
+    if (B > 1) out.push_back({B, 1});
+    return out;
+}
+
+static int64_t prod_of(const std::vector<int>& Ps)
+{
+    int64_t v = 1;
+    for (int P : Ps) v *= P;
+    return v;
+}
+
+// Order the prime-power axes of one stage and pick the pass split.  Returns false if no
+// split keeps both groups within max_elems.
+static bool choose_axes(int64_t B, int64_t max_elems, std::vector<int>* axes, int* split)
+{
+    std::vector<int> odd, pw2;
+    for (auto& pe : factorize(B)) {
+        int64_t q = 1;
+        for (int i = 0; i < pe.second; ++i) q *= pe.first;
+        if (pe.first == 2)
+            pw2.push_back((int)q);
+        else
+            odd.push_back((int)q);
+    }
+    std::sort(odd.begin(), odd.end());
+    std::vector<int> all = odd;
+    for (int q : pw2) all.push_back(q);
+    if (all.empty()) all.push_back(1);
+    if (B <= max_elems) {
+        *axes = all;
+        *split = (int)all.size();
+        return true;
+    }
+    const int n = (int)all.size();
+    int64_t best = -1;
+    unsigned best_mask = 0;
+    for (unsigned mask = 1; mask + 1 < (1u << n); ++mask) {
+        int64_t pi = 1;
+        for (int i = 0; i < n; ++i)
+            if (mask >> i & 1) pi *= all[i];
+        const int64_t po = B / pi;
+        if (pi > max_elems || po > max_elems) continue;
+        const int64_t worst = std::max(pi, po);
+        if (best < 0 || worst < best) {
+            best = worst;
+            best_mask = mask;
+        }
+    }
+    if (best < 0) return false;
+    std::vector<int> in, outg;
+    for (int i = 0; i < n; ++i) (best_mask >> i & 1 ? in : outg).push_back(all[i]);
+    axes->clear();
+    for (int q : in) axes->push_back(q);
+    for (int q : outg) axes->push_back(q);
+    *split = (int)in.size();
+    return true;
+}
+
+static int ilog2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+}  // namespace sfft
+
+// ---------------------------------------------------------------------------------------
+
+extern "C" void sfft_opts_default(sfft_opts* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->dtype = SFFT_C64;
+    o->precision = SFFT_PREC_FP32;
+    o->locate = SFFT_LOCATE_ML;
+    o->max_rounds = 64;
+    o->max_batch = 1;
+    o->noise_var = 0.0;
+    o->a_min = 1.0;
+    o->eta = 0.0;
+    o->c0 = 4.0;
+    o->c1 = 2.0;
+}
+
+static void free_plan_memory(sfft_plan_s* p)
+{
+    void* dev[] = {p->d_nidx, p->d_pbin, p->d_bpos, p->d_tw, p->d_bins, p->d_scratch,
+                   p->d_dec, p->d_ptrs, p->d_sortbuf, p->d_x_stage, p->d_out_stage,
+                   p->d_bins_in};
+    for (void* q : dev)
+        if (q) cudaFree(q);
+    for (int i = 0; i < 2; ++i) {
+        if (p->h_ptrs[i]) cudaFreeHost(p->h_ptrs[i]);
+        if (p->ptr_ev[i]) cudaEventDestroy(p->ptr_ev[i]);
+    }
+}
+
+extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t n_stages,
+                                const int64_t* f, int32_t n_delays, const int64_t* delays,
+                                const sfft_opts* opts_in)
+{
+    if (!out || !f || !delays) return SFFT_EINVAL;
+    *out = nullptr;
+    sfft_opts o;
+    sfft_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    if (N < 1 || N >= (1ll << 30) || K < 1 || n_stages < 1 || n_stages > kMaxStages ||
+        n_delays < 1 || n_delays > kMaxDelays)
+        return SFFT_EINVAL;
+    if ((o.dtype != SFFT_C64 && o.dtype != SFFT_C128) ||
+        (o.precision != SFFT_PREC_FP32 && o.precision != SFFT_PREC_FP64) ||
+        (o.locate != SFFT_LOCATE_ARG && o.locate != SFFT_LOCATE_ML) || o.max_rounds < 1 ||
+        o.max_rounds > 4096 || o.max_batch < 1 || o.noise_var < 0 || o.a_min < 0 ||
+        o.eta < 0 || o.c0 < 0 || o.c1 < 0)
+        return SFFT_EINVAL;
+    for (int d = 0; d < n_stages; ++d) {
+        if (f[d] < 1 || N % f[d] != 0) return SFFT_EINVAL;
+        for (int e = 0; e < d; ++e)
+            if (gcd64(f[d], f[e]) != 1) return SFFT_EINVAL;
+        for (int r = 0; r < n_delays; ++r) {
+            const int64_t t = delays[(int64_t)d * n_delays + r];
+            if (t < 0 || t >= N) return SFFT_EINVAL;
+            for (int q = 0; q < r; ++q)
+                if (delays[(int64_t)d * n_delays + q] == t) return SFFT_EINVAL;
+        }
+    }
+    DevInfo di;
+    int rc = device_info(&di);
+    if (rc) return rc;
+
+    sfft_plan_s* p = new (std::nothrow) sfft_plan_s();
+    if (!p) return SFFT_ENOMEM;
+    p->opts = o;
+    p->prec = o.precision == SFFT_PREC_FP32 ? 1 : 0;
+    p->xdouble = o.dtype == SFFT_C128 ? 1 : 0;
+    p->esz = p->prec ? 8 : 16;
+    p->xesz = p->xdouble ? 16 : 8;
+    p->max_batch = o.max_batch;
+    p->num_sms = di.sms;
+    const double eta = o.eta > 0 ? o.eta : (p->prec ? 3e-3 : 1e-6);
+
+    PlanDesc& pd = p->pd;
+    memset(&pd, 0, sizeof(pd));
+    pd.N = (int32_t)N;
+    pd.D = n_stages;
+    pd.R = n_delays;
+    pd.locate = o.locate;
+    pd.max_rounds = o.max_rounds;
+    pd.K = K;
+
+    // shared memory budget of one tile (leave room for twiddles)
+    const int64_t max_elems = (int64_t)(di.max_smem - 12 * 1024) / (int64_t)p->esz;
+    std::vector<int32_t> h_nidx, h_pbin, h_bpos, tw_P, tw_t;
+    int64_t bin_base = 0;
+    size_t smem1 = 0, smem2 = 0;
+    int64_t max_tile1 = 0, max_tile2 = 0;
+    p->need_pass2 = false;
+    const int64_t tile_target = p->prec ? 4096 : 2048;
+    for (int d = 0; d < n_stages; ++d) {
+        StageDesc& s = pd.st[d];
+        const int64_t L = f[d], B = N / L;
+        s.B = (int32_t)B;
+        s.L = (int32_t)L;
+        std::vector<int> Ps;
+        int split = 0;
+        if (!choose_axes(B, max_elems, &Ps, &split) || (int)Ps.size() > kMaxAxes) {
+            free_plan_memory(p);
+            delete p;
+            return SFFT_EINVAL;
+        }
+        for (int P : Ps)
+            if (!(P > 0 && (P & (P - 1)) == 0) && P > 2049) {  // direct odd DFT: <= 1024 pairs
+                free_plan_memory(p);
+                delete p;
+                return SFFT_EINVAL;
+            }
+        s.n_axes = (int32_t)Ps.size();
+        s.split = split;
+        int32_t S = 1;
+        for (int a = 0; a < s.n_axes; ++a) {
+            AxisDesc& A = s.ax[a];
+            A.P = Ps[a];
+            A.pow2 = (A.P > 1 && (A.P & (A.P - 1)) == 0) ? 1 : 0;
+            A.log2P = A.pow2 ? ilog2(A.P) : 0;
+            A.S = S;
+            S *= A.P;
+            const int64_t Bp = B / A.P;
+            A.rur = (int32_t)(Bp % B);
+            A.crt = (int32_t)((Bp * modinv(Bp % A.P, A.P)) % B);
+            A.tw_off = (int32_t)tw_P.size();
+            const int nt = A.pow2 ? A.P / 2 : A.P;
+            for (int t = 0; t < nt; ++t) {
+                tw_P.push_back(A.P);
+                tw_t.push_back(t);
+            }
+        }
+        for (int r = 0; r < n_delays; ++r) s.tau[r] = (int32_t)delays[(int64_t)d * n_delays + r];
+        s.r0 = s.r1 = -1;
+        for (int r = 0; r < n_delays; ++r) {
+            if (s.tau[r] == 0 && s.r0 < 0) s.r0 = r;
+            if (s.tau[r] == 1 && s.r1 < 0) s.r1 = r;
+        }
+        if (o.locate == SFFT_LOCATE_ARG && (s.r0 < 0 || s.r1 < 0)) {
+            free_plan_memory(p);
+            delete p;
+            return SFFT_EINVAL;
+        }
+        s.bin_base = (int32_t)bin_base;
+        s.y_off = (int32_t)(bin_base * n_delays);
+        // thresholds: T0 = R (c0 B sigma^2 + (eta B a_min)^2), T1 with c1
+        const double sig_y = (double)B * o.noise_var;
+        const double fl = eta * (double)B * o.a_min;
+        s.T0 = (double)n_delays * (o.c0 * sig_y + fl * fl);
+        s.T1 = (double)n_delays * (o.c1 * sig_y + fl * fl);
+
+        // index maps
+        const size_t base = h_nidx.size();
+        h_nidx.resize(base + B);
+        h_pbin.resize(base + B);
+        h_bpos.resize(base + B);
+        for (int64_t pos = 0; pos < B; ++pos) {
+            int64_t n = 0, j = 0;
+            for (int a = 0; a < s.n_axes; ++a) {
+                const AxisDesc& A = s.ax[a];
+                const int32_t c = (int32_t)((pos / A.S) % A.P);
+                const int32_t na = A.pow2 ? bitrev(c, A.log2P) : c;
+                n += (int64_t)na * A.rur;
+                j += (int64_t)c * A.crt;
+            }
+            h_nidx[base + pos] = (int32_t)(n % B);
+            h_pbin[base + pos] = (int32_t)(j % B);
+        }
+        for (int64_t pos = 0; pos < B; ++pos) h_bpos[base + h_pbin[base + pos]] = (int32_t)pos;
+        for (int64_t jj = 0; jj < B; ++jj) {
+            int64_t pp = 0;
+            for (int a = 0; a < s.n_axes; ++a) pp += (jj % s.ax[a].P) * s.ax[a].S;
+            if (pp != h_bpos[base + jj]) {  // CRT maps must be inverse permutations
+                free_plan_memory(p);
+                delete p;
+                return SFFT_EINVAL;
+            }
+        }
+
+        // passes
+        auto tw_elems = [&](int a0, int a1) {
+            int64_t t = 0;
+            for (int a = a0; a < a1; ++a) t += s.ax[a].pow2 ? s.ax[a].P / 2 : s.ax[a].P;
+            return t;
+        };
+        PassDesc& p1 = p->pass1[d];
+        PassDesc& p2 = p->pass2[d];
+        memset(&p1, 0, sizeof(p1));
+        memset(&p2, 0, sizeof(p2));
+        if (split == s.n_axes) {
+            p1 = PassDesc{0, s.n_axes, 1, 1, 1, (int32_t)B, 1, 1};
+            smem1 = std::max(smem1, (size_t)(B + tw_elems(0, s.n_axes)) * p->esz);
+            max_tile1 = std::max<int64_t>(max_tile1, B);
+        } else {
+            p->need_pass2 = true;
+            int64_t inner = 1, outer = 1;
+            for (int a = 0; a < split; ++a) inner *= s.ax[a].P;
+            for (int a = split; a < s.n_axes; ++a) outer *= s.ax[a].P;
+            int64_t Tb = std::max<int64_t>(1, tile_target / outer);
+            Tb = std::min(Tb, inner);
+            while (Tb > 1 && Tb * outer > max_elems) --Tb;
+            int64_t Ta = std::max<int64_t>(1, tile_target / inner);
+            Ta = std::min(Ta, outer);
+            while (Ta > 1 && Ta * inner > max_elems) --Ta;
+            p1 = PassDesc{split, s.n_axes, (int32_t)Tb, 1, (int32_t)((inner + Tb - 1) / Tb),
+                          (int32_t)(Tb * outer), 1, 0};
+            p2 = PassDesc{0, split, 1, (int32_t)Ta, (int32_t)((outer + Ta - 1) / Ta),
+                          (int32_t)(inner * Ta), 0, 1};
+            smem1 = std::max(smem1, (size_t)(Tb * outer + tw_elems(split, s.n_axes)) * p->esz);
+            smem2 = std::max(smem2, (size_t)(inner * Ta + tw_elems(0, split)) * p->esz);
+            max_tile1 = std::max<int64_t>(max_tile1, Tb * outer);
+            max_tile2 = std::max<int64_t>(max_tile2, inner * Ta);
+        }
+        bin_base += B;
+    }
+    pd.sumB = (int32_t)bin_base;
+    pd.y_per_sig = (int64_t)bin_base * n_delays;
+    p->smem1 = smem1;
+    p->smem2 = smem2;
+    auto pick_threads = [](int64_t tile) {
+        int64_t t = (tile / 8 + 31) / 32 * 32;
+        return (int)std::min<int64_t>(512, std::max<int64_t>(128, t));
+    };
+    p->threads1 = pick_threads(max_tile1);
+    p->threads2 = pick_threads(max_tile2);
+
+    // device memory
+    const size_t nb = (size_t)pd.sumB, mb = (size_t)p->max_batch;
+    const size_t ybytes = (size_t)pd.y_per_sig * p->esz * mb;
+    p->ctr_stride = (int32_t)align_up((size_t)ctr_words(pd.max_rounds), 64);
+    p->sort_cap = 1;
+    while ((size_t)p->sort_cap < nb) p->sort_cap <<= 1;
+    p->smem_cap = std::min(p->sort_cap, 4096);
+    // decode workspace, one block carved into arrays
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o2 = off;
+        off = align_up(off + bytes, 256);
+        return o2;
+    };
+    const size_t o_state = carve(nb * mb);
+    const size_t o_dirty = carve(4 * nb * mb);
+    const size_t o_cand = carve(8 * nb * mb);
+    const size_t o_l0 = carve(4 * nb * mb);
+    const size_t o_l1 = carve(4 * nb * mb);
+    const size_t o_nzl = carve(4 * nb * mb);
+    const size_t o_cbin = carve(4 * nb * mb);
+    const size_t o_cf = carve(8 * nb * mb);
+    const size_t o_cv = carve(p->esz * nb * mb);
+    const size_t o_rf = carve(8 * nb * mb);
+    const size_t o_rv = carve(p->esz * nb * mb);
+    const size_t o_ctr = carve(4 * (size_t)p->ctr_stride * mb);
+    p->dec_bytes = off;
+    p->ctr_bytes_per_sig = 4 * (size_t)p->ctr_stride;
+
+    cudaError_t e = cudaSuccess;
+    auto dmalloc = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMalloc(ptr, bytes);
+    };
+    dmalloc((void**)&p->d_nidx, 4 * h_nidx.size());
+    dmalloc((void**)&p->d_pbin, 4 * h_pbin.size());
+    dmalloc((void**)&p->d_bpos, 4 * h_bpos.size());
+    dmalloc(&p->d_tw, p->esz * tw_P.size());
+    dmalloc(&p->d_bins, ybytes);
+    if (p->need_pass2) dmalloc(&p->d_scratch, ybytes);
+    dmalloc(&p->d_dec, p->dec_bytes);
+    dmalloc((void**)&p->d_ptrs, 3 * sizeof(void*) * mb);
+    dmalloc((void**)&p->d_sortbuf, 2 * sizeof(uint64_t) * (size_t)p->sort_cap * mb);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaHostAlloc((void**)&p->h_ptrs[i], 3 * sizeof(void*) * mb, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ptr_ev[i], cudaEventDisableTiming);
+    }
+    int32_t* d_twP = nullptr;
+    int32_t* d_twt = nullptr;
+    dmalloc((void**)&d_twP, 4 * tw_P.size());
+    dmalloc((void**)&d_twt, 4 * tw_t.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_nidx, h_nidx.data(), 4 * h_nidx.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_pbin, h_pbin.data(), 4 * h_pbin.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_bpos, h_bpos.data(), 4 * h_bpos.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_twP, tw_P.data(), 4 * tw_P.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_twt, tw_t.data(), 4 * tw_t.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_twiddles(p->d_tw, d_twP, d_twt, (int64_t)tw_P.size(), p->prec, 0);
+    if (e == cudaSuccess) e = cudaMemset(p->d_dec, 0, p->dec_bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (d_twP) cudaFree(d_twP);
+    if (d_twt) cudaFree(d_twt);
+    if (e != cudaSuccess) {
+        const int code = e == cudaErrorMemoryAllocation ? SFFT_ENOMEM : cuda_fail(e);
+        free_plan_memory(p);
+        delete p;
+        return code;
+    }
+    unsigned char* base = (unsigned char*)p->d_dec;
+    DecodeWs& w = p->ws;
+    w.state = (uint8_t*)(base + o_state);
+    w.dirty = (uint32_t*)(base + o_dirty);
+    w.cand = (int64_t*)(base + o_cand);
+    w.list0 = (int32_t*)(base + o_l0);
+    w.list1 = (int32_t*)(base + o_l1);
+    w.nzl = (int32_t*)(base + o_nzl);
+    w.cbin = (int32_t*)(base + o_cbin);
+    w.cf = (int64_t*)(base + o_cf);
+    w.cv = base + o_cv;
+    w.rec_f = (int64_t*)(base + o_rf);
+    w.rec_v = base + o_rv;
+    w.ctr = (int32_t*)(base + o_ctr);
+    p->footprint = 4 * 3 * h_nidx.size() + p->esz * tw_P.size() + ybytes * (p->need_pass2 ? 2 : 1) +
+                   p->dec_bytes + 2 * sizeof(uint64_t) * (size_t)p->sort_cap * mb;
+    p->decode_occ = decode_occupancy(p->prec, 512);
+    *out = p;
+    return SFFT_OK;
+}
+
+extern "C" void sfft_plan_destroy(sfft_plan_t p)
+{
+    if (!p) return;
+    cudaDeviceSynchronize();
+    free_plan_memory(p);
+    delete p;
+}
+
+extern "C" int64_t sfft_plan_num_bins(sfft_plan_t p) { return p ? p->pd.sumB : -1; }
+
+namespace sfft {
+
+// Enqueue the whole path for n signals of one plan (n <= max_batch).  xs/out pointer
+// tables are already on the device when n > 1 (d_tab != nullptr).
+int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
+              int64_t* idx0, void* val0, int64_t* const* d_idx, void* const* d_val,
+              int32_t* infos, const void* bins_in, cudaStream_t st)
+{
+    PlanDesc& pd = p->pd;
+    CK(cudaMemsetAsync(p->ws.ctr, 0, p->ctr_bytes_per_sig * n, st));
+    if (bins_in) {
+        // caller-supplied natural-order bins (sfft_decode_bins): permute to storage order
+        CK(launch_bins_to_natural(pd, p->d_pbin, bins_in, p->d_bins, p->prec, 0, st));
+    } else {
+        BucketArgs a;
+        memset(&a, 0, sizeof(a));
+        a.pd = pd;
+        a.n_sig = n;
+        a.nidx = p->d_nidx;
+        a.tw = p->d_tw;
+        a.xs = d_xs;
+        a.x0 = x0;
+        a.scratch = p->d_scratch;
+        a.bins = p->d_bins;
+        for (int pass = 0; pass < (p->need_pass2 ? 2 : 1); ++pass) {
+            const PassDesc* src = pass == 0 ? p->pass1 : p->pass2;
+            a.tile_prefix[0] = 0;
+            for (int d = 0; d < kMaxStages; ++d) {
+                a.pass[d] = d < pd.D ? src[d] : PassDesc{};
+                a.tile_prefix[d + 1] = a.tile_prefix[d] + (d < pd.D ? src[d].n_tiles * pd.R : 0);
+            }
+            a.tiles_per_sig = a.tile_prefix[kMaxStages];
+            CK(launch_bucketize(a, p->prec, p->xdouble, pass == 0 ? p->threads1 : p->threads2,
+                                pass == 0 ? p->smem1 : p->smem2, st));
+        }
+    }
+    DecodeArgs da;
+    memset(&da, 0, sizeof(da));
+    da.pd = pd;
+    da.ws = p->ws;
+    da.ctr_stride = p->ctr_stride;
+    da.n_sig = n;
+    da.pbin = p->d_pbin;
+    da.bpos = p->d_bpos;
+    da.bins = p->d_bins;
+    const int threads = 512;
+    const int total = p->num_sms * p->decode_occ;
+    int G = 1;
+    if (n < total) {
+        G = (int)std::min<int64_t>(total / n, ((int64_t)pd.sumB + 2047) / 2048);
+        G = std::max(G, 1);
+    }
+    da.G = G;
+    CK(launch_decode(da, p->prec, threads, G > 1, st));
+
+    CompactArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.pd = pd;
+    ca.ws = p->ws;
+    ca.ctr_stride = p->ctr_stride;
+    ca.n_sig = n;
+    ca.sort_cap = p->sort_cap;
+    ca.smem_cap = p->smem_cap;
+    ca.sortbuf = p->d_sortbuf;
+    ca.out_idx = d_idx;
+    ca.out_val = d_val;
+    ca.infos = infos;
+    ca.idx0 = idx0;
+    ca.val0 = val0;
+    CK(launch_compact(ca, p->prec, p->xdouble, 1024, 2 * sizeof(uint64_t) * (size_t)p->smem_cap, st));
+    return SFFT_OK;
+}
+
+static bool is_host_ptr(const void* ptr)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+}  // namespace sfft
+
+extern "C" int sfft_execute(sfft_plan_t p, const void* x, int64_t* out_idx, void* out_val,
+                            int32_t* out_info, void* stream)
+{
+    if (!p || !x || !out_idx || !out_val || !out_info) return SFFT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool hx = is_host_ptr(x), hi = is_host_ptr(out_idx), hv = is_host_ptr(out_val),
+               hf = is_host_ptr(out_info);
+    if (!(hx || hi || hv || hf)) return run_chunk(p, 1, x, nullptr, out_idx, out_val, nullptr, nullptr, out_info, nullptr, st);
+    // host buffers: stage through device memory owned by the plan
+    const size_t xb = (size_t)p->pd.N * p->xesz;
+    const size_t ob = align_up((size_t)p->pd.K * 8, 256) + align_up((size_t)p->pd.K * p->xesz, 256) + 256;
+    if (!p->d_x_stage) CK(cudaMalloc(&p->d_x_stage, xb));
+    if (!p->d_out_stage) CK(cudaMalloc(&p->d_out_stage, ob));
+    unsigned char* ostage = (unsigned char*)p->d_out_stage;
+    int64_t* di = (int64_t*)ostage;
+    void* dv = ostage + align_up((size_t)p->pd.K * 8, 256);
+    int32_t* dinfo = (int32_t*)(ostage + ob - 256);
+    const void* dx = x;
+    if (hx) {
+        CK(cudaMemcpyAsync(p->d_x_stage, x, xb, cudaMemcpyHostToDevice, st));
+        dx = p->d_x_stage;
+    }
+    int rc = run_chunk(p, 1, dx, nullptr, hi ? di : out_idx, hv ? dv : out_val, nullptr, nullptr,
+                       hf ? dinfo : out_info, nullptr, st);
+    if (rc) return rc;
+    if (hi) CK(cudaMemcpyAsync(out_idx, di, (size_t)p->pd.K * 8, cudaMemcpyDeviceToHost, st));
+    if (hv) CK(cudaMemcpyAsync(out_val, dv, (size_t)p->pd.K * p->xesz, cudaMemcpyDeviceToHost, st));
+    if (hf) CK(cudaMemcpyAsync(out_info, dinfo, 16, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SFFT_OK;
+}
+
+namespace sfft {
+int execute_group(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
+                  void* const* val, int32_t* infos, cudaStream_t st)
+{
+    for (int c0 = 0; c0 < n; c0 += p->max_batch) {
+        const int m = std::min(p->max_batch, n - c0);
+        if (m == 1) {
+            int rc = run_chunk(p, 1, xs[c0], nullptr, idx[c0], val[c0], nullptr, nullptr,
+                               infos + 4 * c0, nullptr, st);
+            if (rc) return rc;
+            continue;
+        }
+        const int slot = p->ptr_slot;
+        p->ptr_slot ^= 1;
+        CK(cudaEventSynchronize(p->ptr_ev[slot]));
+        void** h = p->h_ptrs[slot];
+        const size_t mb = (size_t)p->max_batch;
+        for (int i = 0; i < m; ++i) {
+            h[i] = (void*)xs[c0 + i];
+            h[mb + i] = (void*)idx[c0 + i];
+            h[2 * mb + i] = (void*)val[c0 + i];
+        }
+        CK(cudaMemcpyAsync(p->d_ptrs, h, 3 * sizeof(void*) * mb, cudaMemcpyHostToDevice, st));
+        CK(cudaEventRecord(p->ptr_ev[slot], st));
+        int rc = run_chunk(p, m, nullptr, (const void* const*)p->d_ptrs, nullptr, nullptr,
+                           (int64_t* const*)(p->d_ptrs + mb), (void* const*)(p->d_ptrs + 2 * mb),
+                           infos + 4 * c0, nullptr, st);
+        if (rc) return rc;
+    }
+    return SFFT_OK;
+}
+}  // namespace sfft
+
+extern "C" int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const void* const* xs,
+                                  int64_t* const* idx, void* const* val, int32_t* infos,
+                                  void* stream)
+{
+    if (n < 0 || (n > 0 && (!plans || !xs || !idx || !val || !infos))) return SFFT_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!plans[i] || !xs[i] || !idx[i] || !val[i]) return SFFT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    // group signals by plan, keep first-seen order of plans
+    std::vector<char> done(n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (done[i]) continue;
+        sfft_plan_s* p = plans[i];
+        std::vector<const void*> gx;
+        std::vector<int64_t*> gi;
+        std::vector<void*> gv;
+        std::vector<int> who;
+        for (int k = i; k < n; ++k)
+            if (!done[k] && plans[k] == p) {
+                done[k] = 1;
+                gx.push_back(xs[k]);
+                gi.push_back(idx[k]);
+                gv.push_back(val[k]);
+                who.push_back(k);
+            }
+        // contiguous info rows for the group are only possible when the group is a run;
+        // otherwise decode into a scratch info array and scatter
+        bool run = true;
+        for (size_t q = 0; q < who.size(); ++q)
+            if (who[q] != who[0] + (int)q) run = false;
+        if (run) {
+            int rc = execute_group(p, (int)who.size(), gx.data(), gi.data(), gv.data(),
+                                   infos + 4 * who[0], st);
+            if (rc) return rc;
+        } else {
+            for (size_t q = 0; q < who.size(); ++q) {
+                int rc = execute_group(p, 1, &gx[q], &gi[q], &gv[q], infos + 4 * who[q], st);
+                if (rc) return rc;
+            }
+        }
+    }
+    return SFFT_OK;
+}
+
+extern "C" int sfft_bucketize(sfft_plan_t p, const void* x, void* bins, void* stream)
+{
+    if (!p || !x || !bins) return SFFT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    BucketArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pd = p->pd;
+    a.n_sig = 1;
+    a.nidx = p->d_nidx;
+    a.tw = p->d_tw;
+    a.x0 = x;
+    a.scratch = p->d_scratch;
+    a.bins = p->d_bins;
+    for (int pass = 0; pass < (p->need_pass2 ? 2 : 1); ++pass) {
+        const PassDesc* src = pass == 0 ? p->pass1 : p->pass2;
+        a.tile_prefix[0] = 0;
+        for (int d = 0; d < kMaxStages; ++d) {
+            a.pass[d] = d < p->pd.D ? src[d] : PassDesc{};
+            a.tile_prefix[d + 1] = a.tile_prefix[d] + (d < p->pd.D ? src[d].n_tiles * p->pd.R : 0);
+        }
+        a.tiles_per_sig = a.tile_prefix[kMaxStages];
+        CK(launch_bucketize(a, p->prec, p->xdouble, pass == 0 ? p->threads1 : p->threads2,
+                            pass == 0 ? p->smem1 : p->smem2, st));
+    }
+    CK(launch_bins_to_natural(p->pd, p->d_pbin, p->d_bins, bins, p->prec, 1, st));
+    return SFFT_OK;
+}
+
+extern "C" int sfft_decode_bins(sfft_plan_t p, const void* bins, int64_t* out_idx, void* out_val,
+                                int32_t* out_info, void* stream)
+{
+    if (!p || !bins || !out_idx || !out_val || !out_info) return SFFT_EINVAL;
+    return run_chunk(p, 1, nullptr, nullptr, out_idx, out_val, nullptr, nullptr, out_info, bins,
+                     (cudaStream_t)stream);
+}
+
+extern "C" const char* sfft_error_string(int code)
+{
+    switch (code) {
+        case SFFT_OK: return "ok";
+        case SFFT_PENDING: return "pending";
+        case SFFT_INCOMPLETE: return "incomplete: peeling ended with unresolved bins";
+        case SFFT_EINVAL: return "invalid argument";
+        case SFFT_ENOMEM: return "out of memory";
+        case SFFT_ECUDA: return "CUDA error";
+        case SFFT_ETIMEDOUT: return "device wait timed out";
+        case SFFT_EADMIT: return "request exceeds the server memory budget";
+        case SFFT_ENOTFOUND: return "unknown ticket";
+        case SFFT_EBUSY: return "server queue full";
+        default: return "unknown code";
+    }
+}
+
+extern "C" const char* sfft_last_cuda_error(void) { return sfft::g_last_cuda; }

@@ -1,0 +1,539 @@
+// decode.cu -- peeling decoder (Sec. 3.2, subproblems 1-3, Eq. 20) and output compaction.
+//
+// One group of G CTAs decodes one signal in parallel rounds (genie-assisted peeling):
+//   D1  every examined bin: energy sum_r |Y_r|^2 against T0 -> zero-ton, else queued;
+//   D2  every queued bin: location (ARG phase or ML candidate search), least-squares value
+//       v and residual rho; rho <= T1 -> single-ton candidate (the bin is resolved);
+//   P   every candidate frequency f not already taken (earlier round, or a lower stage in
+//       this round): recorded, and B_e v a_r(f) subtracted from bin f mod B_e of every
+//       stage e and delay r (float/double atomics); bins that change and are still open
+//       are queued for the next round.
+// Phases are separated by a group barrier (a bounded spin when G > 1, so a lost CTA turns
+// into SFFT_ETIMEDOUT instead of a hang).  Locations and fits use FP64 (twiddles from the
+// exact integer residue (f tau) mod N); the FP32 path keeps bins and subtraction in FP32.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "launch.h"
+#include "sfft_internal.cuh"
+
+namespace sfft {
+
+constexpr long long kSpinLimit = 1ll << 22;  // ~0.3-1 s of polling at 64-256 ns per poll
+constexpr int64_t kFMask = (1ll << 40) - 1;
+
+__device__ __forceinline__ int ldv(const int32_t* p) { return *(const volatile int32_t*)p; }
+
+// Barrier of the G CTAs decoding one signal; returns false when the wait ran out (or any
+// CTA of the group saw it run out), in which case the error word is set.
+__device__ bool group_barrier(int32_t* ctr, int G)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = ldv(ctr + kCtrErr) == 0;
+        if (G > 1 && good) {
+            const int gen = ldv(ctr + kCtrBarGen);
+            __threadfence();
+            if (atomicAdd(ctr + kCtrBarCount, 1) == G - 1) {
+                atomicExch(ctr + kCtrBarCount, 0);
+                __threadfence();
+                atomicAdd(ctr + kCtrBarGen, 1);
+            } else {
+                long long it = 0;
+                while (ldv(ctr + kCtrBarGen) == gen) {
+                    if (++it > kSpinLimit || ldv(ctr + kCtrErr) != 0) {
+                        atomicExch(ctr + kCtrErr, 1);
+                        good = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        } else if (G == 1) {
+            __threadfence_block();
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ int stage_of(const PlanDesc& pd, int b)
+{
+    int d = 0;
+    while (d + 1 < pd.D && b >= pd.st[d + 1].bin_base) ++d;
+    return d;
+}
+
+// e^{+2 pi i (f tau mod N) / N} in FP64 from the exact integer residue
+__device__ __forceinline__ double2 delay_phasor(int64_t f, int64_t tau, int64_t N)
+{
+    const int64_t m = (f * tau) % N;
+    double s, c;
+    sincospi(2.0 * (double)m / (double)N, &s, &c);
+    return double2{c, s};
+}
+
+template <typename V>
+__device__ __forceinline__ double2 to_d2(V v)
+{
+    return double2{(double)v.x, (double)v.y};
+}
+
+template <typename T>
+__device__ __forceinline__ void record_candidate(const DecodeArgs& a, int32_t* ctr,
+                                                 const DecodeWs& w, int round, int b, int64_t f,
+                                                 double2 v)
+{
+    using V = typename C2<T>::t;
+    __stcg(w.state + b, (uint8_t)2);
+    __stcg((long long*)w.cand + b, (long long)(((int64_t)round << 40) | f));
+    const int k = atomicAdd(ctr + kCtrRoundBase + 3 * round + 2, 1);
+    __stcg(w.cbin + k, b);
+    __stcg((long long*)w.cf + k, (long long)f);
+    reinterpret_cast<V*>(w.cv)[k] = V{(T)v.x, (T)v.y};
+    atomicAdd(ctr + kCtrResolved, 1);
+}
+
+// D2, ML locate: one warp per non-zero bin.  Lanes score the candidates f = j + q B
+// (q < L) by |sum_r Y_r conj(a_r(f))|^2 (arithmetic type T), the warp keeps the best
+// (lowest q on ties), then fits v and rho in FP64 with one lane per delay.
+template <typename T>
+__device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                               const typename C2<T>::t* Y, int round, int b)
+{
+    using V = typename C2<T>::t;
+    const PlanDesc& pd = a.pd;
+    const int lane = threadIdx.x & 31;
+    const int d = stage_of(pd, b);
+    const StageDesc& st = pd.st[d];
+    const int p = b - st.bin_base;
+    const int R = pd.R;
+    const int B = st.B, L = st.L, N = pd.N;
+    const int j = __ldg(a.pbin + b);
+    const V* Yb = Y + st.y_off + p;
+    V my = {0, 0};
+    if (lane < R) my = __ldcg(Yb + (int64_t)lane * B);
+    T yr[kMaxDelays][2];
+    int mr[kMaxDelays], step[kMaxDelays];
+#pragma unroll
+    for (int r = 0; r < kMaxDelays; ++r) {
+        yr[r][0] = __shfl_sync(0xffffffffu, my.x, r);
+        yr[r][1] = __shfl_sync(0xffffffffu, my.y, r);
+        if (r < R) {
+            const int64_t tau = st.tau[r];
+            mr[r] = (int)((((int64_t)j + (int64_t)lane * B) * tau) % N);
+            step[r] = (int)((((int64_t)32 * B) * tau) % N);
+        } else {
+            mr[r] = 0;
+            step[r] = 0;
+        }
+    }
+    const T two_over_n = (T)2 / (T)N;
+    T best = (T)-1;
+    int bq = 0;
+    for (int q = lane; q < L; q += 32) {
+        T cx = 0, cy = 0;
+#pragma unroll
+        for (int r = 0; r < kMaxDelays; ++r) {
+            if (r < R) {
+                T sv, cv;
+                sincospi((T)mr[r] * two_over_n, &sv, &cv);
+                // Y_r * conj(a) with a = (cv, sv)
+                cx += yr[r][0] * cv + yr[r][1] * sv;
+                cy += yr[r][1] * cv - yr[r][0] * sv;
+                int nm = mr[r] + step[r];
+                mr[r] = nm >= N ? nm - N : nm;
+            }
+        }
+        const T sc = cx * cx + cy * cy;
+        if (sc > best) {
+            best = sc;
+            bq = q;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+        if (ob > best || (ob == best && oq < bq)) {
+            best = ob;
+            bq = oq;
+        }
+    }
+    const int64_t f = (int64_t)j + (int64_t)bq * B;
+    // least-squares value and residual over the R delays, FP64
+    double2 ar = {0, 0}, cr = {0, 0};
+    if (lane < R) {
+        ar = delay_phasor(f, st.tau[lane], N);
+        const double2 y = to_d2(my);
+        cr = double2{y.x * ar.x + y.y * ar.y, y.y * ar.x - y.x * ar.y};
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cr.x += __shfl_xor_sync(0xffffffffu, cr.x, o);
+        cr.y += __shfl_xor_sync(0xffffffffu, cr.y, o);
+    }
+    const double sc = 1.0 / ((double)R * (double)B);
+    const double2 v = {cr.x * sc, cr.y * sc};
+    double e2 = 0;
+    if (lane < R) {
+        const double2 y = to_d2(my);
+        const double ex = y.x - (double)B * (v.x * ar.x - v.y * ar.y);
+        const double ey = y.y - (double)B * (v.x * ar.y + v.y * ar.x);
+        e2 = ex * ex + ey * ey;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    if (lane == 0 && e2 <= st.T1) record_candidate<T>(a, ctr, w, round, b, f, v);
+}
+
+// D2, ARG locate (FFAST, Sec. 3.2 subproblem 2): f from the phase of Y(1) conj(Y(0)),
+// snapped to the candidate set {j + q B}; one thread per bin.
+template <typename T>
+__device__ void locate_arg_thread(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                                  const typename C2<T>::t* Y, int round, int b)
+{
+    const PlanDesc& pd = a.pd;
+    const int d = stage_of(pd, b);
+    const StageDesc& st = pd.st[d];
+    const int p = b - st.bin_base;
+    const int R = pd.R;
+    const int B = st.B, L = st.L, N = pd.N;
+    const int j = __ldg(a.pbin + b);
+    const auto* Yb = Y + st.y_off + p;
+    const double2 y0 = to_d2(__ldcg(Yb + (int64_t)st.r0 * B));
+    const double2 y1 = to_d2(__ldcg(Yb + (int64_t)st.r1 * B));
+    const double rx = y1.x * y0.x + y1.y * y0.y;
+    const double ry = y1.y * y0.x - y1.x * y0.y;
+    const double fe = atan2(ry, rx) * (double)N / 6.283185307179586476925286766559;
+    const double qd = floor((fe - (double)j) / (double)B + 0.5);
+    int64_t q = (int64_t)qd % L;
+    if (q < 0) q += L;
+    const int64_t f = (int64_t)j + q * B;
+    double2 c = {0, 0};
+    for (int r = 0; r < R; ++r) {
+        const double2 ar = delay_phasor(f, st.tau[r], N);
+        const double2 y = to_d2(__ldcg(Yb + (int64_t)r * B));
+        c.x += y.x * ar.x + y.y * ar.y;
+        c.y += y.y * ar.x - y.x * ar.y;
+    }
+    const double sc = 1.0 / ((double)R * (double)B);
+    const double2 v = {c.x * sc, c.y * sc};
+    double e2 = 0;
+    for (int r = 0; r < R; ++r) {
+        const double2 ar = delay_phasor(f, st.tau[r], N);
+        const double2 y = to_d2(__ldcg(Yb + (int64_t)r * B));
+        const double ex = y.x - (double)B * (v.x * ar.x - v.y * ar.y);
+        const double ey = y.y - (double)B * (v.x * ar.y + v.y * ar.x);
+        e2 += ex * ex + ey * ey;
+    }
+    if (e2 <= st.T1) record_candidate<T>(a, ctr, w, round, b, f, v);
+}
+
+__device__ __forceinline__ void atomic_sub_c(float2* p, double2 d)
+{
+    atomicAdd(&p->x, (float)-d.x);
+    atomicAdd(&p->y, (float)-d.y);
+}
+__device__ __forceinline__ void atomic_sub_c(double2* p, double2 d)
+{
+    atomicAdd(&p->x, -d.x);
+    atomicAdd(&p->y, -d.y);
+}
+
+// P: accept candidate c and peel it from every stage (Eq. 20)
+template <typename T>
+__device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                               typename C2<T>::t* Y, int round, int c)
+{
+    using V = typename C2<T>::t;
+    const PlanDesc& pd = a.pd;
+    const int b = __ldcg(w.cbin + c);
+    const int64_t f = (int64_t)__ldcg((const long long*)w.cf + c);
+    const V vv = __ldcg(reinterpret_cast<const V*>(w.cv) + c);
+    const double2 v = to_d2(vv);
+    const int d = stage_of(pd, b);
+    for (int e = 0; e < pd.D; ++e) {
+        if (e == d) continue;
+        const StageDesc& se = pd.st[e];
+        const int je = (int)(f % se.B);
+        const int be = se.bin_base + __ldg(a.bpos + se.bin_base + je);
+        const int64_t cw = (int64_t)__ldcg((const long long*)w.cand + be);
+        if (cw >= 0 && (cw & kFMask) == f) {
+            const int rd = (int)(cw >> 40);
+            if (rd < round || (rd == round && e < d)) return;
+        }
+    }
+    const int k = atomicAdd(ctr + kCtrRec, 1);
+    __stcg((long long*)w.rec_f + k, (long long)f);
+    reinterpret_cast<V*>(w.rec_v)[k] = vv;
+    for (int e = 0; e < pd.D; ++e) {
+        const StageDesc& se = pd.st[e];
+        const int je = (int)(f % se.B);
+        const int pe = __ldg(a.bpos + se.bin_base + je);
+        const int be = se.bin_base + pe;
+        for (int r = 0; r < pd.R; ++r) {
+            const double2 ar = delay_phasor(f, se.tau[r], pd.N);
+            const double2 dlt = {(double)se.B * (v.x * ar.x - v.y * ar.y),
+                                 (double)se.B * (v.x * ar.y + v.y * ar.x)};
+            atomic_sub_c(Y + se.y_off + (int64_t)r * se.B + pe, dlt);
+        }
+        if (__ldcg(w.state + be) == 0 && atomicExch(w.dirty + be, 1u) == 0u) {
+            const int q = atomicAdd(ctr + kCtrRoundBase + 3 * round + 0, 1);
+            int32_t* nl = (round & 1) ? w.list1 : w.list0;
+            __stcg(nl + q, be);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) decode_kernel(const __grid_constant__ DecodeArgs a)
+{
+    using V = typename C2<T>::t;
+    const PlanDesc& pd = a.pd;
+    const int G = a.G;
+    const int sig = blockIdx.x / G;
+    const int gi = blockIdx.x - sig * G;
+    if (sig >= a.n_sig) return;
+    const int nb = pd.sumB;
+    DecodeWs w = a.ws;
+    const int64_t so = (int64_t)sig * nb;
+    w.state += so;
+    w.dirty += so;
+    w.cand += so;
+    w.list0 += so;
+    w.list1 += so;
+    w.nzl += so;
+    w.cbin += so;
+    w.cf += so;
+    w.cv = reinterpret_cast<V*>(w.cv) + so;
+    w.rec_f += so;
+    w.rec_v = reinterpret_cast<V*>(w.rec_v) + so;
+    int32_t* ctr = w.ctr + (int64_t)sig * a.ctr_stride;
+    V* Y = reinterpret_cast<V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
+
+    const int wt = gi * blockDim.x + threadIdx.x;
+    const int nw = G * blockDim.x;
+    const int gw = wt >> 5, nwarps = nw >> 5;
+    const int R = pd.R;
+
+    int round = 0;
+    while (true) {
+        ++round;
+        // D1: energies of the examined bins
+        const int n_act = round == 1 ? nb : ldv(ctr + kCtrRoundBase + 3 * (round - 1) + 0);
+        const int32_t* act = ((round - 1) & 1) ? w.list1 : w.list0;
+        for (int i = wt; i < n_act; i += nw) {
+            const int b = round == 1 ? i : __ldcg(act + i);
+            if (round == 1) __stcg((long long*)w.cand + b, -1ll);
+            __stcg(w.dirty + b, 0u);
+            const int d = stage_of(pd, b);
+            const StageDesc& st = pd.st[d];
+            const V* Yb = Y + st.y_off + (b - st.bin_base);
+            double E = 0;
+            for (int r = 0; r < R; ++r) {
+                const V y = __ldcg(Yb + (int64_t)r * st.B);
+                E += (double)y.x * y.x + (double)y.y * y.y;
+            }
+            if (E <= st.T0) {
+                __stcg(w.state + b, (uint8_t)1);
+                atomicAdd(ctr + kCtrResolved, 1);
+            } else {
+                if (round == 1) __stcg(w.state + b, (uint8_t)0);
+                const int k = atomicAdd(ctr + kCtrRoundBase + 3 * round + 1, 1);
+                __stcg(w.nzl + k, b);
+            }
+        }
+        if (wt == 0) atomicAdd(ctr + kCtrIdents, n_act);
+        if (!group_barrier(ctr, G)) break;
+
+        // D2: locate, fit, singleton test
+        const int n_nz = ldv(ctr + kCtrRoundBase + 3 * round + 1);
+        if (pd.locate == 1) {
+            for (int i = gw; i < n_nz; i += nwarps)
+                locate_ml_warp<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
+        } else {
+            for (int i = wt; i < n_nz; i += nw)
+                locate_arg_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
+        }
+        if (!group_barrier(ctr, G)) break;
+
+        // P: accept and peel
+        const int n_c = ldv(ctr + kCtrRoundBase + 3 * round + 2);
+        for (int i = wt; i < n_c; i += nw) peel_candidate<T>(a, ctr, w, Y, round, i);
+        if (!group_barrier(ctr, G)) break;
+
+        const int n_next = ldv(ctr + kCtrRoundBase + 3 * round + 0);
+        if (n_next == 0 || round >= pd.max_rounds) break;
+    }
+    if (gi == 0 && threadIdx.x == 0) ctr[kCtrRounds] = round;
+}
+
+// ---------------------------------------------------------------------------------------
+// Output (Sec. 2.1): the K largest recovered coefficients, sorted by frequency.  One CTA
+// per signal; bitonic sorts in shared memory (or in the slot's global sort buffer when the
+// recovered list is larger than the shared-memory capacity).
+
+__device__ void bitonic_sort(uint64_t* key, int n_pad)
+{
+    for (int k = 2; k <= n_pad; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n_pad; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t x = key[i], y = key[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        key[i] = y;
+                        key[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t mag_key(float2 v)
+{
+    return __float_as_uint(v.x * v.x + v.y * v.y);
+}
+__device__ __forceinline__ uint32_t mag_key(double2 v)
+{
+    return (uint32_t)(__double_as_longlong(v.x * v.x + v.y * v.y) >> 32);
+}
+
+template <typename T, typename XS>
+__global__ void __launch_bounds__(1024) compact_kernel(const __grid_constant__ CompactArgs a)
+{
+    using V = typename C2<T>::t;
+    using XV = typename C2<XS>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int sig = blockIdx.x;
+    const PlanDesc& pd = a.pd;
+    const int nb = pd.sumB;
+    const int32_t* ctr = a.ws.ctr + (int64_t)sig * a.ctr_stride;
+    const int64_t* rec_f = a.ws.rec_f + (int64_t)sig * nb;
+    const V* rec_v = reinterpret_cast<const V*>(a.ws.rec_v) + (int64_t)sig * nb;
+    const int n = ldv(ctr + kCtrRec);
+    const int K = pd.K;
+    int n_pad = 1;
+    while (n_pad < n) n_pad <<= 1;
+    uint64_t* k1;
+    uint64_t* k2;
+    if (n_pad <= a.smem_cap) {
+        k1 = reinterpret_cast<uint64_t*>(smem_raw);
+        k2 = k1 + a.smem_cap;
+    } else {
+        k1 = a.sortbuf + (int64_t)sig * 2 * a.sort_cap;
+        k2 = k1 + a.sort_cap;
+    }
+    for (int i = threadIdx.x; i < n_pad; i += blockDim.x)
+        k1[i] = i < n ? (((uint64_t)__ldcg((const long long*)rec_f + i) << 32) | (uint32_t)i)
+                      : ~0ull;
+    __syncthreads();
+    bitonic_sort(k1, n_pad);
+    int cnt = n;
+    const uint64_t* order = k1;  // entries [0, cnt) in frequency order
+    if (n > K) {
+        // rank by magnitude (larger first, lower frequency on ties), keep K, re-sort ranks
+        for (int i = threadIdx.x; i < n_pad; i += blockDim.x) {
+            uint64_t kk = ~0ull;
+            if (i < n) {
+                const uint32_t idx = (uint32_t)(k1[i] & 0xffffffffu);
+                kk = ((uint64_t)(~mag_key(__ldcg(rec_v + idx))) << 32) | (uint32_t)i;
+            }
+            k2[i] = kk;
+        }
+        __syncthreads();
+        bitonic_sort(k2, n_pad);
+        for (int i = threadIdx.x; i < n_pad; i += blockDim.x)
+            k2[i] = i < K ? (k2[i] & 0xffffffffu) : ~0ull;
+        __syncthreads();
+        bitonic_sort(k2, n_pad);
+        cnt = K;
+    }
+    int64_t* oi = a.out_idx ? a.out_idx[sig] : a.idx0;
+    XV* ov = reinterpret_cast<XV*>(a.out_val ? a.out_val[sig] : a.val0);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint64_t e = n > K ? order[k2[i]] : order[i];
+        const uint32_t idx = (uint32_t)(e & 0xffffffffu);
+        oi[i] = (int64_t)(e >> 32);
+        const V v = __ldcg(rec_v + idx);
+        ov[i] = XV{(XS)v.x, (XS)v.y};
+    }
+    if (threadIdx.x == 0) {
+        int32_t* info = a.infos + 4 * sig;
+        const int err = ldv(ctr + kCtrErr);
+        const int resolved = ldv(ctr + kCtrResolved);
+        info[0] = cnt;
+        info[1] = err ? -4 : (resolved < nb ? 2 : 0);
+        info[2] = ldv(ctr + kCtrRounds);
+        info[3] = ldv(ctr + kCtrIdents);
+    }
+}
+
+cudaError_t launch_decode(const DecodeArgs& a, int precision, int threads, bool cooperative,
+                          cudaStream_t st)
+{
+    const unsigned grid = (unsigned)a.n_sig * (unsigned)a.G;
+    if (grid == 0) return cudaSuccess;
+    void* fn = precision == 1 ? (void*)decode_kernel<float> : (void*)decode_kernel<double>;
+    if (cooperative) {
+        void* args[] = {(void*)&a};
+        return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, st);
+    }
+    if (precision == 1)
+        decode_kernel<float><<<grid, threads, 0, st>>>(a);
+    else
+        decode_kernel<double><<<grid, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int decode_occupancy(int precision, int threads)
+{
+    int nb = 0;
+    void* fn = precision == 1 ? (void*)decode_kernel<float> : (void*)decode_kernel<double>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_compact(const CompactArgs& a, int precision, int xdouble, int threads,
+                           size_t smem, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)a.n_sig;
+    if (grid == 0) return cudaSuccess;
+    if (precision == 1) {
+        if (xdouble)
+            compact_kernel<float, double><<<grid, threads, smem, st>>>(a);
+        else
+            compact_kernel<float, float><<<grid, threads, smem, st>>>(a);
+    } else {
+        if (xdouble)
+            compact_kernel<double, double><<<grid, threads, smem, st>>>(a);
+        else
+            compact_kernel<double, float><<<grid, threads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t set_compact_smem_limit(int max_smem)
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(compact_kernel<float, float>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(compact_kernel<float, double>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(compact_kernel<double, float>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)))
+        return e;
+    return cudaFuncSetAttribute(compact_kernel<double, double>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+}
+
+}  // namespace sfft

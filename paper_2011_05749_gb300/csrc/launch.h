@@ -1,0 +1,66 @@
+// launch.h -- host-side launchers of the libsfft kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sfft_internal.cuh"
+
+namespace sfft {
+
+// Arguments of one bucketization launch (gather + prime-factor DFT passes).
+struct BucketArgs {
+    PlanDesc pd;
+    PassDesc pass[kMaxStages];
+    int32_t tile_prefix[kMaxStages + 1];  // cumulative R * n_tiles over stages
+    int32_t tiles_per_sig;
+    int32_t n_sig;
+    const int32_t* nidx;     // per stage (at bin_base): input sample index n of position p
+    const void* tw;          // plan twiddles (float2 or double2): (cos, sin)(2 pi t / P)
+    const void* const* xs;  // device array of n_sig signal pointers, or nullptr
+    const void* x0;          // the signal when xs == nullptr
+    void* scratch;           // complex, n_sig * y_per_sig
+    void* bins;              // complex, n_sig * y_per_sig
+};
+
+struct DecodeArgs {
+    PlanDesc pd;
+    DecodeWs ws;          // slot 0 pointers; slot s at + s * sumB (ctr: + s * ctr_stride)
+    int32_t ctr_stride;
+    int32_t G;            // CTAs per signal
+    int32_t n_sig;
+    int32_t pad;
+    const int32_t* pbin;  // position -> bin j, per stage at bin_base
+    const int32_t* bpos;  // bin j -> position
+    void* bins;           // complex, n_sig * y_per_sig, modified in place
+};
+
+struct CompactArgs {
+    PlanDesc pd;
+    DecodeWs ws;
+    int32_t ctr_stride;
+    int32_t n_sig;
+    int32_t sort_cap;           // pow2 capacity of sortbuf per slot
+    int32_t smem_cap;           // pow2 capacity of the shared-memory sort
+    uint64_t* sortbuf;          // 2 * sort_cap per slot
+    int64_t* const* out_idx;    // device array of n_sig pointers, or nullptr
+    void* const* out_val;
+    int64_t* idx0;              // the outputs when out_idx == nullptr (one signal)
+    void* val0;
+    int32_t* infos;             // int32[4 * n_sig]
+};
+
+// precision: 0 = double arithmetic, 1 = float; xdouble: input/output complex128
+cudaError_t launch_bucketize(const BucketArgs& a, int precision, int xdouble, int threads,
+                             size_t smem, cudaStream_t st);
+cudaError_t launch_decode(const DecodeArgs& a, int precision, int threads, bool cooperative,
+                          cudaStream_t st);
+cudaError_t launch_compact(const CompactArgs& a, int precision, int xdouble, int threads,
+                           size_t smem, cudaStream_t st);
+// natural-order copy of bins (for sfft_bucketize) and back (for sfft_decode_bins)
+cudaError_t launch_bins_to_natural(const PlanDesc& pd, const int32_t* pbin, const void* src,
+                                   void* dst, int precision, int to_natural, cudaStream_t st);
+cudaError_t launch_twiddles(void* tw, const int32_t* P_of, const int32_t* t_of, int64_t n,
+                            int precision, cudaStream_t st);
+cudaError_t set_kernel_smem_limits(int max_smem);
+int decode_occupancy(int precision, int threads);
+
+}  // namespace sfft

@@ -1,0 +1,142 @@
+// sfft_internal.cuh -- descriptors and device helpers shared by the libsfft kernels.
+//
+// Data layout in HBM (per plan workspace, per signal slot s):
+//   bins      [s][stage d][delay r][PFA position p]   complex (float2 / double2)
+//             stage d starts at y_off_d = R * sum_{d'<d} B_d'; position p is the
+//             prime-factor (Good-Thomas) storage order of the B_d outputs, see AxisDesc.
+//   scratch   same shape as bins, used between the two passes of a two-pass DFT.
+//   decode    per-bin state and lists, see DecodeWs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sfft {
+
+constexpr int kMaxStages = 4;
+constexpr int kMaxDelays = 16;
+constexpr int kMaxAxes = 6;
+
+// One axis of the prime-factor decomposition B = prod_a P_a (pairwise co-prime prime
+// powers).  Storage position p = sum_a c_a S_a.  Before an axis is transformed its
+// coordinate c_a holds input index n_a (bit-reversed for power-of-two axes, which are
+// transformed by in-place radix-2 decimation in time); afterwards it holds output k_a in
+// natural order.  Input sample index (Ruritanian map): n = sum_a n_a (B / P_a) mod B.
+// Output bin (CRT map): j = sum_a k_a crt_a mod B, crt_a = (B/P_a) ((B/P_a)^-1 mod P_a).
+struct AxisDesc {
+    int32_t P;
+    int32_t pow2;    // 1: power of two
+    int32_t log2P;
+    int32_t S;       // stride in the stage array
+    int32_t rur;     // (B / P) mod B
+    int32_t crt;     // CRT coefficient
+    int32_t tw_off;  // offset of this axis' twiddles in the plan twiddle table
+    int32_t pad;
+};
+
+// One DFT pass over a contiguous range of axes [a0, a1) of a stage.  A tile is Tb
+// consecutive positions of the dims below a0 times the axes [a0, a1) times Ta consecutive
+// positions of the dims from a1 up.
+struct PassDesc {
+    int32_t a0, a1;
+    int32_t Tb, Ta;
+    int32_t n_tiles;      // tiles per (signal, delay); 0 = stage not in this launch
+    int32_t tile_elems;   // Tb * prod P * Ta
+    int32_t src_gather;   // 1: load from x, 0: load from scratch
+    int32_t dst_bins;     // 1: store to bins, 0: store to scratch
+};
+
+struct StageDesc {
+    int32_t B, L;
+    int32_t n_axes, split;   // axes [0, split) inner group, [split, n_axes) outer group
+    AxisDesc ax[kMaxAxes];
+    int32_t tau[kMaxDelays];
+    int32_t bin_base;        // sum of B of earlier stages
+    int32_t y_off;           // R * bin_base
+    int32_t r0, r1;          // delay slots holding tau = 0 and tau = 1 (-1 if absent)
+    double T0, T1;           // thresholds on sum_r |Y_r|^2 and on the single-tone residual
+};
+
+struct PlanDesc {
+    int32_t N;
+    int32_t D, R;
+    int32_t sumB;            // bins per delay over all stages
+    int64_t y_per_sig;       // R * sumB
+    int32_t locate;          // 0 ARG, 1 ML
+    int32_t max_rounds;
+    int32_t K;
+    int32_t pad;
+    StageDesc st[kMaxStages];
+};
+
+// Decode workspace of one signal slot (all arrays sumB entries unless stated).
+struct DecodeWs {
+    uint8_t* state;      // 0 open, 1 zero-ton, 2 single-ton
+    uint32_t* dirty;     // queued for the next round
+    int64_t* cand;       // (round << 40) | f of the bin's single-ton, -1 none
+    int32_t* list0;      // bins examined in even rounds
+    int32_t* list1;      // bins examined in odd rounds
+    int32_t* nzl;        // non-zero bins of the current round
+    int32_t* cbin;       // single-ton candidates: bin
+    int64_t* cf;         //                        frequency
+    void* cv;            //                        value (complex of the arithmetic type)
+    int64_t* rec_f;      // recovered frequencies
+    void* rec_v;         // recovered values
+    int32_t* ctr;        // counters, see Ctr
+};
+
+// counter words of a signal slot
+enum Ctr : int {
+    kCtrRec = 0,        // recovered count
+    kCtrResolved = 1,   // bins resolved (zero- or single-ton)
+    kCtrIdents = 2,     // bins classified
+    kCtrRounds = 3,     // rounds run
+    kCtrErr = 4,        // device error (timeout)
+    kCtrBarCount = 5,   // group barrier arrivals
+    kCtrBarGen = 6,     // group barrier generation
+    kCtrRoundBase = 8,  // per round r (1-based): [3 r + 0] next-list size, [+1] non-zero
+                        // bins, [+2] single-ton candidates
+};
+constexpr int ctr_words(int max_rounds) { return kCtrRoundBase + 3 * (max_rounds + 2); }
+
+template <typename T> struct C2;
+template <> struct C2<float> { using t = float2; };
+template <> struct C2<double> { using t = double2; };
+
+template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) { return {a.x + b.x, a.y + b.y}; }
+template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) { return {a.x - b.x, a.y - b.y}; }
+template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+__host__ __device__ __forceinline__ int32_t bitrev(int32_t v, int32_t bits)
+{
+#ifdef __CUDA_ARCH__
+    return bits == 0 ? 0 : (int32_t)(__brev((unsigned)v) >> (32 - bits));
+#else
+    int32_t r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((v >> i) & 1) << (bits - 1 - i);
+    return r;
+#endif
+}
+
+// bin index j of storage position p in stage s (CRT map)
+__host__ __device__ __forceinline__ int32_t pos_to_bin(const StageDesc& s, int32_t p)
+{
+    int64_t j = 0;
+    for (int a = 0; a < s.n_axes; ++a) {
+        int32_t k = (p / s.ax[a].S) % s.ax[a].P;
+        j += (int64_t)k * s.ax[a].crt;
+    }
+    return (int32_t)(j % s.B);
+}
+
+// storage position of bin j in stage s
+__host__ __device__ __forceinline__ int32_t bin_to_pos(const StageDesc& s, int32_t j)
+{
+    int32_t p = 0;
+    for (int a = 0; a < s.n_axes; ++a) p += (j % s.ax[a].P) * s.ax[a].S;
+    return p;
+}
+
+}  // namespace sfft

@@ -1,0 +1,47 @@
+// sfft_plan.h -- the plan object behind sfft_plan_t (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sfft_internal.cuh"
+
+struct sfft_plan_s {
+    sfft::PlanDesc pd;                       // host copy of the device-side description
+    sfft::PassDesc pass1[sfft::kMaxStages];  // first bucketization launch, per stage
+    sfft::PassDesc pass2[sfft::kMaxStages];  // second launch (two-pass stages only)
+    bool need_pass2 = false;
+    sfft_opts opts;
+    int prec = 1;        // 1 FP32 arithmetic, 0 FP64
+    int xdouble = 0;     // 1 complex128 input/output
+    size_t esz = 8;      // bytes of one complex of the arithmetic type
+    size_t xesz = 8;     // bytes of one complex of the I/O type
+    int max_batch = 1;
+    int num_sms = 0;
+    int decode_occ = 1;
+    int threads1 = 256, threads2 = 256;
+    size_t smem1 = 0, smem2 = 0;
+    // plan tables
+    int32_t* d_nidx = nullptr;  // position -> input sample index, per stage
+    int32_t* d_pbin = nullptr;  // position -> bin j
+    int32_t* d_bpos = nullptr;  // bin j -> position
+    void* d_tw = nullptr;       // twiddles of every axis
+    // workspace for max_batch signals
+    void* d_bins = nullptr;
+    void* d_scratch = nullptr;
+    void* d_dec = nullptr;
+    size_t dec_bytes = 0;
+    sfft::DecodeWs ws;
+    int32_t ctr_stride = 0;
+    size_t ctr_bytes_per_sig = 0;
+    uint64_t* d_sortbuf = nullptr;
+    int32_t sort_cap = 1, smem_cap = 1;
+    // batch pointer tables: device copy + two pinned host slots
+    void** d_ptrs = nullptr;
+    void** h_ptrs[2] = {nullptr, nullptr};
+    cudaEvent_t ptr_ev[2] = {nullptr, nullptr};
+    int ptr_slot = 0;
+    // staging for host-memory inputs/outputs and for sfft_decode_bins
+    void* d_x_stage = nullptr;
+    void* d_out_stage = nullptr;
+    void* d_bins_in = nullptr;
+    size_t footprint = 0;  // device bytes owned by the plan
+};

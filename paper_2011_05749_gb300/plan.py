@@ -1,0 +1,182 @@
+"""Python front end of libsfft plans, batches and the serving loop (marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import check, load, ptr_of, stream_handle
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Plan:
+    """A resident sFFT plan: N, the stages' subsampling factors f (B_d = N / f_d), the
+    delays tau_{d,r} (advance sign, [n_stages, R]), the output size K and the options of
+    include/sfft.h (sfft_opts)."""
+
+    def __init__(self, N: int, K: int, f, delays, *, dtype: str = "c64",
+                 precision: str = "fp32", locate: str = "ml", noise_var: float = 0.0,
+                 a_min: float = 1.0, eta: float = 0.0, c0: float = 4.0, c1: float = 2.0,
+                 max_rounds: int = 64, max_batch: int = 1):
+        lib = load()
+        f = np.ascontiguousarray(f, dtype=np.int64)
+        delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
+        o = _lib.Opts()
+        lib.sfft_opts_default(ctypes.byref(o))
+        o.dtype = {"c64": _lib.C64, "c128": _lib.C128}[dtype]
+        o.precision = {"fp32": _lib.PREC_FP32, "fp64": _lib.PREC_FP64}[precision]
+        o.locate = {"arg": _lib.LOCATE_ARG, "ml": _lib.LOCATE_ML}[locate]
+        o.max_rounds = max_rounds
+        o.max_batch = max_batch
+        o.noise_var = noise_var
+        o.a_min = a_min
+        o.eta = eta
+        o.c0 = c0
+        o.c1 = c1
+        h = ctypes.c_void_p()
+        check(lib.sfft_plan_create(ctypes.byref(h), N, K, f.size, f.ctypes.data,
+                                   delays.shape[1], delays.ctypes.data, ctypes.byref(o)),
+              "sfft_plan_create")
+        self._h = h
+        self.N, self.K = int(N), int(K)
+        self.f = tuple(int(v) for v in f)
+        self.delays = delays.copy()
+        self.R = int(delays.shape[1])
+        self.dtype, self.precision, self.locate = dtype, precision, locate
+        self.max_batch = max_batch
+        self.num_bins = int(lib.sfft_plan_num_bins(h))
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().sfft_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ outputs
+    def _val_dtype(self, torch=None):
+        if torch is None:
+            return np.complex64 if self.dtype == "c64" else np.complex128
+        return torch.complex64 if self.dtype == "c64" else torch.complex128
+
+    def empty_outputs(self, device="cuda", n: int | None = None):
+        """(idx int64[K], val complex[K], info int32[4]) buffers on the device (or host
+        numpy arrays with device='cpu'), with a leading batch dimension when n is given."""
+        shape = (self.K,) if n is None else (n, self.K)
+        ishape = (4,) if n is None else (n, 4)
+        if device == "cpu":
+            return (np.zeros(shape, np.int64), np.zeros(shape, self._val_dtype()),
+                    np.zeros(ishape, np.int32))
+        torch = _torch()
+        return (torch.zeros(shape, dtype=torch.int64, device=device),
+                torch.zeros(shape, dtype=self._val_dtype(torch), device=device),
+                torch.zeros(ishape, dtype=torch.int32, device=device))
+
+    def execute(self, x, out=None, stream=None):
+        """Recover one signal.  x: N complex samples (cuda tensor, or host numpy array /
+        cpu tensor, which the library stages through device memory).  Returns
+        (idx, val, info) with info = [count, status, rounds, identifications]; entries
+        past count are untouched (zero on fresh buffers)."""
+        if out is None:
+            host = isinstance(x, np.ndarray) or (hasattr(x, "is_cuda") and not x.is_cuda)
+            out = self.empty_outputs("cpu" if host else "cuda")
+        idx, val, info = out
+        check(load().sfft_execute(self._h, ptr_of(x), ptr_of(idx), ptr_of(val), ptr_of(info),
+                                  stream_handle(stream)), "sfft_execute")
+        return idx, val, info
+
+    def execute_many(self, xs, out=None, stream=None):
+        """Recover a batch of signals of this plan (xs: cuda tensor [n, N] or a list)."""
+        n = len(xs)
+        if out is None:
+            out = self.empty_outputs("cuda", n)
+        execute_batch([self] * n, list(xs), out, stream)
+        return out
+
+    def bucketize(self, x, bins=None, stream=None):
+        """Bins of Eq. 6 / Eq. 19 in natural order [stage][delay][j] (device only)."""
+        torch = _torch()
+        if bins is None:
+            dt = torch.complex64 if self.precision == "fp32" else torch.complex128
+            bins = torch.empty(self.R * self.num_bins, dtype=dt, device=x.device)
+        check(load().sfft_bucketize(self._h, ptr_of(x), ptr_of(bins), stream_handle(stream)),
+              "sfft_bucketize")
+        return bins
+
+    def decode_bins(self, bins, out=None, stream=None):
+        """Peeling decoder on caller bins (natural order, arithmetic dtype; device only)."""
+        if out is None:
+            out = self.empty_outputs("cuda")
+        idx, val, info = out
+        check(load().sfft_decode_bins(self._h, ptr_of(bins), ptr_of(idx), ptr_of(val),
+                                      ptr_of(info), stream_handle(stream)), "sfft_decode_bins")
+        return idx, val, info
+
+
+def execute_batch(plans, xs, out, stream=None):
+    """sfft_execute_batch over signals of (possibly) different plans.  out = (idx list,
+    val list, infos int32 tensor [n, 4]) or per-plan stacked tensors [n, K]."""
+    n = len(plans)
+    idx, val, infos = out
+    P = ctypes.c_void_p * max(n, 1)
+    hp = P(*[p._h.value for p in plans])
+    hx = P(*[ptr_of(x) for x in xs])
+    hi = P(*[ptr_of(i) for i in idx])
+    hv = P(*[ptr_of(v) for v in val])
+    check(load().sfft_execute_batch(n, ctypes.cast(hp, ctypes.c_void_p),
+                                    ctypes.cast(hx, ctypes.c_void_p),
+                                    ctypes.cast(hi, ctypes.c_void_p),
+                                    ctypes.cast(hv, ctypes.c_void_p), ptr_of(infos),
+                                    stream_handle(stream)), "sfft_execute_batch")
+    return out
+
+
+class Server:
+    """Continuous-batching request loop of libsfft (sfft_server_*)."""
+
+    def __init__(self, hbm_budget: int = 8 << 30, max_slots: int = 64):
+        h = ctypes.c_void_p()
+        check(load().sfft_server_create(ctypes.byref(h), hbm_budget, max_slots),
+              "sfft_server_create")
+        self._h = h
+
+    def submit(self, plan: Plan, x, out) -> int:
+        idx, val, info = out
+        t = ctypes.c_uint64()
+        check(load().sfft_submit(self._h, plan._h, ptr_of(x), ptr_of(idx), ptr_of(val),
+                                 ptr_of(info), ctypes.byref(t)), "sfft_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """(status, latency_us): status SFFT_PENDING (1) or SFFT_OK (0)."""
+        s = ctypes.c_int32()
+        lat = ctypes.c_double()
+        check(load().sfft_poll(self._h, ticket, ctypes.byref(s), ctypes.byref(lat)), "sfft_poll")
+        return s.value, lat.value
+
+    def drain(self):
+        check(load().sfft_server_drain(self._h), "sfft_server_drain")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().sfft_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,305 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 CPU oracle, on the same
+seeded inputs.  Bins: relative L2 per (stage, delay) <= 1e-12 (FP64) / 1e-5 (FP32).
+Recovery: support bit-exact, values relative L2 <= 1e-12 / 1e-5 against the oracle."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def sfft():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2011_05749_gb300 as m
+    m.load()
+    return m
+
+
+def to_dev(x, dtype):
+    return torch.from_numpy(np.ascontiguousarray(x.astype(dtype))).to("cuda")
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def split_bins(Y, N, f, R):
+    out, off = [], 0
+    for L in f:
+        B = N // L
+        for _ in range(R):
+            out.append(Y[off:off + B])
+            off += B
+    return out
+
+
+def oracle_opts(oracle_mod, plan_kw, p):
+    prec = plan_kw.get("precision", "fp32")
+    return oracle_mod.OracleOpts(noise_var=plan_kw.get("noise_var", 0.0),
+                                 eta=1e-6 if prec == "fp64" else 3e-3,
+                                 locate=0 if plan_kw.get("locate", "ml") == "arg" else 1)
+
+
+def run_plan(sfft, p, **kw):
+    dtype = kw.pop("dtype", "c64")
+    plan = sfft.Plan(p.N, p.K, p.f, p.delays, dtype=dtype, **kw)
+    x = to_dev(p.x, np.complex64 if dtype == "c64" else np.complex128)
+    idx, val, info = plan.execute(x)
+    torch.cuda.synchronize()
+    info = info.cpu().numpy().copy()
+    n = int(info[0])
+    return plan, idx[:n].cpu().numpy(), val[:n].cpu().numpy(), info
+
+
+def assert_matches_oracle(idx, val, info, ref, prec):
+    assert info[1] >= 0, info
+    np.testing.assert_array_equal(idx, ref["idx"])
+    assert rel_l2(val, ref["val"]) <= TOL[prec], rel_l2(val, ref["val"])
+    assert info[2] == ref["rounds"], (info, ref["rounds"])
+    assert info[3] == ref["idents"], (info, ref["idents"])
+    assert (info[1] == 2) == (ref["status"] == 1)
+
+
+# ---------------------------------------------------------------------- bucketization
+BUCKET_CASES = [
+    # N, f, R, delays, precision, dtype
+    (20, (5, 4), 3, "ffast", "fp64", "c128"),
+    (60, (3, 4, 5), 4, "random", "fp32", "c64"),
+    (9660, (20, 21, 23), 3, "ffast", "fp64", "c128"),
+    (9660, (20, 21, 23), 6, "random", "fp32", "c64"),
+    (124950, (49, 50, 51), 6, "random", "fp32", "c64"),
+    (124950, (49, 50, 51), 4, "random", "fp64", "c128"),
+    (96, (1,), 2, "random", "fp32", "c64"),          # one stage, B = N: the full DFT
+    (2097024, (127, 128, 129), 2, "random", "fp64", "c128"),  # FP64: two-pass DFTs
+]
+
+
+@pytest.mark.parametrize("case", BUCKET_CASES, ids=lambda c: f"N{c[0]}-R{c[2]}-{c[4]}")
+def test_bucketize_matches_oracle(sfft, oracle_mod, case):
+    N, f, R, dl, prec, dtype = case
+    rng = np.random.default_rng(N + R)
+    # a dense random signal exercises every bin (not only a sparse support)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    delays = (np.tile(np.arange(R), (len(f), 1)) if dl == "ffast"
+              else synth.draw_delays(N, len(f), R, rng))
+    plan = sfft.Plan(N, 4, f, delays, dtype=dtype, precision=prec)
+    xd = x.astype(np.complex64 if dtype == "c64" else np.complex128)
+    bins = plan.bucketize(to_dev(xd, xd.dtype)).cpu().numpy()
+    Y = oracle_mod.bucketize(N, f, delays, xd.astype(np.complex128))
+    for g, r in zip(split_bins(bins, N, f, R), split_bins(Y, N, f, R)):
+        assert rel_l2(g, r) <= TOL[prec], rel_l2(g, r)
+
+
+@pytest.mark.parametrize("N,f", [(16776960, (255, 256, 257)), (134217216, (511, 512, 513))])
+def test_bucketize_large_sampled(sfft, oracle_mod, N, f):
+    """Two-pass stages (B up to 262656, factors 257 / 2^9 * 3^3 * 19): sampled bins against
+    the oracle's one-bin dot product."""
+    rng = np.random.default_rng(7)
+    x = (rng.standard_normal(N, dtype=np.float32)
+         + 1j * rng.standard_normal(N, dtype=np.float32)).astype(np.complex64)
+    delays = synth.draw_delays(N, 3, 3, rng)
+    plan = sfft.Plan(N, 4, f, delays, precision="fp32")
+    bins = plan.bucketize(to_dev(x, np.complex64)).cpu().numpy()
+    xr = x.astype(np.complex128)
+    off = 0
+    for d, L in enumerate(f):
+        B = N // L
+        for r in range(3):
+            for j in list(rng.integers(0, B, 3)) + [0, B - 1]:
+                ref = oracle_mod.bin_value(N, L, int(delays[d, r]), int(j), xr)
+                scale = np.sqrt(B) * np.sqrt(2.0)  # rms of a bin of unit-variance noise
+                assert abs(bins[off + j] - ref) <= 1e-5 * scale * 10, (d, r, j)
+            off += B
+    plan.close()
+
+
+# ---------------------------------------------------------------------- decoding
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_decode_on_oracle_bins(sfft, oracle_mod, prec):
+    """The decoder alone, fed the oracle's bins (natural order)."""
+    p = synth.make_problem(124950, (49, 50, 51), 80, seed=31, R=6, delays="random",
+                           mag=(1.0, 10.0), snr_db=25.0)
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x)
+    kw = dict(precision=prec, locate="ml", noise_var=p.noise_var)
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    plan = sfft.Plan(p.N, p.K, p.f, p.delays, dtype="c64" if prec == "fp32" else "c128", **kw)
+    bins = to_dev(Y, np.complex64 if prec == "fp32" else np.complex128)
+    idx, val, info = plan.decode_bins(bins)
+    torch.cuda.synchronize()
+    info = info.cpu().numpy()
+    n = int(info[0])
+    assert_matches_oracle(idx[:n].cpu().numpy(), val[:n].cpu().numpy(), info, ref, prec)
+
+
+def test_paper_worked_example_n20(sfft, oracle_mod):
+    """Sec. 3.2 example (N = 20, K = 5, B = 4, 5): 9 + 3 + 1 identifications, 3 rounds."""
+    rng = np.random.default_rng(20)
+    vals = np.exp(1j * rng.uniform(0, 2 * np.pi, 5))
+    p = synth.make_problem(20, (5, 4), 0, seed=0, R=3, delays="ffast",
+                           support=[1, 3, 5, 10, 13], values=vals)
+    plan, idx, val, info = run_plan(sfft, p, dtype="c128", precision="fp64", locate="arg")
+    assert list(idx) == [1, 3, 5, 10, 13]
+    assert info[2] == 3 and info[3] == 13 and info[1] == 0
+    np.testing.assert_allclose(val, vals, atol=1e-12)
+
+
+EXEC_CASES = [
+    ("ffast_exact_9660", dict(dtype="c128", precision="fp64", locate="arg")),
+    ("ffast_exact_9660", dict(dtype="c64", precision="fp32", locate="arg")),
+    ("ffast_exact_9660", dict(dtype="c128", precision="fp64", locate="ml")),
+]
+
+
+@pytest.mark.parametrize("name,kw", EXEC_CASES, ids=lambda v: str(v))
+def test_execute_ffast_exact(sfft, oracle_mod, name, kw):
+    p = synth.config_problem(name, seed=1)
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x)
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    np.testing.assert_array_equal(ref["idx"], p.support)
+    plan, idx, val, info = run_plan(sfft, p, **kw)
+    assert_matches_oracle(idx, val, info, ref, kw["precision"])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("snr", [None, 20.0])
+def test_execute_rffast_124950(sfft, oracle_mod, prec, snr):
+    p = synth.make_problem(124950, (49, 50, 51), 100, seed=44, R=6, delays="random",
+                           mag=(1.0, 10.0), snr_db=snr)
+    kw = dict(precision=prec, locate="ml", noise_var=p.noise_var,
+              dtype="c64" if prec == "fp32" else "c128")
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays,
+                             p.x.astype(np.complex64).astype(np.complex128)
+                             if prec == "fp32" else p.x)
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    plan, idx, val, info = run_plan(sfft, p, **kw)
+    assert_matches_oracle(idx, val, info, ref, prec)
+
+
+def test_execute_rffast_full_size_2097024(sfft, oracle_mod):
+    """The benchmark workload (N = 127*128*129, R = 8, K = 1000, U[1,10], 20 dB) on the
+    FP32 path, against a full oracle decode of the same complex64 input."""
+    p = synth.config_problem("rffast_2097024", seed=2)
+    x64 = p.x.astype(np.complex64)
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, x64.astype(np.complex128))
+    kw = dict(precision="fp32", locate="ml", noise_var=p.noise_var)
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    plan = sfft.Plan(p.N, p.K, p.f, p.delays, **kw)
+    idx, val, info = plan.execute(to_dev(x64, np.complex64))
+    torch.cuda.synchronize()
+    info = info.cpu().numpy()
+    n = int(info[0])
+    assert_matches_oracle(idx[:n].cpu().numpy(), val[:n].cpu().numpy(), info, ref, "fp32")
+    np.testing.assert_array_equal(idx[:n].cpu().numpy(), p.support)
+
+
+# ---------------------------------------------------------------------- edge cases
+def test_zero_signal(sfft):
+    p = synth.make_problem(9660, (20, 21, 23), 0, seed=0, R=3, support=[], values=[])
+    p.K = 5
+    plan, idx, val, info = run_plan(sfft, p, precision="fp32", locate="arg")
+    assert info[0] == 0 and info[1] == 0 and info[2] == 1 and info[3] == 483 + 460 + 420
+
+
+def test_truncation_to_k_largest(sfft, oracle_mod):
+    rng = np.random.default_rng(30)
+    support = np.sort(rng.choice(9660, 12, replace=False))
+    mags = np.arange(1, 13, dtype=float)
+    rng.shuffle(mags)
+    vals = mags * np.exp(1j * rng.uniform(0, 2 * np.pi, 12))
+    p = synth.make_problem(9660, (20, 21, 23), 0, seed=0, R=3, support=support, values=vals)
+    p.K = 5
+    plan, idx, val, info = run_plan(sfft, p, dtype="c128", precision="fp64", locate="arg")
+    keep = np.sort(support[np.argsort(-mags)[:5]])
+    np.testing.assert_array_equal(idx, keep)
+    assert info[0] == 5
+
+
+def test_host_buffers_match_device(sfft):
+    p = synth.make_problem(124950, (49, 50, 51), 50, seed=8, R=6, delays="random",
+                           mag=(1.0, 10.0))
+    plan = sfft.Plan(p.N, p.K, p.f, p.delays, precision="fp32")
+    xd = p.x.astype(np.complex64)
+    hi, hv, hf = plan.execute(xd)  # numpy host arrays in and out
+    di, dv, df = plan.execute(to_dev(xd, np.complex64))
+    torch.cuda.synchronize()
+    n = int(hf[0])
+    assert n == int(df[0].item()) == p.K
+    np.testing.assert_array_equal(hi[:n], di[:n].cpu().numpy())
+    assert rel_l2(hv[:n], dv[:n].cpu().numpy()) <= 1e-6
+
+
+def test_batch_matches_single(sfft):
+    probs = [synth.make_problem(124950, (49, 50, 51), 40 + 7 * i, seed=100 + i, R=6,
+                                delays=np.array([[0, 1, 7, 99, 1234, 50000]] * 3),
+                                mag=(1.0, 10.0), snr_db=30.0) for i in range(5)]
+    nv = probs[0].noise_var
+    plan = sfft.Plan(124950, 80, (49, 50, 51), probs[0].delays, precision="fp32",
+                     noise_var=nv, max_batch=4)
+    xs = torch.stack([to_dev(p.x, np.complex64) for p in probs])
+    idx, val, infos = plan.execute_many(xs)
+    torch.cuda.synchronize()
+    one = sfft.Plan(124950, 80, (49, 50, 51), probs[0].delays, precision="fp32", noise_var=nv)
+    for i in range(5):
+        i1, v1, f1 = one.execute(xs[i])
+        torch.cuda.synchronize()
+        n = int(f1[0])
+        assert int(infos[i, 0]) == n
+        np.testing.assert_array_equal(idx[i, :n].cpu().numpy(), i1[:n].cpu().numpy())
+        assert rel_l2(val[i, :n].cpu().numpy(), v1[:n].cpu().numpy()) <= 1e-6
+
+
+def test_mixed_plan_batch(sfft):
+    a = synth.make_problem(9660, (20, 21, 23), 30, seed=1, R=3)
+    b = synth.make_problem(124950, (49, 50, 51), 60, seed=2, R=6, delays="random",
+                           mag=(1.0, 10.0))
+    pa = sfft.Plan(a.N, a.K, a.f, a.delays, precision="fp32", locate="arg", max_batch=2)
+    pb = sfft.Plan(b.N, b.K, b.f, b.delays, precision="fp32", locate="ml", max_batch=2)
+    xs = [to_dev(a.x, np.complex64), to_dev(b.x, np.complex64), to_dev(a.x, np.complex64)]
+    plans = [pa, pb, pa]
+    outs = [p.empty_outputs() for p in plans]
+    infos = torch.zeros((3, 4), dtype=torch.int32, device="cuda")
+    sfft.execute_batch(plans, xs, ([o[0] for o in outs], [o[1] for o in outs], infos))
+    torch.cuda.synchronize()
+    for i, (p, prob) in enumerate(zip(plans, [a, b, a])):
+        n = int(infos[i, 0])
+        np.testing.assert_array_equal(outs[i][0][:n].cpu().numpy(), prob.support)
+
+
+def test_invalid_plans_rejected(sfft):
+    with pytest.raises(sfft.SfftError):
+        sfft.Plan(9660, 10, (20, 22, 23), np.zeros((3, 3)))      # 22 does not divide / co-prime
+    with pytest.raises(sfft.SfftError):
+        sfft.Plan(9660, 10, (20, 21, 23), np.array([[0, 0, 1]] * 3))  # repeated delay
+    with pytest.raises(sfft.SfftError):
+        sfft.Plan(9660, 10, (20, 21, 23), np.array([[0, 5, 7]] * 3), locate="arg")  # no tau=1
+
+
+def test_server_matches_direct(sfft):
+    probs = [synth.make_problem(124950, (49, 50, 51), 30 + i, seed=200 + i, R=6,
+                                delays=np.array([[0, 1, 3, 77, 901, 60000]] * 3),
+                                mag=(1.0, 10.0)) for i in range(6)]
+    plan = sfft.Plan(124950, 64, (49, 50, 51), probs[0].delays, precision="fp32")
+    srv = sfft.Server(hbm_budget=4 << 30, max_slots=4)
+    xs = [to_dev(p.x, np.complex64) for p in probs]
+    outs = [plan.empty_outputs() for _ in probs]
+    tickets = [srv.submit(plan, x, o) for x, o in zip(xs, outs)]
+    srv.drain()
+    for t in tickets:
+        st, lat = srv.poll(t)
+        assert st == 0 and lat > 0
+    torch.cuda.synchronize()
+    for p, x, o in zip(probs, xs, outs):
+        i1, v1, f1 = plan.execute(x)
+        torch.cuda.synchronize()
+        n = int(f1[0])
+        assert int(o[2][0]) == n == p.K
+        np.testing.assert_array_equal(o[0][:n].cpu().numpy(), i1[:n].cpu().numpy())
+        assert rel_l2(o[1][:n].cpu().numpy(), v1[:n].cpu().numpy()) <= 1e-6
+    srv.close()
