@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 sparse FFT (R-FFAST peeling) on its headline workload.
+
+Workload (one step): a batch of S synthetic signals shaped like the paper's general sparse
+experiments (Sec. 5.1): N = 127*128*129 = 2,097,024 complex64 samples, three stages with
+B_d = 16512, 16383, 16256, eight delays per stage (0, 1 and six uniform draws), K = 1000
+coefficients with |xhat| ~ U[1, 10] and uniform phase, complex white Gaussian noise at
+20 dB SNR.  Every step recovers all S signals through the library's batched path (gather
++ prime-factor DFTs, peeling decode, compaction).  The S inputs (1.07 GB at S = 64) are
+resident in HBM and larger than L2, so no L2 flush is needed between steps.
+
+Printed: one JSON line (rank 0) with signals/s, per-signal latency (p50/p99), accuracy
+against the plain FP64 path, the plain FP64 path's own signals/s, the dominant kernel's
+roofline, the CPU oracle's rate on the host cores, an end-to-end number through host
+buffers, and the SM clocks seen during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch S] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "rffast_2097024"
+CFG = synth.CONFIGS[WORKLOAD]
+METRIC = ("signals/s and p50/p99 latency at stated L2 error vs plain FP64 path; "
+          "gather % HBM")
+N_DISTINCT = 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=64, help="signals per step per GPU")
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--timed-only", action="store_true",
+                    help="run only the timed batched loop (for profiler captures)")
+    return ap.parse_args()
+
+
+def expected_noise_var():
+    lo, hi = CFG["mag"]
+    e_mag2 = (hi ** 3 - lo ** 3) / (3.0 * (hi - lo))  # E|xhat|^2 for |xhat| ~ U[lo, hi]
+    return CFG["K"] * e_mag2 / 10.0 ** (CFG["snr_db"] / 10.0)
+
+
+def plan_delays(seed):
+    rng = np.random.default_rng(10_000 + seed)
+    return synth.draw_delays(CFG["N"], len(CFG["f"]), CFG["R"], rng)
+
+
+def problems(seed, delays, n):
+    return [synth.make_problem(CFG["N"], CFG["f"], CFG["K"], seed * 1000 + i, R=CFG["R"],
+                               delays=delays, mag=CFG["mag"], snr_db=CFG["snr_db"])
+            for i in range(n)]
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), max=float(parts[2]),
+                                 util=float(parts[4]) if parts[4] not in ("", "[N/A]") else 0.0,
+                                 reasons=[n for n, v in zip(
+                                     ("hw_slowdown", "hw_thermal_slowdown",
+                                      "sw_thermal_slowdown", "sw_power_cap"), parts[5:9])
+                                     if v.lower() == "active"]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        busy = [r for r in rows if r["util"] > 0] or rows
+        reasons = sorted({x for r in busy for x in r["reasons"]})
+        return {"sm_mhz": statistics.median(r["sm"] for r in busy),
+                "sm_max_mhz": max(r["max"] for r in rows), "reasons": reasons,
+                "samples": len(busy)}
+
+
+# ------------------------------------------------------------------------------ oracle arm
+def oracle_rate(seed, budget_s, max_signals=64):
+    """Time the FP64 CPU oracle (naive bucketization + peeling decode), as it stands, on
+    up to max_signals workload signals until budget_s of wall time is used."""
+    import oracle
+    oracle.build_oracle()
+    delays = plan_delays(seed)
+    nv = expected_noise_var()
+    opts = oracle.OracleOpts(noise_var=nv, eta=3e-3, locate=1)
+    done, t_work = 0, 0.0
+    for i in range(max_signals):
+        p = synth.make_problem(CFG["N"], CFG["f"], CFG["K"], 77_000 + seed * 100 + i,
+                               R=CFG["R"], delays=delays, mag=CFG["mag"], snr_db=CFG["snr_db"])
+        x = p.x.astype(np.complex64).astype(np.complex128)
+        t0 = time.perf_counter()
+        Y = oracle.bucketize(p.N, p.f, p.delays, x)
+        oracle.decode(p.N, p.f, p.delays, Y, p.K, opts)
+        t_work += time.perf_counter() - t0
+        done += 1
+        if t_work >= budget_s:
+            break
+    return done / t_work, done, t_work
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    import oracle
+    oracle.build_oracle()
+    delays = plan_delays(args.seed)
+    opts = oracle.OracleOpts(noise_var=expected_noise_var(), eta=3e-3, locate=1)
+    probs = problems(args.seed + 500, delays, min(args.steps + args.warmup, 4))
+    xs = [p.x.astype(np.complex64).astype(np.complex128) for p in probs]
+    for i in range(args.warmup):
+        p = probs[i % len(probs)]
+        oracle.decode(p.N, p.f, p.delays, oracle.bucketize(p.N, p.f, p.delays, xs[i % len(xs)]),
+                      p.K, opts)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        p = probs[i % len(probs)]
+        oracle.decode(p.N, p.f, p.delays, oracle.bucketize(p.N, p.f, p.delays, xs[i % len(xs)]),
+                      p.K, opts)
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "signals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: one signal per step through the FP64 CPU oracle "
+                               "(naive B-point DFTs + peeling decode)",
+                   "N": CFG["N"], "K": CFG["K"], "R": CFG["R"], "snr_db": CFG["snr_db"]},
+        "cpu_baseline": {"value": v, "unit": "signals/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} signals of the workload, one per step"},
+        "e2e": {"value": v, "unit": "signals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line, default=float), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def kernel_traffic(kernel: str, src_files, per_unit_key: str):
+    """Traffic per unit from the committed ncu summary, if the kernel source still
+    matches the hash recorded there; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for f in src_files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if rec.get("src_sha256") != h.hexdigest():
+        return None
+    return rec.get(per_unit_key)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2011_05749_gb300 as sfft
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    S = args.batch
+    N, K, R, f = CFG["N"], CFG["K"], CFG["R"], CFG["f"]
+    nv = expected_noise_var()
+    delays = plan_delays(args.seed)
+    probs = problems(args.seed + rank, delays, N_DISTINCT)
+    dev = torch.device("cuda", local)
+    distinct = [torch.from_numpy(p.x.astype(np.complex64)).to(dev) for p in probs]
+    xs = torch.empty((S, N), dtype=torch.complex64, device=dev)
+    for i in range(S):
+        xs[i].copy_(distinct[i % N_DISTINCT])
+    plan = sfft.Plan(N, K, f, delays, precision="fp32", locate="ml", noise_var=nv,
+                     max_batch=S)
+    out = plan.empty_outputs("cuda", S)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.execute_many(xs, out)
+    barrier()
+    plan.profile(reset=True)
+    plan.set_profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.execute_many(xs, out)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    plan.set_profiling(False)
+    prof = plan.profile(reset=True)
+    el_ms = ev0.elapsed_time(ev1)
+    el_ms = max_over_ranks(el_ms)
+    value = S * args.steps * world / (el_ms / 1e3)
+    infos = out[2].cpu().numpy()
+
+    # dominant kernel: gather + prime-factor DFTs (bucketization), one launch per step
+    bk = prof["bucketize"]
+    bk_ms = bk["ms"] / max(bk["calls"], 1)
+    esz = 8
+    alg_bytes_sig = R * plan.num_bins * esz * 2  # samples read + bins written (complex64)
+    achieved = S * alg_bytes_sig / (bk_ms / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    traffic_sig = kernel_traffic("bucketize_kernel<float,float>",
+                                 ["paper_2011_05749_gb300/csrc/dft.cu",
+                                  "paper_2011_05749_gb300/csrc/api.cu"],
+                                 "dram_bytes_per_signal")
+    launches = sum(v["launches"] for v in prof.values())
+
+    if args.timed_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "signals/s",
+                              "timed_only": True, "phases": prof}, default=float), flush=True)
+        return 0
+
+    # per-signal latency of one request (sfft_execute, one signal per call)
+    plan1 = sfft.Plan(N, K, f, delays, precision="fp32", locate="ml", noise_var=nv)
+    o1 = plan1.empty_outputs("cuda")
+    lat = []
+    for i in range(10):
+        plan1.execute(distinct[i % N_DISTINCT], o1)
+    torch.cuda.synchronize()
+    for i in range(200):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan1.execute(xs[(i * 7) % S], o1)
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b) * 1e3)
+    lat.sort()
+
+    # plain FP64 path: one signal per launch group, FP64 arithmetic throughout
+    plan64 = sfft.Plan(N, K, f, delays, precision="fp64", locate="ml", noise_var=nv)
+    o64 = [plan64.empty_outputs("cuda") for _ in range(N_DISTINCT)]
+    for i in range(2):
+        plan64.execute(distinct[i], o64[i])
+    torch.cuda.synchronize()
+    n64 = 16
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i in range(n64):
+        plan64.execute(distinct[i % N_DISTINCT], o64[i % N_DISTINCT])
+    b.record(stream)
+    torch.cuda.synchronize()
+    fp64_rate = n64 / (a.elapsed_time(b) / 1e3)
+
+    # accuracy of the batched FP32 results on the distinct signals
+    idx32 = out[0].cpu().numpy()
+    val32 = out[1].cpu().numpy()
+    l2_vs64, sup_eq, l0_truth, l2_truth = [], 0, 0, []
+    for i, p in enumerate(probs):
+        n = int(infos[i, 0])
+        i64, v64, f64 = (t.cpu().numpy() for t in o64[i])
+        m = int(f64[0])
+        same = n == m and np.array_equal(idx32[i, :n], i64[:m])
+        sup_eq += int(same)
+        if same:
+            l2_vs64.append(np.linalg.norm(val32[i, :n] - v64[:m]) / np.linalg.norm(v64[:m]))
+        l0_truth += len(set(idx32[i, :n].tolist()) ^ set(p.support.tolist()))
+        if n == p.K and np.array_equal(idx32[i, :n], p.support):
+            l2_truth.append(np.linalg.norm(val32[i, :n] - p.values) / np.linalg.norm(p.values))
+
+    # end to end through host buffers: H2D of every input, D2H of every output per step
+    e2e = None
+    try:
+        hx = [torch.empty(N, dtype=torch.complex64).pin_memory() for _ in range(S)]
+        for i in range(S):
+            hx[i].copy_(distinct[i % N_DISTINCT].cpu())
+        hidx = [torch.zeros(K, dtype=torch.int64).pin_memory() for _ in range(S)]
+        hval = [torch.zeros(K, dtype=torch.complex64).pin_memory() for _ in range(S)]
+        hinf = torch.zeros((S, 4), dtype=torch.int32).pin_memory()
+        sfft.execute_batch([plan] * S, hx, (hidx, hval, hinf))
+        e_steps = max(3, min(args.steps, 10))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            sfft.execute_batch([plan] * S, hx, (hidx, hval, hinf))
+        torch.cuda.synchronize()
+        e_el = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": S * e_steps * world / e_el, "unit": "signals/s",
+               "h2d_bytes_per_step": S * N * 8,
+               "d2h_bytes_per_step": S * (K * 8 + K * 8) + S * 16,
+               "path": "sfft_execute_batch with pinned host buffers (staged per launch group)"}
+        assert np.array_equal(hidx[0].numpy()[:int(hinf[0, 0])], idx32[0, :int(infos[0, 0])])
+    except Exception as exc:  # report, never fall back
+        e2e = {"value": None, "unit": "signals/s", "error": repr(exc)[:200],
+               "h2d_bytes_per_step": S * N * 8, "d2h_bytes_per_step": S * (K * 16 + 16)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, nsig, secs = oracle_rate(args.seed, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "signals/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{nsig} workload signals through the FP64 C oracle "
+                         f"(naive DFT bucketization + peeling), {secs:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: R-FFAST general sparse, N=127*128*129=2097024 "
+                               "complex64, B=(16512,16383,16256), 8 delays/stage (0,1,6 random), "
+                               "K=1000, |xhat|~U[1,10], SNR 20 dB; FP32 bulk, FP64 locate/fit",
+                   "global_batch": S * world, "signals_per_step_per_gpu": S,
+                   "distinct_signals": N_DISTINCT, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (S x 16.8 MB resident), no flush"},
+        "latency_us": {"p50": lat[len(lat) // 2], "p99": lat[int(len(lat) * 0.99) - 1],
+                       "path": "sfft_execute, one signal per call, device buffers"},
+        "accuracy": {"support_equal_fp64_plain": f"{sup_eq}/{len(probs)}",
+                     "rel_l2_vs_fp64_plain_max": max(l2_vs64) if l2_vs64 else None,
+                     "l0_vs_truth_total": l0_truth,
+                     "rel_l2_vs_truth_max": max(l2_truth) if l2_truth else None,
+                     "status_incomplete": int(np.sum(infos[:, 1] == 2)),
+                     "rounds_max": int(infos[:, 2].max())},
+        "fp64_plain": {"value": fp64_rate, "unit": "signals/s",
+                       "path": "FP64 arithmetic, one signal per sfft_execute"},
+        "speedup_vs_fp64_plain": value / world / fp64_rate,
+        "roofline": {"bound": "hbm", "kernel": "bucketize_kernel<float,float>",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_source": peak_src,
+                     "traffic": (traffic_sig * S if traffic_sig else None),
+                     "alg_bytes_per_launch": S * alg_bytes_sig,
+                     "avg_launch_ms": bk_ms},
+        "phases_ms_per_step": {k: v["ms"] / max(v["calls"], 1) for k, v in prof.items()},
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line, default=float), flush=True)
+    plan.close()
+    plan1.close()
+    plan64.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -123,8 +123,10 @@ int sfft_execute(sfft_plan_t plan, const void* x, int64_t* out_idx, void* out_va
 /* Recover n signals in one set of launches.  plans[i] (may repeat), xs[i], idx[i], val[i]
  * as in sfft_execute for signal i; infos: int32[4 * n], signal i at infos + 4 i.  The
  * host arrays of pointers are read during the call.  Signals that share a plan are
- * processed together, at most that plan's max_batch per launch group.  Device pointers
- * only.                                                                                   */
+ * processed together, at most that plan's max_batch per launch group.  The buffers are
+ * either all device memory (asynchronous) or all host memory (staged per launch group
+ * through device memory the plan owns; the call returns when the outputs are written).
+ * Mixing the two is SFFT_EINVAL.                                                          */
 int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const void* const* xs,
                        int64_t* const* idx, void* const* val, int32_t* infos, void* stream);
 
@@ -137,6 +139,13 @@ int sfft_bucketize(sfft_plan_t plan, const void* x, void* bins, void* stream);
  * not modified).  Outputs as sfft_execute.  Device pointers only.                         */
 int sfft_decode_bins(sfft_plan_t plan, const void* bins, int64_t* out_idx, void* out_val,
                      int32_t* out_info, void* stream);
+
+/* Phase timing.  While enabled, every execute call brackets its bucketization, decode and
+ * compaction launches with CUDA events on the launch stream.  sfft_plan_profile waits for
+ * the recorded events and returns the accumulated milliseconds, kernel launches and calls
+ * per phase (ms[3], launches[3], calls[3]; any may be NULL), then clears them if reset.   */
+int sfft_plan_set_profiling(sfft_plan_t plan, int enable);
+int sfft_plan_profile(sfft_plan_t plan, double* ms, int64_t* launches, int64_t* calls, int reset);
 
 /* Serving: continuous batching of requests of any plans on one GPU.  A host thread
  * admits requests while their workspace fits hbm_budget bytes and fewer than max_slots

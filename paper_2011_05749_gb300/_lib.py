@@ -63,6 +63,8 @@ EXPORTS = {
     "sfft_execute_batch": (ctypes.c_int, [ctypes.c_int32] + [ctypes.c_void_p] * 6),
     "sfft_bucketize": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "sfft_decode_bins": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "sfft_plan_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "sfft_plan_profile": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int]),
     "sfft_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t,
                                           ctypes.c_int32]),
     "sfft_submit": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.POINTER(ctypes.c_uint64)]),

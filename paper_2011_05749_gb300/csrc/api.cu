@@ -194,13 +194,18 @@ static void free_plan_memory(sfft_plan_s* p)
 {
     void* dev[] = {p->d_nidx, p->d_pbin, p->d_bpos, p->d_tw, p->d_bins, p->d_scratch,
                    p->d_dec, p->d_ptrs, p->d_sortbuf, p->d_x_stage, p->d_out_stage,
-                   p->d_bins_in};
+                   p->d_bins_in, p->d_xb_stage, p->d_ob_stage};
     for (void* q : dev)
         if (q) cudaFree(q);
     for (int i = 0; i < 2; ++i) {
         if (p->h_ptrs[i]) cudaFreeHost(p->h_ptrs[i]);
         if (p->ptr_ev[i]) cudaEventDestroy(p->ptr_ev[i]);
     }
+    for (auto& e : p->prof_pending) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (auto e : p->prof_pool) cudaEventDestroy(e);
 }
 
 extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t n_stages,
@@ -495,6 +500,42 @@ extern "C" int64_t sfft_plan_num_bins(sfft_plan_t p) { return p ? p->pd.sumB : -
 
 namespace sfft {
 
+static cudaEvent_t prof_event(sfft_plan_s* p)
+{
+    if (!p->prof_pool.empty()) {
+        cudaEvent_t e = p->prof_pool.back();
+        p->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// bracket one phase (0 bucketize, 1 decode, 2 compact) with events on the launch stream
+struct PhaseScope {
+    sfft_plan_s* p;
+    cudaStream_t st;
+    int phase, launches;
+    cudaEvent_t a = nullptr;
+    PhaseScope(sfft_plan_s* p_, cudaStream_t st_, int phase_, int launches_)
+        : p(p_), st(st_), phase(phase_), launches(launches_)
+    {
+        if (p->prof) {
+            a = prof_event(p);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~PhaseScope()
+    {
+        if (p->prof && a) {
+            cudaEvent_t b = prof_event(p);
+            cudaEventRecord(b, st);
+            p->prof_pending.push_back({a, b, phase, launches});
+        }
+    }
+};
+
 // Enqueue the whole path for n signals of one plan (n <= max_batch).  xs/out pointer
 // tables are already on the device when n > 1 (d_tab != nullptr).
 int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
@@ -507,6 +548,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
         // caller-supplied natural-order bins (sfft_decode_bins): permute to storage order
         CK(launch_bins_to_natural(pd, p->d_pbin, bins_in, p->d_bins, p->prec, 0, st));
     } else {
+        PhaseScope ps(p, st, 0, p->need_pass2 ? 2 : 1);
         BucketArgs a;
         memset(&a, 0, sizeof(a));
         a.pd = pd;
@@ -546,7 +588,10 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
         G = std::max(G, 1);
     }
     da.G = G;
-    CK(launch_decode(da, p->prec, threads, G > 1, st));
+    {
+        PhaseScope ps(p, st, 1, 1);
+        CK(launch_decode(da, p->prec, threads, G > 1, st));
+    }
 
     CompactArgs ca;
     memset(&ca, 0, sizeof(ca));
@@ -562,7 +607,10 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     ca.infos = infos;
     ca.idx0 = idx0;
     ca.val0 = val0;
-    CK(launch_compact(ca, p->prec, p->xdouble, 1024, 2 * sizeof(uint64_t) * (size_t)p->smem_cap, st));
+    {
+        PhaseScope ps(p, st, 2, 1);
+        CK(launch_compact(ca, p->prec, p->xdouble, 1024, 2 * sizeof(uint64_t) * (size_t)p->smem_cap, st));
+    }
     return SFFT_OK;
 }
 
@@ -611,33 +659,58 @@ extern "C" int sfft_execute(sfft_plan_t p, const void* x, int64_t* out_idx, void
 }
 
 namespace sfft {
+// n signals of one plan, device buffers; host buffers when `host` (staged per chunk)
 int execute_group(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
-                  void* const* val, int32_t* infos, cudaStream_t st)
+                  void* const* val, int32_t* infos, cudaStream_t st, bool host = false)
 {
+    const size_t mb = (size_t)p->max_batch;
+    const size_t xb = (size_t)p->pd.N * p->xesz;
+    const size_t ib = align_up((size_t)p->pd.K * 8, 256), vb = align_up((size_t)p->pd.K * p->xesz, 256);
+    if (host) {
+        if (!p->d_xb_stage) CK(cudaMalloc(&p->d_xb_stage, xb * mb));
+        if (!p->d_ob_stage) CK(cudaMalloc(&p->d_ob_stage, (ib + vb) * mb + 16 * mb));
+    }
     for (int c0 = 0; c0 < n; c0 += p->max_batch) {
         const int m = std::min(p->max_batch, n - c0);
+        unsigned char* ob = (unsigned char*)p->d_ob_stage;
+        int32_t* dinf = host ? (int32_t*)(ob + (ib + vb) * mb) : infos + 4 * c0;
+        auto dx = [&](int i) -> const void* {
+            return host ? (const void*)((unsigned char*)p->d_xb_stage + xb * i) : xs[c0 + i];
+        };
+        auto di = [&](int i) -> int64_t* { return host ? (int64_t*)(ob + ib * i) : idx[c0 + i]; };
+        auto dv = [&](int i) -> void* { return host ? (void*)(ob + ib * mb + vb * i) : val[c0 + i]; };
+        if (host)
+            for (int i = 0; i < m; ++i)
+                CK(cudaMemcpyAsync((void*)dx(i), xs[c0 + i], xb, cudaMemcpyHostToDevice, st));
+        int rc;
         if (m == 1) {
-            int rc = run_chunk(p, 1, xs[c0], nullptr, idx[c0], val[c0], nullptr, nullptr,
-                               infos + 4 * c0, nullptr, st);
-            if (rc) return rc;
-            continue;
-        }
-        const int slot = p->ptr_slot;
-        p->ptr_slot ^= 1;
-        CK(cudaEventSynchronize(p->ptr_ev[slot]));
-        void** h = p->h_ptrs[slot];
-        const size_t mb = (size_t)p->max_batch;
-        for (int i = 0; i < m; ++i) {
-            h[i] = (void*)xs[c0 + i];
-            h[mb + i] = (void*)idx[c0 + i];
-            h[2 * mb + i] = (void*)val[c0 + i];
-        }
-        CK(cudaMemcpyAsync(p->d_ptrs, h, 3 * sizeof(void*) * mb, cudaMemcpyHostToDevice, st));
-        CK(cudaEventRecord(p->ptr_ev[slot], st));
-        int rc = run_chunk(p, m, nullptr, (const void* const*)p->d_ptrs, nullptr, nullptr,
+            rc = run_chunk(p, 1, dx(0), nullptr, di(0), dv(0), nullptr, nullptr, dinf, nullptr, st);
+        } else {
+            const int slot = p->ptr_slot;
+            p->ptr_slot ^= 1;
+            CK(cudaEventSynchronize(p->ptr_ev[slot]));
+            void** h = p->h_ptrs[slot];
+            for (int i = 0; i < m; ++i) {
+                h[i] = (void*)dx(i);
+                h[mb + i] = (void*)di(i);
+                h[2 * mb + i] = dv(i);
+            }
+            CK(cudaMemcpyAsync(p->d_ptrs, h, 3 * sizeof(void*) * mb, cudaMemcpyHostToDevice, st));
+            CK(cudaEventRecord(p->ptr_ev[slot], st));
+            rc = run_chunk(p, m, nullptr, (const void* const*)p->d_ptrs, nullptr, nullptr,
                            (int64_t* const*)(p->d_ptrs + mb), (void* const*)(p->d_ptrs + 2 * mb),
-                           infos + 4 * c0, nullptr, st);
+                           dinf, nullptr, st);
+        }
         if (rc) return rc;
+        if (host) {
+            for (int i = 0; i < m; ++i) {
+                CK(cudaMemcpyAsync(idx[c0 + i], di(i), (size_t)p->pd.K * 8, cudaMemcpyDeviceToHost, st));
+                CK(cudaMemcpyAsync(val[c0 + i], dv(i), (size_t)p->pd.K * p->xesz, cudaMemcpyDeviceToHost, st));
+            }
+            CK(cudaMemcpyAsync(infos + 4 * c0, dinf, 16 * (size_t)m, cudaMemcpyDeviceToHost, st));
+            // the staging buffers are reused by the next chunk: finish this one first
+            CK(cudaStreamSynchronize(st));
+        }
     }
     return SFFT_OK;
 }
@@ -648,8 +721,15 @@ extern "C" int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const voi
                                   void* stream)
 {
     if (n < 0 || (n > 0 && (!plans || !xs || !idx || !val || !infos))) return SFFT_EINVAL;
+    if (n == 0) return SFFT_OK;
     for (int i = 0; i < n; ++i)
         if (!plans[i] || !xs[i] || !idx[i] || !val[i]) return SFFT_EINVAL;
+    // all buffers on the device, or all in host memory (staged through the plans)
+    const bool host = is_host_ptr(xs[0]);
+    for (int i = 0; i < n; ++i)
+        if (is_host_ptr(xs[i]) != host || is_host_ptr(idx[i]) != host || is_host_ptr(val[i]) != host)
+            return SFFT_EINVAL;
+    if (is_host_ptr(infos) != host) return SFFT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     // group signals by plan, keep first-seen order of plans
     std::vector<char> done(n, 0);
@@ -668,20 +748,55 @@ extern "C" int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const voi
                 gv.push_back(val[k]);
                 who.push_back(k);
             }
-        // contiguous info rows for the group are only possible when the group is a run;
-        // otherwise decode into a scratch info array and scatter
+        // info rows are written contiguously: a group that is a run of consecutive signals
+        // goes as one; otherwise signal by signal
         bool run = true;
         for (size_t q = 0; q < who.size(); ++q)
             if (who[q] != who[0] + (int)q) run = false;
         if (run) {
             int rc = execute_group(p, (int)who.size(), gx.data(), gi.data(), gv.data(),
-                                   infos + 4 * who[0], st);
+                                   infos + 4 * who[0], st, host);
             if (rc) return rc;
         } else {
             for (size_t q = 0; q < who.size(); ++q) {
-                int rc = execute_group(p, 1, &gx[q], &gi[q], &gv[q], infos + 4 * who[q], st);
+                int rc = execute_group(p, 1, &gx[q], &gi[q], &gv[q], infos + 4 * who[q], st, host);
                 if (rc) return rc;
             }
+        }
+    }
+    return SFFT_OK;
+}
+
+extern "C" int sfft_plan_set_profiling(sfft_plan_t p, int enable)
+{
+    if (!p) return SFFT_EINVAL;
+    p->prof = enable != 0;
+    return SFFT_OK;
+}
+
+extern "C" int sfft_plan_profile(sfft_plan_t p, double* ms, int64_t* launches, int64_t* calls,
+                                 int reset)
+{
+    if (!p) return SFFT_EINVAL;
+    for (auto& e : p->prof_pending) {
+        CK(cudaEventSynchronize(e.b));
+        float t = 0;
+        CK(cudaEventElapsedTime(&t, e.a, e.b));
+        p->prof_ms[e.phase] += t;
+        p->prof_launches[e.phase] += e.launches;
+        p->prof_calls[e.phase] += 1;
+        p->prof_pool.push_back(e.a);
+        p->prof_pool.push_back(e.b);
+    }
+    p->prof_pending.clear();
+    for (int i = 0; i < 3; ++i) {
+        if (ms) ms[i] = p->prof_ms[i];
+        if (launches) launches[i] = p->prof_launches[i];
+        if (calls) calls[i] = p->prof_calls[i];
+        if (reset) {
+            p->prof_ms[i] = 0;
+            p->prof_launches[i] = 0;
+            p->prof_calls[i] = 0;
         }
     }
     return SFFT_OK;

@@ -27,7 +27,7 @@
 
 namespace sfft {
 int execute_group(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
-                  void* const* val, int32_t* infos, cudaStream_t st);
+                  void* const* val, int32_t* infos, cudaStream_t st, bool host);
 }
 
 namespace {
@@ -213,7 +213,7 @@ void scheduler_loop(sfft_server_s* s)
                 vs.push_back(r.val);
             }
             int rc = sfft::execute_group(w->plan, (int)grp.size(), xs.data(), ix.data(), vs.data(),
-                                         w->d_infos, st);
+                                         w->d_infos, st, false);
             for (size_t i = 0; i < grp.size() && rc == SFFT_OK; ++i)
                 if (cudaMemcpyAsync(grp[i].info, w->d_infos + 4 * i, 16, cudaMemcpyDeviceToDevice,
                                     st) != cudaSuccess)

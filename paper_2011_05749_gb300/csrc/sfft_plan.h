@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "sfft_internal.cuh"
 
 struct sfft_plan_s {
@@ -43,5 +45,19 @@ struct sfft_plan_s {
     void* d_x_stage = nullptr;
     void* d_out_stage = nullptr;
     void* d_bins_in = nullptr;
+    void* d_xb_stage = nullptr;   // host-buffer batches: max_batch inputs
+    void* d_ob_stage = nullptr;   //                      max_batch outputs + infos
     size_t footprint = 0;  // device bytes owned by the plan
+    // phase timing (sfft_plan_set_profiling): CUDA events recorded on the launch stream
+    bool prof = false;
+    struct PhaseEv {
+        cudaEvent_t a, b;
+        int phase;
+        int launches;
+    };
+    std::vector<PhaseEv> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[3] = {0, 0, 0};
+    int64_t prof_launches[3] = {0, 0, 0};
+    int64_t prof_calls[3] = {0, 0, 0};
 };

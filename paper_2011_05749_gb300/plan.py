@@ -106,6 +106,18 @@ class Plan:
         execute_batch([self] * n, list(xs), out, stream)
         return out
 
+    def set_profiling(self, enable: bool = True):
+        check(load().sfft_plan_set_profiling(self._h, int(enable)), "sfft_plan_set_profiling")
+
+    def profile(self, reset: bool = True) -> dict:
+        """Accumulated CUDA-event time (ms), kernel launches and calls per phase."""
+        ms = (ctypes.c_double * 3)()
+        la = (ctypes.c_int64 * 3)()
+        ca = (ctypes.c_int64 * 3)()
+        check(load().sfft_plan_profile(self._h, ms, la, ca, int(reset)), "sfft_plan_profile")
+        return {ph: {"ms": ms[i], "launches": la[i], "calls": ca[i]}
+                for i, ph in enumerate(("bucketize", "decode", "compact"))}
+
     def bucketize(self, x, bins=None, stream=None):
         """Bins of Eq. 6 / Eq. 19 in natural order [stage][delay][j] (device only)."""
         torch = _torch()
