@@ -58,6 +58,7 @@ typedef struct sfft_server_s* sfft_server_t;
 #define SFFT_EADMIT (-5)     /* server: request can never fit the memory budget */
 #define SFFT_ENOTFOUND (-6)  /* server: unknown ticket */
 #define SFFT_EBUSY (-7)      /* server: queue full */
+#define SFFT_ETOOBIG (-8)    /* sfft_bucketize_static: problem exceeds its static scratch */
 
 /* element type of x and of the returned values */
 #define SFFT_C64 0
@@ -134,6 +135,23 @@ int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const void* const* x
  * bins[off_d + r * B_d + j] with off_d = n_delays * sum_{d'<d} B_d', as complex of the
  * plan's arithmetic (FP32 -> C64, FP64 -> C128).  Device pointers only.                  */
 int sfft_bucketize(sfft_plan_t plan, const void* x, void* bins, void* stream);
+
+/* Bucketization without any device allocation (no counterpart in the paper: this is a
+ * deployment variant of sfft_bucketize).  For callers that cannot call cudaMalloc -- an
+ * application whose own allocator already holds the GPU's memory, or a latency-critical
+ * loop where cudaMalloc/cudaFree would synchronise the device -- and so cannot create a
+ * plan.  The problem is described directly (arguments as sfft_plan_create; precision
+ * SFFT_PREC_*, dtype SFFT_C* of x); x (N samples) and bins (output, the layout and type of
+ * sfft_bucketize) are device pointers the caller owns.  Tables, twiddles and the scratch
+ * of two-pass stages live in one static 16 MiB device array inside the library, held by
+ * every GPU that loads it until the process exits; a problem needing more than fits
+ * (roughly sum_d B_d * (8 + 2 R * sizeof(complex)) bytes) returns SFFT_ETOOBIG before any
+ * device work.  The first call on each device resolves the array's device address (it
+ * should come before any stream capture).  All calls share the array and leave their data
+ * in it: calls that overlap on the GPU race, so the caller must order them.              */
+int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t* f, int32_t n_delays,
+                          const int64_t* delays, int32_t precision, int32_t dtype,
+                          const void* x, void* bins, void* stream);
 
 /* Peeling decoder only, on caller-supplied bins in the layout of sfft_bucketize (read,
  * not modified).  Outputs as sfft_execute.  Device pointers only.                         */

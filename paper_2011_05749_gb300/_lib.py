@@ -24,6 +24,7 @@ SFFT_ETIMEDOUT = -4
 SFFT_EADMIT = -5
 SFFT_ENOTFOUND = -6
 SFFT_EBUSY = -7
+SFFT_ETOOBIG = -8
 
 C64, C128 = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
@@ -72,6 +73,10 @@ EXPORTS = {
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     "sfft_server_drain": (ctypes.c_int, [ctypes.c_void_p]),
     "sfft_server_destroy": (None, [ctypes.c_void_p]),
+    "sfft_bucketize_static": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
     "sfft_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sfft_last_cuda_error": (ctypes.c_char_p, []),
 }

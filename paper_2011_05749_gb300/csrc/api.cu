@@ -851,6 +851,7 @@ extern "C" const char* sfft_error_string(int code)
         case SFFT_EADMIT: return "request exceeds the server memory budget";
         case SFFT_ENOTFOUND: return "unknown ticket";
         case SFFT_EBUSY: return "server queue full";
+        case SFFT_ETOOBIG: return "problem larger than the static scratch of sfft_bucketize_static";
         default: return "unknown code";
     }
 }

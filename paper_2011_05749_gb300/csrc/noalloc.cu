@@ -1,0 +1,378 @@
+// noalloc.cu -- sfft_bucketize_static: the bucketization (gather + prime-factor DFTs)
+// without any device allocation.
+//
+// Who needs it: code that cannot call cudaMalloc -- a host application or framework whose
+// own allocator has already reserved the GPU's memory (a further cudaMalloc fails or is
+// not allowed), or a latency-critical loop where cudaMalloc/cudaFree would synchronise the
+// device and stall other streams.  Such callers cannot create a plan (plans own device
+// tables and workspace), so this entry point takes the problem description directly.
+//
+// Memory: the index maps, twiddles, the inter-pass scratch of two-pass stages and the
+// storage-order bins all live in one file-scope __device__ array of kStaticBytes (16 MiB),
+// which every GPU that loads the library holds until the process exits.  Problems needing
+// more are rejected with SFFT_ETOOBIG.  Every call rewrites the parts it uses (nothing has
+// to start at zero); calls share the one array, so calls that overlap on the GPU (other
+// streams, other host threads) race and must be ordered by the caller.
+//
+// Device address: in host code the array's name is only a host-side stand-in, so the
+// first call on each device (with that device current) resolves the device address with
+// cudaGetSymbolAddress and caches it; that first call should come before any stream
+// capture.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "launch.h"
+#include "sfft.h"
+#include "sfft_internal.cuh"
+
+namespace sfft {
+cudaError_t set_bucketize_smem_limit(int max_smem);
+int cuda_fail(cudaError_t e);
+}  // namespace sfft
+
+using namespace sfft;
+
+namespace {
+
+constexpr size_t kStaticBytes = 16u << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_dev_ptr[kMaxDevices] = {};
+int g_max_smem[kMaxDevices] = {};
+
+int64_t gcd_i(int64_t a, int64_t b)
+{
+    while (b) {
+        const int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+int64_t inv_mod(int64_t a, int64_t m)
+{
+    if (m == 1) return 0;
+    int64_t g = m, x = 0, x1 = 1, b = a % m;
+    while (b) {
+        const int64_t q = g / b;
+        int64_t t = g - q * b;
+        g = b;
+        b = t;
+        t = x - q * x1;
+        x = x1;
+        x1 = t;
+    }
+    x %= m;
+    return x < 0 ? x + m : x;
+}
+
+// Prime-power factors of B, odd ones ascending, the power of two last; fixed arrays only.
+int prime_powers(int64_t B, int32_t* out, int cap)
+{
+    int n = 0, pw2 = 1;
+    while (B % 2 == 0) {
+        B /= 2;
+        pw2 *= 2;
+    }
+    for (int64_t p = 3; p * p <= B; p += 2) {
+        if (B % p) continue;
+        int64_t q = 1;
+        while (B % p == 0) {
+            B /= p;
+            q *= p;
+        }
+        if (n == cap) return -1;
+        out[n++] = (int32_t)q;
+    }
+    if (B > 1) {
+        if (n == cap) return -1;
+        out[n++] = (int32_t)B;
+    }
+    // ascending odd factors (insertion sort)
+    for (int i = 1; i < n; ++i)
+        for (int k = i; k > 0 && out[k - 1] > out[k]; --k) {
+            const int32_t t = out[k];
+            out[k] = out[k - 1];
+            out[k - 1] = t;
+        }
+    if (pw2 > 1) {
+        if (n == cap) return -1;
+        out[n++] = pw2;
+    }
+    if (n == 0) out[n++] = 1;
+    return n;
+}
+
+int ceil_log2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// Tables of one call, computed on the device from the description: input sample index and
+// bin of every storage position, and the twiddles of every axis.
+template <typename T>
+__global__ void static_tables_kernel(const __grid_constant__ PlanDesc pd, int32_t* nidx,
+                                     int32_t* pbin, typename C2<T>::t* tw, int32_t n_tw)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < pd.sumB) {
+        int d = 0;
+        while (d + 1 < pd.D && i >= pd.st[d + 1].bin_base) ++d;
+        const StageDesc& s = pd.st[d];
+        const int32_t pos = (int32_t)(i - s.bin_base);
+        int64_t n = 0, j = 0;
+        for (int a = 0; a < s.n_axes; ++a) {
+            const AxisDesc& A = s.ax[a];
+            const int32_t c = (pos / A.S) % A.P;
+            n += (int64_t)(A.pow2 ? bitrev(c, A.log2P) : c) * A.rur;
+            j += (int64_t)c * A.crt;
+        }
+        nidx[i] = (int32_t)(n % s.B);
+        pbin[i] = (int32_t)(j % s.B);
+    }
+    if (i < n_tw) {
+        // locate the axis owning twiddle slot i
+        for (int d = 0; d < pd.D; ++d)
+            for (int a = 0; a < pd.st[d].n_axes; ++a) {
+                const AxisDesc& A = pd.st[d].ax[a];
+                const int cnt = A.pow2 ? A.P / 2 : A.P;
+                if (i >= A.tw_off && i < A.tw_off + cnt) {
+                    double sv, cv;
+                    sincospi(2.0 * (double)(i - A.tw_off) / (double)A.P, &sv, &cv);
+                    tw[i] = typename C2<T>::t{(T)cv, (T)sv};
+                }
+            }
+    }
+}
+
+int device_scratch(void** ptr, int* max_smem)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= kMaxDevices) return SFFT_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_dev_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e);
+        int sm = 0;
+        e = cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = set_bucketize_smem_limit(sm);
+        if (e != cudaSuccess) return cuda_fail(e);
+        g_max_smem[dev] = sm;
+        g_dev_ptr[dev] = p;
+    }
+    *ptr = g_dev_ptr[dev];
+    *max_smem = g_max_smem[dev];
+    return SFFT_OK;
+}
+
+size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t* f,
+                                     int32_t n_delays, const int64_t* delays, int32_t precision,
+                                     int32_t dtype, const void* x, void* bins, void* stream)
+{
+    if (!f || !delays || !x || !bins) return SFFT_EINVAL;
+    if (N < 1 || N >= (1ll << 30) || n_stages < 1 || n_stages > kMaxStages || n_delays < 1 ||
+        n_delays > kMaxDelays)
+        return SFFT_EINVAL;
+    if ((precision != SFFT_PREC_FP32 && precision != SFFT_PREC_FP64) ||
+        (dtype != SFFT_C64 && dtype != SFFT_C128))
+        return SFFT_EINVAL;
+    for (int d = 0; d < n_stages; ++d) {
+        if (f[d] < 1 || N % f[d] != 0) return SFFT_EINVAL;
+        for (int e = 0; e < d; ++e)
+            if (gcd_i(f[d], f[e]) != 1) return SFFT_EINVAL;
+        for (int r = 0; r < n_delays; ++r) {
+            const int64_t t = delays[(int64_t)d * n_delays + r];
+            if (t < 0 || t >= N) return SFFT_EINVAL;
+            for (int q = 0; q < r; ++q)
+                if (delays[(int64_t)d * n_delays + q] == t) return SFFT_EINVAL;
+        }
+    }
+    const int prec = precision == SFFT_PREC_FP32 ? 1 : 0;
+    const size_t esz = prec ? 8 : 16;
+    int64_t sumB = 0;
+    for (int d = 0; d < n_stages; ++d) sumB += N / f[d];
+    // size check before any device work: tables, twiddles (<= 2 B per stage), two bin arrays
+    const size_t need = up256(4 * (size_t)sumB) * 2 + up256(esz * 2 * (size_t)sumB) +
+                        2 * up256(esz * (size_t)sumB * n_delays);
+    if (need > kStaticBytes) return SFFT_ETOOBIG;
+
+    void* base = nullptr;
+    int max_smem = 0;
+    int rc = device_scratch(&base, &max_smem);
+    if (rc) return rc;
+
+    BucketArgs a;
+    memset(&a, 0, sizeof(a));
+    PassDesc pass2[kMaxStages];
+    memset(pass2, 0, sizeof(pass2));
+    PlanDesc& pd = a.pd;
+    pd.N = (int32_t)N;
+    pd.D = n_stages;
+    pd.R = n_delays;
+    pd.K = 1;
+    const int64_t max_elems = ((int64_t)max_smem - 12 * 1024) / (int64_t)esz;
+    const int64_t tile_target = prec ? 4096 : 2048;
+    int32_t n_tw = 0, bin_base = 0;
+    size_t smem1 = 0, smem2 = 0;
+    int64_t tile1 = 0, tile2 = 0;
+    bool two = false;
+    for (int d = 0; d < n_stages; ++d) {
+        StageDesc& s = pd.st[d];
+        const int64_t L = f[d], B = N / L;
+        s.B = (int32_t)B;
+        s.L = (int32_t)L;
+        int32_t Ps[kMaxAxes];
+        const int n = prime_powers(B, Ps, kMaxAxes);
+        if (n < 0) return SFFT_EINVAL;
+        for (int i = 0; i < n; ++i)
+            if ((Ps[i] & (Ps[i] - 1)) != 0 && Ps[i] > 2049) return SFFT_EINVAL;
+        // split: one pass when B fits in shared memory, else the most balanced 2-group split
+        int split = n;
+        int32_t order[kMaxAxes];
+        for (int i = 0; i < n; ++i) order[i] = Ps[i];
+        if (B > max_elems) {
+            int64_t best = -1;
+            unsigned best_mask = 0;
+            for (unsigned mask = 1; mask + 1 < (1u << n); ++mask) {
+                int64_t pi = 1;
+                for (int i = 0; i < n; ++i)
+                    if (mask >> i & 1) pi *= Ps[i];
+                const int64_t po = B / pi;
+                if (pi > max_elems || po > max_elems) continue;
+                const int64_t worst = pi > po ? pi : po;
+                if (best < 0 || worst < best) {
+                    best = worst;
+                    best_mask = mask;
+                }
+            }
+            if (best < 0) return SFFT_EINVAL;
+            int k = 0;
+            for (int i = 0; i < n; ++i)
+                if (best_mask >> i & 1) order[k++] = Ps[i];
+            split = k;
+            for (int i = 0; i < n; ++i)
+                if (!(best_mask >> i & 1)) order[k++] = Ps[i];
+        }
+        s.n_axes = n;
+        s.split = split;
+        int32_t S = 1;
+        for (int i = 0; i < n; ++i) {
+            AxisDesc& A = s.ax[i];
+            A.P = order[i];
+            A.pow2 = (A.P > 1 && (A.P & (A.P - 1)) == 0) ? 1 : 0;
+            A.log2P = A.pow2 ? ceil_log2(A.P) : 0;
+            A.S = S;
+            S *= A.P;
+            const int64_t Bp = B / A.P;
+            A.rur = (int32_t)(Bp % B);
+            A.crt = (int32_t)((Bp * inv_mod(Bp % A.P, A.P)) % B);
+            A.tw_off = n_tw;
+            n_tw += A.pow2 ? A.P / 2 : A.P;
+        }
+        for (int r = 0; r < n_delays; ++r) s.tau[r] = (int32_t)delays[(int64_t)d * n_delays + r];
+        s.r0 = s.r1 = -1;
+        s.bin_base = bin_base;
+        s.y_off = bin_base * n_delays;
+        int64_t tw_all = 0, tw_in = 0, tw_out = 0;
+        for (int i = 0; i < n; ++i) {
+            const int64_t c = s.ax[i].pow2 ? s.ax[i].P / 2 : s.ax[i].P;
+            tw_all += c;
+            (i < split ? tw_in : tw_out) += c;
+        }
+        PassDesc& p1 = a.pass[d];
+        if (split == n) {
+            p1 = PassDesc{0, n, 1, 1, 1, (int32_t)B, 1, 1};
+            if ((size_t)(B + tw_all) * esz > smem1) smem1 = (size_t)(B + tw_all) * esz;
+            if (B > tile1) tile1 = B;
+        } else {
+            two = true;
+            int64_t inner = 1, outer = 1;
+            for (int i = 0; i < split; ++i) inner *= s.ax[i].P;
+            for (int i = split; i < n; ++i) outer *= s.ax[i].P;
+            int64_t Tb = tile_target / outer;
+            if (Tb < 1) Tb = 1;
+            if (Tb > inner) Tb = inner;
+            while (Tb > 1 && Tb * outer > max_elems) --Tb;
+            int64_t Ta = tile_target / inner;
+            if (Ta < 1) Ta = 1;
+            if (Ta > outer) Ta = outer;
+            while (Ta > 1 && Ta * inner > max_elems) --Ta;
+            p1 = PassDesc{split, n, (int32_t)Tb, 1, (int32_t)((inner + Tb - 1) / Tb),
+                          (int32_t)(Tb * outer), 1, 0};
+            pass2[d] = PassDesc{0, split, 1, (int32_t)Ta, (int32_t)((outer + Ta - 1) / Ta),
+                                (int32_t)(inner * Ta), 0, 1};
+            if ((size_t)(Tb * outer + tw_out) * esz > smem1) smem1 = (size_t)(Tb * outer + tw_out) * esz;
+            if ((size_t)(inner * Ta + tw_in) * esz > smem2) smem2 = (size_t)(inner * Ta + tw_in) * esz;
+            if (Tb * outer > tile1) tile1 = Tb * outer;
+            if (inner * Ta > tile2) tile2 = inner * Ta;
+        }
+        bin_base += (int32_t)B;
+    }
+    pd.sumB = bin_base;
+    pd.y_per_sig = (int64_t)bin_base * n_delays;
+
+    // carve the static array: nidx | pbin | twiddles | scratch | storage-order bins
+    unsigned char* p = (unsigned char*)base;
+    int32_t* nidx = (int32_t*)p;
+    p += up256(4 * (size_t)sumB);
+    int32_t* pbin = (int32_t*)p;
+    p += up256(4 * (size_t)sumB);
+    void* tw = p;
+    p += up256(esz * (size_t)n_tw);
+    void* scratch = p;
+    p += up256(esz * (size_t)pd.y_per_sig);
+    void* sbins = p;
+    p += up256(esz * (size_t)pd.y_per_sig);
+    if ((size_t)(p - (unsigned char*)base) > kStaticBytes) return SFFT_ETOOBIG;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nt = sumB > n_tw ? sumB : n_tw;
+    const unsigned grid = (unsigned)((nt + 255) / 256);
+    if (prec)
+        static_tables_kernel<float><<<grid, 256, 0, st>>>(pd, nidx, pbin, (float2*)tw, n_tw);
+    else
+        static_tables_kernel<double><<<grid, 256, 0, st>>>(pd, nidx, pbin, (double2*)tw, n_tw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+
+    a.n_sig = 1;
+    a.nidx = nidx;
+    a.tw = tw;
+    a.x0 = x;
+    a.scratch = scratch;
+    a.bins = sbins;
+    auto pick_threads = [](int64_t tile) {
+        int64_t t = (tile / 8 + 31) / 32 * 32;
+        return (int)(t < 128 ? 128 : (t > 512 ? 512 : t));
+    };
+    for (int pass = 0; pass < (two ? 2 : 1); ++pass) {
+        if (pass == 1)
+            for (int d = 0; d < kMaxStages; ++d) a.pass[d] = d < n_stages ? pass2[d] : PassDesc{};
+        a.tile_prefix[0] = 0;
+        for (int d = 0; d < kMaxStages; ++d)
+            a.tile_prefix[d + 1] = a.tile_prefix[d] + (d < n_stages ? a.pass[d].n_tiles * n_delays : 0);
+        a.tiles_per_sig = a.tile_prefix[kMaxStages];
+        e = launch_bucketize(a, prec, dtype == SFFT_C128 ? 1 : 0,
+                             pick_threads(pass == 0 ? tile1 : tile2), pass == 0 ? smem1 : smem2, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    e = launch_bins_to_natural(pd, pbin, sbins, bins, prec, 1, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return SFFT_OK;
+}

@@ -156,6 +156,25 @@ def execute_batch(plans, xs, out, stream=None):
     return out
 
 
+def bucketize_static(N: int, f, delays, x, bins, precision: str = "fp32",
+                     dtype: str = "c64", stream=None) -> int:
+    """sfft_bucketize_static: the bins of Eq. 6 / Eq. 19 (natural order, like
+    Plan.bucketize) for callers that cannot allocate device memory, so cannot hold a plan.
+    x and bins are caller-owned device tensors; the library's fixed 16 MiB device array
+    holds everything else.  Returns the C code (SFFT_ETOOBIG when the problem does not fit);
+    raises on other errors."""
+    f = np.ascontiguousarray(f, dtype=np.int64)
+    delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
+    rc = load().sfft_bucketize_static(
+        N, f.size, f.ctypes.data, delays.shape[1], delays.ctypes.data,
+        {"fp32": _lib.PREC_FP32, "fp64": _lib.PREC_FP64}[precision],
+        {"c64": _lib.C64, "c128": _lib.C128}[dtype], ptr_of(x), ptr_of(bins),
+        stream_handle(stream))
+    if rc != _lib.SFFT_ETOOBIG:
+        check(rc, "sfft_bucketize_static")
+    return rc
+
+
 class Server:
     """Continuous-batching request loop of libsfft (sfft_server_*)."""
 
