@@ -14,6 +14,7 @@
 #include "launch.h"
 #include "sfft.h"
 #include "sfft_internal.cuh"
+#include "pfa_layout.h"
 #include "sfft_plan.h"
 
 using namespace sfft;
@@ -46,25 +47,6 @@ static int64_t gcd64(int64_t a, int64_t b)
     return a;
 }
 
-static int64_t modinv(int64_t a, int64_t m)
-{
-    // extended Euclid; a and m co-prime
-    int64_t g = m, x = 0, x1 = 1, aa = a % m;
-    if (m == 1) return 0;
-    int64_t b = aa;
-    while (b) {
-        int64_t q = g / b, t = g - q * b;
-        g = b;
-        b = t;
-        t = x - q * x1;
-        x = x1;
-        x1 = t;
-    }
-    (void)g;
-    x %= m;
-    return x < 0 ? x + m : x;
-}
-
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct DevInfo {
@@ -91,83 +73,6 @@ static int device_info(DevInfo* out)
     }
     *out = cache[dev];
     return SFFT_OK;
-}
-
-// factor B into (prime, power) pairs
-static std::vector<std::pair<int64_t, int>> factorize(int64_t B)
-{
-    std::vector<std::pair<int64_t, int>> out;
-    for (int64_t p = 2; p * p <= B; ++p) {
-        int e = 0;
-        while (B % p == 0) {
-            B /= p;
-            ++e;
-        }
-        if (e) out.push_back({p, e});
-    }
-    if (B > 1) out.push_back({B, 1});
-    return out;
-}
-
-static int64_t prod_of(const std::vector<int>& Ps)
-{
-    int64_t v = 1;
-    for (int P : Ps) v *= P;
-    return v;
-}
-
-// Order the prime-power axes of one stage and pick the pass split.  Returns false if no
-// split keeps both groups within max_elems.
-static bool choose_axes(int64_t B, int64_t max_elems, std::vector<int>* axes, int* split)
-{
-    std::vector<int> odd, pw2;
-    for (auto& pe : factorize(B)) {
-        int64_t q = 1;
-        for (int i = 0; i < pe.second; ++i) q *= pe.first;
-        if (pe.first == 2)
-            pw2.push_back((int)q);
-        else
-            odd.push_back((int)q);
-    }
-    std::sort(odd.begin(), odd.end());
-    std::vector<int> all = odd;
-    for (int q : pw2) all.push_back(q);
-    if (all.empty()) all.push_back(1);
-    if (B <= max_elems) {
-        *axes = all;
-        *split = (int)all.size();
-        return true;
-    }
-    const int n = (int)all.size();
-    int64_t best = -1;
-    unsigned best_mask = 0;
-    for (unsigned mask = 1; mask + 1 < (1u << n); ++mask) {
-        int64_t pi = 1;
-        for (int i = 0; i < n; ++i)
-            if (mask >> i & 1) pi *= all[i];
-        const int64_t po = B / pi;
-        if (pi > max_elems || po > max_elems) continue;
-        const int64_t worst = std::max(pi, po);
-        if (best < 0 || worst < best) {
-            best = worst;
-            best_mask = mask;
-        }
-    }
-    if (best < 0) return false;
-    std::vector<int> in, outg;
-    for (int i = 0; i < n; ++i) (best_mask >> i & 1 ? in : outg).push_back(all[i]);
-    axes->clear();
-    for (int q : in) axes->push_back(q);
-    for (int q : outg) axes->push_back(q);
-    *split = (int)in.size();
-    return true;
-}
-
-static int ilog2(int v)
-{
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
 }
 
 }  // namespace sfft
@@ -261,53 +166,27 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     pd.max_rounds = o.max_rounds;
     pd.K = K;
 
-    // shared memory budget of one tile (leave room for twiddles)
-    const int64_t max_elems = (int64_t)(di.max_smem - 12 * 1024) / (int64_t)p->esz;
     std::vector<int32_t> h_nidx, h_pbin, h_bpos, tw_P, tw_t;
     int64_t bin_base = 0;
-    size_t smem1 = 0, smem2 = 0;
-    int64_t max_tile1 = 0, max_tile2 = 0;
+    PassPlan l1, l2;
     p->need_pass2 = false;
     const int64_t tile_target = p->prec ? 4096 : 2048;
+    int32_t tw_cursor = 0;
     for (int d = 0; d < n_stages; ++d) {
         StageDesc& s = pd.st[d];
         const int64_t L = f[d], B = N / L;
         s.B = (int32_t)B;
         s.L = (int32_t)L;
-        std::vector<int> Ps;
-        int split = 0;
-        if (!choose_axes(B, max_elems, &Ps, &split) || (int)Ps.size() > kMaxAxes) {
+        if (!pfa_layout_stage(&s, p->esz, di.max_smem, tile_target, &p->pass1[d], &p->pass2[d],
+                              &l1, &l2, &tw_cursor, &p->need_pass2)) {
             free_plan_memory(p);
             delete p;
             return SFFT_EINVAL;
         }
-        for (int P : Ps)
-            if (!(P > 0 && (P & (P - 1)) == 0) && P > 2049) {  // direct odd DFT: <= 1024 pairs
-                free_plan_memory(p);
-                delete p;
-                return SFFT_EINVAL;
-            }
-        s.n_axes = (int32_t)Ps.size();
-        s.split = split;
-        int32_t S = 1;
-        for (int a = 0; a < s.n_axes; ++a) {
-            AxisDesc& A = s.ax[a];
-            A.P = Ps[a];
-            A.pow2 = (A.P > 1 && (A.P & (A.P - 1)) == 0) ? 1 : 0;
-            A.log2P = A.pow2 ? ilog2(A.P) : 0;
-            A.S = S;
-            S *= A.P;
-            const int64_t Bp = B / A.P;
-            A.rur = (int32_t)(Bp % B);
-            A.crt = (int32_t)((Bp * modinv(Bp % A.P, A.P)) % B);
-            A.tw_off = (int32_t)tw_P.size();
-            const int nt = A.pow2 ? A.P / 2 : A.P;
-            for (int t = 0; t < nt; ++t) {
-                tw_P.push_back(A.P);
-                tw_t.push_back(t);
-            }
+        for (int r = 0; r < n_delays; ++r) {
+            s.tau[r] = (int32_t)delays[(int64_t)d * n_delays + r];
+            s.tauL[r] = (int32_t)(delays[(int64_t)d * n_delays + r] % L);
         }
-        for (int r = 0; r < n_delays; ++r) s.tau[r] = (int32_t)delays[(int64_t)d * n_delays + r];
         s.r0 = s.r1 = -1;
         for (int r = 0; r < n_delays; ++r) {
             if (s.tau[r] == 0 && s.r0 < 0) s.r0 = r;
@@ -353,53 +232,35 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
                 return SFFT_EINVAL;
             }
         }
-
-        // passes
-        auto tw_elems = [&](int a0, int a1) {
-            int64_t t = 0;
-            for (int a = a0; a < a1; ++a) t += s.ax[a].pow2 ? s.ax[a].P / 2 : s.ax[a].P;
-            return t;
-        };
-        PassDesc& p1 = p->pass1[d];
-        PassDesc& p2 = p->pass2[d];
-        memset(&p1, 0, sizeof(p1));
-        memset(&p2, 0, sizeof(p2));
-        if (split == s.n_axes) {
-            p1 = PassDesc{0, s.n_axes, 1, 1, 1, (int32_t)B, 1, 1};
-            smem1 = std::max(smem1, (size_t)(B + tw_elems(0, s.n_axes)) * p->esz);
-            max_tile1 = std::max<int64_t>(max_tile1, B);
-        } else {
-            p->need_pass2 = true;
-            int64_t inner = 1, outer = 1;
-            for (int a = 0; a < split; ++a) inner *= s.ax[a].P;
-            for (int a = split; a < s.n_axes; ++a) outer *= s.ax[a].P;
-            int64_t Tb = std::max<int64_t>(1, tile_target / outer);
-            Tb = std::min(Tb, inner);
-            while (Tb > 1 && Tb * outer > max_elems) --Tb;
-            int64_t Ta = std::max<int64_t>(1, tile_target / inner);
-            Ta = std::min(Ta, outer);
-            while (Ta > 1 && Ta * inner > max_elems) --Ta;
-            p1 = PassDesc{split, s.n_axes, (int32_t)Tb, 1, (int32_t)((inner + Tb - 1) / Tb),
-                          (int32_t)(Tb * outer), 1, 0};
-            p2 = PassDesc{0, split, 1, (int32_t)Ta, (int32_t)((outer + Ta - 1) / Ta),
-                          (int32_t)(inner * Ta), 0, 1};
-            smem1 = std::max(smem1, (size_t)(Tb * outer + tw_elems(split, s.n_axes)) * p->esz);
-            smem2 = std::max(smem2, (size_t)(inner * Ta + tw_elems(0, split)) * p->esz);
-            max_tile1 = std::max<int64_t>(max_tile1, Tb * outer);
-            max_tile2 = std::max<int64_t>(max_tile2, inner * Ta);
-        }
         bin_base += B;
+    }
+    // twiddle table: every axis (layout of axis_tw_residue), then the L roots of each stage
+    tw_P.assign((size_t)tw_cursor, 1);
+    tw_t.assign((size_t)tw_cursor, 0);
+    for (int d = 0; d < n_stages; ++d)
+        for (int a = 0; a < pd.st[d].n_axes; ++a) {
+            const AxisDesc& A = pd.st[d].ax[a];
+            const int cnt = axis_tw_count(A.P, A.pow2);
+            for (int i = 0; i < cnt; ++i) {
+                tw_P[(size_t)A.tw_off + i] = A.P;
+                tw_t[(size_t)A.tw_off + i] = axis_tw_residue(A.P, A.pow2, i);
+            }
+        }
+    pd.root_total = 0;
+    for (int d = 0; d < n_stages; ++d) {
+        pd.st[d].root_off = (int32_t)tw_P.size();
+        for (int t = 0; t < pd.st[d].L; ++t) {
+            tw_P.push_back(pd.st[d].L);
+            tw_t.push_back(t);
+        }
+        pd.root_total += pd.st[d].L;
     }
     pd.sumB = (int32_t)bin_base;
     pd.y_per_sig = (int64_t)bin_base * n_delays;
-    p->smem1 = smem1;
-    p->smem2 = smem2;
-    auto pick_threads = [](int64_t tile) {
-        int64_t t = (tile / 8 + 31) / 32 * 32;
-        return (int)std::min<int64_t>(512, std::max<int64_t>(128, t));
-    };
-    p->threads1 = pick_threads(max_tile1);
-    p->threads2 = pick_threads(max_tile2);
+    p->smem1 = l1.smem;
+    p->smem2 = l2.smem;
+    p->threads1 = pfa_threads(l1.tile);
+    p->threads2 = pfa_threads(l2.tile);
 
     // device memory
     const size_t nb = (size_t)pd.sumB, mb = (size_t)p->max_batch;
@@ -580,16 +441,19 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     da.pbin = p->d_pbin;
     da.bpos = p->d_bpos;
     da.bins = p->d_bins;
+    da.roots = (const unsigned char*)p->d_tw + (size_t)pd.st[0].root_off * p->esz;
     const int threads = 512;
     const int total = p->num_sms * p->decode_occ;
+    // later rounds touch O(K) bins: about one CTA per 256 expected single-tons
     int G = 1;
     if (n < total) {
-        G = (int)std::min<int64_t>(total / n, ((int64_t)pd.sumB + 2047) / 2048);
+        G = (int)std::min<int64_t>(total / n, ((int64_t)pd.K + 255) / 256);
         G = std::max(G, 1);
     }
     da.G = G;
     {
-        PhaseScope ps(p, st, 1, 1);
+        PhaseScope ps(p, st, 1, 2);
+        CK(launch_classify(da, p->prec, st));
         CK(launch_decode(da, p->prec, threads, G > 1, st));
     }
 

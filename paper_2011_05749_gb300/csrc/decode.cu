@@ -1,16 +1,24 @@
 // decode.cu -- peeling decoder (Sec. 3.2, subproblems 1-3, Eq. 20) and output compaction.
 //
-// One group of G CTAs decodes one signal in parallel rounds (genie-assisted peeling):
-//   D1  every examined bin: energy sum_r |Y_r|^2 against T0 -> zero-ton, else queued;
-//   D2  every queued bin: location (ARG phase or ML candidate search), least-squares value
-//       v and residual rho; rho <= T1 -> single-ton candidate (the bin is resolved);
+// Round 1 examines every bin of every signal and is embarrassingly parallel, so it runs as
+// one grid-wide launch (classify_kernel): tiles of bins, energies with all R loads in
+// flight, then locate/fit of the tile's non-zero bins.  The later rounds touch O(K) bins and
+// run in peel_kernel, one group of G CTAs per signal:
 //   P   every candidate frequency f not already taken (earlier round, or a lower stage in
 //       this round): recorded, and B_e v a_r(f) subtracted from bin f mod B_e of every
-//       stage e and delay r (float/double atomics); bins that change and are still open
-//       are queued for the next round.
+//       stage e and delay r (atomics); bins that change and are still open are queued;
+//   D1  every queued bin: energy sum_r |Y_r|^2 against T0 -> zero-ton, else non-zero;
+//   D2  every non-zero bin: location (ARG phase or ML candidate search), least-squares
+//       value v and residual rho; rho <= T1 -> single-ton candidate (the bin is resolved).
 // Phases are separated by a group barrier (a bounded spin when G > 1, so a lost CTA turns
-// into SFFT_ETIMEDOUT instead of a hang).  Locations and fits use FP64 (twiddles from the
-// exact integer residue (f tau) mod N); the FP32 path keeps bins and subtraction in FP32.
+// into SFFT_ETIMEDOUT instead of a hang).
+//
+// Arithmetic: the delay phasors a_r(f) = e^{2 pi i (f tau_r mod N) / N} come from the exact
+// integer residue (f tau_r) mod N, evaluated in the path's type (FP32: phase error below
+// 4e-7 rad).  The ML search of a bin j factors a_r(j + q B) = a_r(j) e^{2 pi i q tau_r / L},
+// so its L candidates are scored against a table of the L-th roots of unity indexed by
+// (q (tau_r mod L)) mod L.  The ARG location takes the angle and the snap to the bin's
+// candidates in FP64.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,6 +29,8 @@ namespace sfft {
 
 constexpr long long kSpinLimit = 1ll << 22;  // ~0.3-1 s of polling at 64-256 ns per poll
 constexpr int64_t kFMask = (1ll << 40) - 1;
+constexpr int kClassifyTile = 2048;          // bins per classify CTA
+constexpr int kClassifyThreads = 256;
 
 __device__ __forceinline__ int ldv(const int32_t* p) { return *(const volatile int32_t*)p; }
 
@@ -67,25 +77,33 @@ __device__ __forceinline__ int stage_of(const PlanDesc& pd, int b)
     return d;
 }
 
-// e^{+2 pi i (f tau mod N) / N} in FP64 from the exact integer residue
-__device__ __forceinline__ double2 delay_phasor(int64_t f, int64_t tau, int64_t N)
+// e^{+2 pi i m / N} for an exact residue 0 <= m < N (argument reduced to (-1, 1] of pi)
+__device__ __forceinline__ float2 unit_twiddle(int64_t m, int32_t N, float)
 {
-    const int64_t m = (f * tau) % N;
-    double s, c;
-    sincospi(2.0 * (double)m / (double)N, &s, &c);
-    return double2{c, s};
+    int64_t m2 = 2 * m;
+    if (m2 > N) m2 -= 2 * (int64_t)N;
+    float sv, cv;
+    sincospif((float)m2 / (float)N, &sv, &cv);
+    return float2{cv, sv};
 }
-
-template <typename V>
-__device__ __forceinline__ double2 to_d2(V v)
+__device__ __forceinline__ double2 unit_twiddle(int64_t m, int32_t N, double)
 {
-    return double2{(double)v.x, (double)v.y};
+    int64_t m2 = 2 * m;
+    if (m2 > N) m2 -= 2 * (int64_t)N;
+    double sv, cv;
+    sincospi((double)m2 / (double)N, &sv, &cv);
+    return double2{cv, sv};
 }
 
 template <typename T>
-__device__ __forceinline__ void record_candidate(const DecodeArgs& a, int32_t* ctr,
-                                                 const DecodeWs& w, int round, int b, int64_t f,
-                                                 double2 v)
+__device__ __forceinline__ typename C2<T>::t delay_phasor(int64_t f, int32_t tau, int32_t N)
+{
+    return unit_twiddle((f * (int64_t)tau) % N, N, T(0));
+}
+
+template <typename T>
+__device__ __forceinline__ void record_candidate(int32_t* ctr, const DecodeWs& w, int round, int b,
+                                                 int64_t f, typename C2<T>::t v)
 {
     using V = typename C2<T>::t;
     __stcg(w.state + b, (uint8_t)2);
@@ -93,45 +111,44 @@ __device__ __forceinline__ void record_candidate(const DecodeArgs& a, int32_t* c
     const int k = atomicAdd(ctr + kCtrRoundBase + 3 * round + 2, 1);
     __stcg(w.cbin + k, b);
     __stcg((long long*)w.cf + k, (long long)f);
-    reinterpret_cast<V*>(w.cv)[k] = V{(T)v.x, (T)v.y};
+    reinterpret_cast<V*>(w.cv)[k] = v;
     atomicAdd(ctr + kCtrResolved, 1);
 }
 
-// D2, ML locate: one warp per non-zero bin.  Lanes score the candidates f = j + q B
-// (q < L) by |sum_r Y_r conj(a_r(f))|^2 (arithmetic type T), the warp keeps the best
-// (lowest q on ties), then fits v and rho in FP64 with one lane per delay.
+// D2, ML locate: one warp per non-zero bin j of stage d.  Lane r < R forms
+// Z_r = Y_r conj(a_r(j)); lanes then score candidates q = lane, lane + 32, ... by
+// |sum_r Z_r e^{-2 pi i q tauL_r / L}|^2, the warp keeps the best (lowest q on ties) and
+// fits v = sum_r Z_r e^{-2 pi i q tauL_r / L} / (R B) and rho = sum_r |Z_r - B v e^{..}|^2.
 template <typename T>
 __device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
-                               const typename C2<T>::t* Y, int round, int b)
+                               const typename C2<T>::t* Y, const typename C2<T>::t* roots,
+                               int round, int b)
 {
     using V = typename C2<T>::t;
     const PlanDesc& pd = a.pd;
     const int lane = threadIdx.x & 31;
     const int d = stage_of(pd, b);
     const StageDesc& st = pd.st[d];
-    const int p = b - st.bin_base;
     const int R = pd.R;
     const int B = st.B, L = st.L, N = pd.N;
     const int j = __ldg(a.pbin + b);
-    const V* Yb = Y + st.y_off + p;
-    V my = {0, 0};
-    if (lane < R) my = __ldcg(Yb + (int64_t)lane * B);
-    T yr[kMaxDelays][2];
-    int mr[kMaxDelays], step[kMaxDelays];
+    const V* wl = roots + (st.root_off - pd.st[0].root_off);
+    V z = {0, 0};
+    if (lane < R) {
+        const V y = __ldcg(Y + st.y_off + (int64_t)lane * B + (b - st.bin_base));
+        const V aj = delay_phasor<T>(j, st.tau[lane], N);
+        z = V{y.x * aj.x + y.y * aj.y, y.y * aj.x - y.x * aj.y};
+    }
+    T zx[kMaxDelays], zy[kMaxDelays];
+    int idx[kMaxDelays], step[kMaxDelays];
 #pragma unroll
     for (int r = 0; r < kMaxDelays; ++r) {
-        yr[r][0] = __shfl_sync(0xffffffffu, my.x, r);
-        yr[r][1] = __shfl_sync(0xffffffffu, my.y, r);
-        if (r < R) {
-            const int64_t tau = st.tau[r];
-            mr[r] = (int)((((int64_t)j + (int64_t)lane * B) * tau) % N);
-            step[r] = (int)((((int64_t)32 * B) * tau) % N);
-        } else {
-            mr[r] = 0;
-            step[r] = 0;
-        }
+        zx[r] = __shfl_sync(0xffffffffu, z.x, r);
+        zy[r] = __shfl_sync(0xffffffffu, z.y, r);
+        const int t = r < R ? st.tauL[r] : 0;
+        idx[r] = (lane * t) % L;
+        step[r] = (32 * t) % L;
     }
-    const T two_over_n = (T)2 / (T)N;
     T best = (T)-1;
     int bq = 0;
     for (int q = lane; q < L; q += 32) {
@@ -139,13 +156,11 @@ __device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs
 #pragma unroll
         for (int r = 0; r < kMaxDelays; ++r) {
             if (r < R) {
-                T sv, cv;
-                sincospi((T)mr[r] * two_over_n, &sv, &cv);
-                // Y_r * conj(a) with a = (cv, sv)
-                cx += yr[r][0] * cv + yr[r][1] * sv;
-                cy += yr[r][1] * cv - yr[r][0] * sv;
-                int nm = mr[r] + step[r];
-                mr[r] = nm >= N ? nm - N : nm;
+                const V wv = wl[idx[r]];
+                cx += zx[r] * wv.x + zy[r] * wv.y;
+                cy += zy[r] * wv.x - zx[r] * wv.y;
+                const int ni = idx[r] + step[r];
+                idx[r] = ni >= L ? ni - L : ni;
             }
         }
         const T sc = cx * cx + cy * cy;
@@ -164,79 +179,76 @@ __device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs
         }
     }
     const int64_t f = (int64_t)j + (int64_t)bq * B;
-    // least-squares value and residual over the R delays, FP64
-    double2 ar = {0, 0}, cr = {0, 0};
+    V e = {1, 0}, c = {0, 0};
     if (lane < R) {
-        ar = delay_phasor(f, st.tau[lane], N);
-        const double2 y = to_d2(my);
-        cr = double2{y.x * ar.x + y.y * ar.y, y.y * ar.x - y.x * ar.y};
+        e = wl[(int)(((int64_t)bq * st.tauL[lane]) % L)];
+        c = V{z.x * e.x + z.y * e.y, z.y * e.x - z.x * e.y};
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        cr.x += __shfl_xor_sync(0xffffffffu, cr.x, o);
-        cr.y += __shfl_xor_sync(0xffffffffu, cr.y, o);
+        c.x += __shfl_xor_sync(0xffffffffu, c.x, o);
+        c.y += __shfl_xor_sync(0xffffffffu, c.y, o);
     }
-    const double sc = 1.0 / ((double)R * (double)B);
-    const double2 v = {cr.x * sc, cr.y * sc};
-    double e2 = 0;
+    const T sc = (T)1 / ((T)R * (T)B);
+    const V v = {c.x * sc, c.y * sc};
+    T e2 = 0;
     if (lane < R) {
-        const double2 y = to_d2(my);
-        const double ex = y.x - (double)B * (v.x * ar.x - v.y * ar.y);
-        const double ey = y.y - (double)B * (v.x * ar.y + v.y * ar.x);
+        const T ex = z.x - (T)B * (v.x * e.x - v.y * e.y);
+        const T ey = z.y - (T)B * (v.x * e.y + v.y * e.x);
         e2 = ex * ex + ey * ey;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-    if (lane == 0 && e2 <= st.T1) record_candidate<T>(a, ctr, w, round, b, f, v);
+    if (lane == 0 && (double)e2 <= st.T1) record_candidate<T>(ctr, w, round, b, f, v);
 }
 
-// D2, ARG locate (FFAST, Sec. 3.2 subproblem 2): f from the phase of Y(1) conj(Y(0)),
-// snapped to the candidate set {j + q B}; one thread per bin.
+// D2, ARG locate (FFAST, Sec. 3.2 subproblem 2): f from the phase of Y(1) conj(Y(0)) in
+// FP64, snapped to the candidate set {j + q B}; one thread per bin.
 template <typename T>
 __device__ void locate_arg_thread(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
                                   const typename C2<T>::t* Y, int round, int b)
 {
+    using V = typename C2<T>::t;
     const PlanDesc& pd = a.pd;
     const int d = stage_of(pd, b);
     const StageDesc& st = pd.st[d];
-    const int p = b - st.bin_base;
     const int R = pd.R;
     const int B = st.B, L = st.L, N = pd.N;
     const int j = __ldg(a.pbin + b);
-    const auto* Yb = Y + st.y_off + p;
-    const double2 y0 = to_d2(__ldcg(Yb + (int64_t)st.r0 * B));
-    const double2 y1 = to_d2(__ldcg(Yb + (int64_t)st.r1 * B));
-    const double rx = y1.x * y0.x + y1.y * y0.y;
-    const double ry = y1.y * y0.x - y1.x * y0.y;
+    const V* Yb = Y + st.y_off + (b - st.bin_base);
+    const V y0 = __ldcg(Yb + (int64_t)st.r0 * B);
+    const V y1 = __ldcg(Yb + (int64_t)st.r1 * B);
+    const double rx = (double)y1.x * y0.x + (double)y1.y * y0.y;
+    const double ry = (double)y1.y * y0.x - (double)y1.x * y0.y;
     const double fe = atan2(ry, rx) * (double)N / 6.283185307179586476925286766559;
     const double qd = floor((fe - (double)j) / (double)B + 0.5);
     int64_t q = (int64_t)qd % L;
     if (q < 0) q += L;
     const int64_t f = (int64_t)j + q * B;
-    double2 c = {0, 0};
+    V c = {0, 0};
     for (int r = 0; r < R; ++r) {
-        const double2 ar = delay_phasor(f, st.tau[r], N);
-        const double2 y = to_d2(__ldcg(Yb + (int64_t)r * B));
+        const V ar = delay_phasor<T>(f, st.tau[r], N);
+        const V y = __ldcg(Yb + (int64_t)r * B);
         c.x += y.x * ar.x + y.y * ar.y;
         c.y += y.y * ar.x - y.x * ar.y;
     }
-    const double sc = 1.0 / ((double)R * (double)B);
-    const double2 v = {c.x * sc, c.y * sc};
-    double e2 = 0;
+    const T sc = (T)1 / ((T)R * (T)B);
+    const V v = {c.x * sc, c.y * sc};
+    T e2 = 0;
     for (int r = 0; r < R; ++r) {
-        const double2 ar = delay_phasor(f, st.tau[r], N);
-        const double2 y = to_d2(__ldcg(Yb + (int64_t)r * B));
-        const double ex = y.x - (double)B * (v.x * ar.x - v.y * ar.y);
-        const double ey = y.y - (double)B * (v.x * ar.y + v.y * ar.x);
+        const V ar = delay_phasor<T>(f, st.tau[r], N);
+        const V y = __ldcg(Yb + (int64_t)r * B);
+        const T ex = y.x - (T)B * (v.x * ar.x - v.y * ar.y);
+        const T ey = y.y - (T)B * (v.x * ar.y + v.y * ar.x);
         e2 += ex * ex + ey * ey;
     }
-    if (e2 <= st.T1) record_candidate<T>(a, ctr, w, round, b, f, v);
+    if ((double)e2 <= st.T1) record_candidate<T>(ctr, w, round, b, f, v);
 }
 
-__device__ __forceinline__ void atomic_sub_c(float2* p, double2 d)
+__device__ __forceinline__ void atomic_sub_c(float2* p, float2 d)
 {
-    atomicAdd(&p->x, (float)-d.x);
-    atomicAdd(&p->y, (float)-d.y);
+    atomicAdd(&p->x, -d.x);
+    atomicAdd(&p->y, -d.y);
 }
 __device__ __forceinline__ void atomic_sub_c(double2* p, double2 d)
 {
@@ -253,8 +265,7 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     const PlanDesc& pd = a.pd;
     const int b = __ldcg(w.cbin + c);
     const int64_t f = (int64_t)__ldcg((const long long*)w.cf + c);
-    const V vv = __ldcg(reinterpret_cast<const V*>(w.cv) + c);
-    const double2 v = to_d2(vv);
+    const V v = __ldcg(reinterpret_cast<const V*>(w.cv) + c);
     const int d = stage_of(pd, b);
     for (int e = 0; e < pd.D; ++e) {
         if (e == d) continue;
@@ -269,16 +280,16 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     }
     const int k = atomicAdd(ctr + kCtrRec, 1);
     __stcg((long long*)w.rec_f + k, (long long)f);
-    reinterpret_cast<V*>(w.rec_v)[k] = vv;
+    reinterpret_cast<V*>(w.rec_v)[k] = v;
     for (int e = 0; e < pd.D; ++e) {
         const StageDesc& se = pd.st[e];
         const int je = (int)(f % se.B);
         const int pe = __ldg(a.bpos + se.bin_base + je);
         const int be = se.bin_base + pe;
+        const T Bv = (T)se.B;
         for (int r = 0; r < pd.R; ++r) {
-            const double2 ar = delay_phasor(f, se.tau[r], pd.N);
-            const double2 dlt = {(double)se.B * (v.x * ar.x - v.y * ar.y),
-                                 (double)se.B * (v.x * ar.y + v.y * ar.x)};
+            const V ar = delay_phasor<T>(f, se.tau[r], pd.N);
+            const V dlt = {Bv * (v.x * ar.x - v.y * ar.y), Bv * (v.x * ar.y + v.y * ar.x)};
             atomic_sub_c(Y + se.y_off + (int64_t)r * se.B + pe, dlt);
         }
         if (__ldcg(w.state + be) == 0 && atomicExch(w.dirty + be, 1u) == 0u) {
@@ -289,18 +300,31 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     }
 }
 
+// D1 of one bin: energy over the R delays (all loads in flight)
 template <typename T>
-__global__ void __launch_bounds__(512) decode_kernel(const __grid_constant__ DecodeArgs a)
+__device__ __forceinline__ bool bin_is_zero(const PlanDesc& pd, const typename C2<T>::t* Y, int b)
 {
     using V = typename C2<T>::t;
-    const PlanDesc& pd = a.pd;
-    const int G = a.G;
-    const int sig = blockIdx.x / G;
-    const int gi = blockIdx.x - sig * G;
-    if (sig >= a.n_sig) return;
-    const int nb = pd.sumB;
+    const int d = stage_of(pd, b);
+    const StageDesc& st = pd.st[d];
+    const V* Yb = Y + st.y_off + (b - st.bin_base);
+    V y[kMaxDelays];
+#pragma unroll
+    for (int r = 0; r < kMaxDelays; ++r)
+        if (r < pd.R) y[r] = __ldcg(Yb + (int64_t)r * st.B);
+    T E = 0;
+#pragma unroll
+    for (int r = 0; r < kMaxDelays; ++r)
+        if (r < pd.R) E += y[r].x * y[r].x + y[r].y * y[r].y;
+    return (double)E <= st.T0;
+}
+
+template <typename T>
+__device__ __forceinline__ DecodeWs slot_ws(const DecodeArgs& a, int sig)
+{
+    using V = typename C2<T>::t;
     DecodeWs w = a.ws;
-    const int64_t so = (int64_t)sig * nb;
+    const int64_t so = (int64_t)sig * a.pd.sumB;
     w.state += so;
     w.dirty += so;
     w.cand += so;
@@ -312,62 +336,121 @@ __global__ void __launch_bounds__(512) decode_kernel(const __grid_constant__ Dec
     w.cv = reinterpret_cast<V*>(w.cv) + so;
     w.rec_f += so;
     w.rec_v = reinterpret_cast<V*>(w.rec_v) + so;
-    int32_t* ctr = w.ctr + (int64_t)sig * a.ctr_stride;
+    w.ctr += (int64_t)sig * a.ctr_stride;
+    return w;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_roots(const DecodeArgs& a, typename C2<T>::t* roots_s)
+{
+    using V = typename C2<T>::t;
+    if (a.pd.locate != 1) return;
+    const V* src = reinterpret_cast<const V*>(a.roots);
+    for (int i = threadIdx.x; i < a.pd.root_total; i += blockDim.x) roots_s[i] = src[i];
+}
+
+// Round 1: classify every bin.  One CTA per tile of kClassifyTile bins of one signal.
+template <typename T>
+__global__ void __launch_bounds__(kClassifyThreads) classify_kernel(const __grid_constant__ DecodeArgs a)
+{
+    using V = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* roots_s = reinterpret_cast<V*>(smem_raw);
+    __shared__ int s_nz[kClassifyTile];
+    __shared__ int s_cnt, s_res;
+    const PlanDesc& pd = a.pd;
+    const int tiles = (pd.sumB + kClassifyTile - 1) / kClassifyTile;
+    const int sig = blockIdx.x / tiles;
+    const int tile = blockIdx.x - sig * tiles;
+    const DecodeWs w = slot_ws<T>(a, sig);
     V* Y = reinterpret_cast<V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
+    const int b0 = tile * kClassifyTile;
+    const int b1 = min(pd.sumB, b0 + kClassifyTile);
+    load_roots<T>(a, roots_s);
+    if (threadIdx.x == 0) {
+        s_cnt = 0;
+        s_res = 0;
+    }
+    __syncthreads();
+    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+        __stcg((long long*)w.cand + b, -1ll);
+        __stcg(w.dirty + b, 0u);
+        if (bin_is_zero<T>(pd, Y, b)) {
+            __stcg(w.state + b, (uint8_t)1);
+            atomicAdd(&s_res, 1);
+        } else {
+            __stcg(w.state + b, (uint8_t)0);
+            s_nz[atomicAdd(&s_cnt, 1)] = b;
+        }
+    }
+    __syncthreads();
+    const int n_nz = s_cnt;
+    if (pd.locate == 1) {
+        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int i = warp; i < n_nz; i += nwarps) locate_ml_warp<T>(a, w.ctr, w, Y, roots_s, 1, s_nz[i]);
+    } else {
+        for (int i = threadIdx.x; i < n_nz; i += blockDim.x) locate_arg_thread<T>(a, w.ctr, w, Y, 1, s_nz[i]);
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(w.ctr + kCtrResolved, s_res);
+        atomicAdd(w.ctr + kCtrIdents, b1 - b0);
+    }
+}
+
+// Rounds 1 (peel) .. last: one group of G CTAs per signal.
+template <typename T>
+__global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ DecodeArgs a)
+{
+    using V = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* roots_s = reinterpret_cast<V*>(smem_raw);
+    const PlanDesc& pd = a.pd;
+    const int G = a.G;
+    const int sig = blockIdx.x / G;
+    const int gi = blockIdx.x - sig * G;
+    if (sig >= a.n_sig) return;
+    const DecodeWs w = slot_ws<T>(a, sig);
+    int32_t* ctr = w.ctr;
+    V* Y = reinterpret_cast<V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
+    load_roots<T>(a, roots_s);
+    __syncthreads();
 
     const int wt = gi * blockDim.x + threadIdx.x;
     const int nw = G * blockDim.x;
     const int gw = wt >> 5, nwarps = nw >> 5;
-    const int R = pd.R;
 
-    int round = 0;
+    int round = 1;
     while (true) {
+        // P: accept and peel this round's single-tons
+        const int n_c = ldv(ctr + kCtrRoundBase + 3 * round + 2);
+        for (int i = wt; i < n_c; i += nw) peel_candidate<T>(a, ctr, w, Y, round, i);
+        if (!group_barrier(ctr, G)) break;
+        const int n_next = ldv(ctr + kCtrRoundBase + 3 * round + 0);
+        if (n_next == 0 || round >= pd.max_rounds) break;
         ++round;
-        // D1: energies of the examined bins
-        const int n_act = round == 1 ? nb : ldv(ctr + kCtrRoundBase + 3 * (round - 1) + 0);
+        // D1: energies of the queued bins
         const int32_t* act = ((round - 1) & 1) ? w.list1 : w.list0;
-        for (int i = wt; i < n_act; i += nw) {
-            const int b = round == 1 ? i : __ldcg(act + i);
-            if (round == 1) __stcg((long long*)w.cand + b, -1ll);
+        for (int i = wt; i < n_next; i += nw) {
+            const int b = __ldcg(act + i);
             __stcg(w.dirty + b, 0u);
-            const int d = stage_of(pd, b);
-            const StageDesc& st = pd.st[d];
-            const V* Yb = Y + st.y_off + (b - st.bin_base);
-            double E = 0;
-            for (int r = 0; r < R; ++r) {
-                const V y = __ldcg(Yb + (int64_t)r * st.B);
-                E += (double)y.x * y.x + (double)y.y * y.y;
-            }
-            if (E <= st.T0) {
+            if (bin_is_zero<T>(pd, Y, b)) {
                 __stcg(w.state + b, (uint8_t)1);
                 atomicAdd(ctr + kCtrResolved, 1);
             } else {
-                if (round == 1) __stcg(w.state + b, (uint8_t)0);
-                const int k = atomicAdd(ctr + kCtrRoundBase + 3 * round + 1, 1);
-                __stcg(w.nzl + k, b);
+                __stcg(w.nzl + atomicAdd(ctr + kCtrRoundBase + 3 * round + 1, 1), b);
             }
         }
-        if (wt == 0) atomicAdd(ctr + kCtrIdents, n_act);
+        if (wt == 0) atomicAdd(ctr + kCtrIdents, n_next);
         if (!group_barrier(ctr, G)) break;
-
         // D2: locate, fit, singleton test
         const int n_nz = ldv(ctr + kCtrRoundBase + 3 * round + 1);
         if (pd.locate == 1) {
             for (int i = gw; i < n_nz; i += nwarps)
-                locate_ml_warp<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
+                locate_ml_warp<T>(a, ctr, w, Y, roots_s, round, __ldcg(w.nzl + i));
         } else {
-            for (int i = wt; i < n_nz; i += nw)
-                locate_arg_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
+            for (int i = wt; i < n_nz; i += nw) locate_arg_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
         }
         if (!group_barrier(ctr, G)) break;
-
-        // P: accept and peel
-        const int n_c = ldv(ctr + kCtrRoundBase + 3 * round + 2);
-        for (int i = wt; i < n_c; i += nw) peel_candidate<T>(a, ctr, w, Y, round, i);
-        if (!group_barrier(ctr, G)) break;
-
-        const int n_next = ldv(ctr + kCtrRoundBase + 3 * round + 0);
-        if (n_next == 0 || round >= pd.max_rounds) break;
     }
     if (gi == 0 && threadIdx.x == 0) ctr[kCtrRounds] = round;
 }
@@ -476,28 +559,43 @@ __global__ void __launch_bounds__(1024) compact_kernel(const __grid_constant__ C
     }
 }
 
+cudaError_t launch_classify(const DecodeArgs& a, int precision, cudaStream_t st)
+{
+    const int tiles = (a.pd.sumB + kClassifyTile - 1) / kClassifyTile;
+    const unsigned grid = (unsigned)a.n_sig * (unsigned)tiles;
+    if (grid == 0) return cudaSuccess;
+    const size_t smem = a.pd.locate == 1 ? (size_t)a.pd.root_total * (precision == 1 ? 8 : 16) : 0;
+    if (precision == 1)
+        classify_kernel<float><<<grid, kClassifyThreads, smem, st>>>(a);
+    else
+        classify_kernel<double><<<grid, kClassifyThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_decode(const DecodeArgs& a, int precision, int threads, bool cooperative,
                           cudaStream_t st)
 {
     const unsigned grid = (unsigned)a.n_sig * (unsigned)a.G;
     if (grid == 0) return cudaSuccess;
-    void* fn = precision == 1 ? (void*)decode_kernel<float> : (void*)decode_kernel<double>;
+    const size_t smem = a.pd.locate == 1 ? (size_t)a.pd.root_total * (precision == 1 ? 8 : 16) : 0;
+    void* fn = precision == 1 ? (void*)peel_kernel<float> : (void*)peel_kernel<double>;
     if (cooperative) {
         void* args[] = {(void*)&a};
-        return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, st);
+        return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, smem, st);
     }
     if (precision == 1)
-        decode_kernel<float><<<grid, threads, 0, st>>>(a);
+        peel_kernel<float><<<grid, threads, smem, st>>>(a);
     else
-        decode_kernel<double><<<grid, threads, 0, st>>>(a);
+        peel_kernel<double><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 int decode_occupancy(int precision, int threads)
 {
     int nb = 0;
-    void* fn = precision == 1 ? (void*)decode_kernel<float> : (void*)decode_kernel<double>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 0) != cudaSuccess) return 1;
+    void* fn = precision == 1 ? (void*)peel_kernel<float> : (void*)peel_kernel<double>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 16 * 1024) != cudaSuccess)
+        return 1;
     return nb > 0 ? nb : 1;
 }
 

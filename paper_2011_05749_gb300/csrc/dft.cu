@@ -21,15 +21,18 @@ namespace sfft {
 //   sub-DFT m starts at (m % LS) + (m / LS) * LS * P, element n at + n * LS.
 // X_k = x_0 + sum_{n=1}^{(P-1)/2} [ (x_n + x_{P-n}) cos(2 pi n k / P)
 //                                   - i (x_n - x_{P-n}) sin(2 pi n k / P) ],
-// X_{P-k} the same with the sine term negated.  Thread (g, m) computes GP output pairs.
+// X_{P-k} the same with the sine term negated.  Thread (g, m) computes GP output pairs
+// k = g GP + 1 .. g GP + GP of sub-DFT m; the twiddle matrix row n (cos, sin)(2 pi n k / P)
+// is read as 16-byte vectors that every lane of a warp shares.
 template <typename T, int GP>
-__device__ void axis_dft_odd(typename C2<T>::t* s, const typename C2<T>::t* tw, int P, int LS,
+__device__ void axis_dft_odd(typename C2<T>::t* s, const typename C2<T>::t* twm, int P, int LS,
                              int TS)
 {
     using V = typename C2<T>::t;
     const int M = TS / P;
     const int pairs = (P - 1) >> 1;
-    const int NG = (pairs + GP - 1) / GP;
+    const int KP = odd_row_len(P);  // row length of the twiddle matrix (a multiple of GP)
+    const int NG = KP / GP;
     const int Mc = max(1, (int)blockDim.x / NG);
     const int g = threadIdx.x / Mc;
     const int ml = threadIdx.x - g * Mc;
@@ -37,7 +40,6 @@ __device__ void axis_dft_odd(typename C2<T>::t* s, const typename C2<T>::t* tw, 
         const int m = m0 + ml;
         const bool act = g < NG && m < M;
         V acc[GP], sac[GP];
-        int idx[GP], kk[GP];
         V x0 = {0, 0}, dc = {0, 0};
         int base = 0;
         if (act) {
@@ -46,28 +48,35 @@ __device__ void axis_dft_odd(typename C2<T>::t* s, const typename C2<T>::t* tw, 
             dc = x0;
 #pragma unroll
             for (int i = 0; i < GP; ++i) {
-                const int k = g * GP + 1 + i;
-                kk[i] = k <= pairs ? k : 0;
-                idx[i] = 0;
                 acc[i] = {0, 0};
                 sac[i] = {0, 0};
             }
-            for (int n = 1; n <= pairs; ++n) {
+            const V* row = twm + g * GP;
+            for (int n = 1; n <= pairs; ++n, row += KP) {
                 const V xa = s[base + n * LS];
                 const V xb = s[base + (P - n) * LS];
                 const V av = {xa.x + xb.x, xa.y + xb.y};
                 const V bv = {xa.x - xb.x, xa.y - xb.y};
                 dc.x += av.x;
                 dc.y += av.y;
+                V w[GP];
+                if constexpr (sizeof(V) == 8 && GP >= 2) {
+#pragma unroll
+                    for (int i = 0; i < GP / 2; ++i) {
+                        const float4 q = reinterpret_cast<const float4*>(row)[i];
+                        w[2 * i] = V{q.x, q.y};
+                        w[2 * i + 1] = V{q.z, q.w};
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < GP; ++i) w[i] = row[i];
+                }
 #pragma unroll
                 for (int i = 0; i < GP; ++i) {
-                    idx[i] += kk[i];
-                    if (idx[i] >= P) idx[i] -= P;
-                    const V w = tw[idx[i]];
-                    acc[i].x = fma(av.x, w.x, acc[i].x);
-                    acc[i].y = fma(av.y, w.x, acc[i].y);
-                    sac[i].x = fma(bv.x, w.y, sac[i].x);
-                    sac[i].y = fma(bv.y, w.y, sac[i].y);
+                    acc[i].x = fma(av.x, w[i].x, acc[i].x);
+                    acc[i].y = fma(av.y, w[i].x, acc[i].y);
+                    sac[i].x = fma(bv.x, w[i].y, sac[i].x);
+                    sac[i].y = fma(bv.y, w[i].y, sac[i].y);
                 }
             }
         }
@@ -76,8 +85,8 @@ __device__ void axis_dft_odd(typename C2<T>::t* s, const typename C2<T>::t* tw, 
             if (g == 0) s[base] = dc;
 #pragma unroll
             for (int i = 0; i < GP; ++i) {
-                if (kk[i] == 0) continue;
-                const int k = kk[i];
+                const int k = g * GP + 1 + i;
+                if (k > pairs) continue;
                 const V c = {x0.x + acc[i].x, x0.y + acc[i].y};
                 s[base + k * LS] = V{c.x + sac[i].y, c.y - sac[i].x};
                 s[base + (P - k) * LS] = V{c.x - sac[i].y, c.y + sac[i].x};
@@ -87,39 +96,62 @@ __device__ void axis_dft_odd(typename C2<T>::t* s, const typename C2<T>::t* tw, 
     }
 }
 
-// In-place radix-2 decimation-in-time FFTs of length P = 2^log2P along one axis; the
-// input is stored bit-reversed along the axis, the output comes out in natural order.
-// tw[t] = (cos, sin)(2 pi t / P), t < P / 2.
+// In-place decimation-in-time FFTs of length P = 2^log2P along one axis; the input is
+// stored bit-reversed along the axis, the output comes out in natural order.  Up to three
+// radix-2 stages run per pass in registers (a radix-8 group of elements i h, i < 8, of a
+// block), so the tile makes ceil(log2P / 3) trips through shared memory.
+// tw[t] = (cos, sin)(2 pi t / P), t < P / 2; the butterfly of the stage with half-size H
+// multiplies by W_P^{(p mod H) P / (2 H)}.
 template <typename T>
 __device__ void axis_fft_pow2(typename C2<T>::t* s, const typename C2<T>::t* tw, int P,
                               int log2P, int LS, int TS)
 {
     using V = typename C2<T>::t;
     const int M = TS / P;
-    const int half = P >> 1;
-    const int nb = M * half;
-    for (int lh = 0; lh < log2P; ++lh) {
+    for (int lh = 0; lh < log2P;) {
+        const int c = min(3, log2P - lh);
+        const int G8 = 1 << c;
         const int h = 1 << lh;
-        for (int w = threadIdx.x; w < nb; w += blockDim.x) {
-            int i, m;
+        const int ngrp = P >> c;
+        const int nw = M * ngrp;
+        for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+            int gi, m;
             if (LS == 1) {
-                i = w & (half - 1);
-                m = w >> (log2P - 1);
+                gi = w % ngrp;
+                m = w / ngrp;
             } else {
                 m = w % M;
-                i = w / M;
+                gi = w / M;
             }
-            const int grp = i >> lh, ii = i & (h - 1);
+            const int ii = gi & (h - 1), blk = gi >> lh;
             const int base = (m % LS) + (m / LS) * LS * P;
-            const int p0 = base + ((grp << (lh + 1)) + ii) * LS;
-            const int p1 = p0 + h * LS;
-            const V wv = tw[ii << (log2P - 1 - lh)];
-            const V u = s[p0], v = s[p1];
-            const V vt = {v.x * wv.x + v.y * wv.y, v.y * wv.x - v.x * wv.y};
-            s[p0] = V{u.x + vt.x, u.y + vt.y};
-            s[p1] = V{u.x - vt.x, u.y - vt.y};
+            const int p0 = base + (blk * (G8 * h) + ii) * LS;
+            const int st = h * LS;
+            V v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < G8) v[i] = s[p0 + i * st];
+#pragma unroll
+            for (int sg = 0; sg < 3; ++sg) {
+                if (sg >= c) break;
+                const int hs = 1 << sg;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (i >= G8 || (i & hs)) continue;
+                    const int t = (ii + (i & (hs - 1)) * h) << (log2P - 1 - lh - sg);
+                    const V wv = tw[t];
+                    const V u = v[i], x = v[i + hs];
+                    const V xt = {x.x * wv.x + x.y * wv.y, x.y * wv.x - x.x * wv.y};
+                    v[i] = V{u.x + xt.x, u.y + xt.y};
+                    v[i + hs] = V{u.x - xt.x, u.y - xt.y};
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < G8) s[p0 + i * st] = v[i];
         }
         __syncthreads();
+        lh += c;
     }
 }
 
@@ -128,15 +160,14 @@ __device__ __forceinline__ void axis_dft_odd_dispatch(typename C2<T>::t* s,
                                                       const typename C2<T>::t* tw, int P,
                                                       int LS, int TS)
 {
-    const int pairs = (P - 1) >> 1;
-    if (pairs <= 1)
-        axis_dft_odd<T, 1>(s, tw, P, LS, TS);
-    else if (pairs <= 2)
-        axis_dft_odd<T, 2>(s, tw, P, LS, TS);
-    else if (pairs <= 4)
-        axis_dft_odd<T, 4>(s, tw, P, LS, TS);
-    else
-        axis_dft_odd<T, 8>(s, tw, P, LS, TS);
+    // FP64 keeps at most 4 output pairs per thread (register pressure); the matrix rows
+    // are padded for 8, which 4 divides
+    switch (odd_group_pairs(P)) {
+        case 1: axis_dft_odd<T, 1>(s, tw, P, LS, TS); break;
+        case 2: axis_dft_odd<T, 2>(s, tw, P, LS, TS); break;
+        case 4: axis_dft_odd<T, 4>(s, tw, P, LS, TS); break;
+        default: axis_dft_odd<T, sizeof(T) == 8 ? 4 : 8>(s, tw, P, LS, TS); break;
+    }
 }
 
 template <typename XS, typename V>
@@ -179,16 +210,16 @@ __global__ void __launch_bounds__(512) bucketize_kernel(const __grid_constant__ 
     const int tb0 = (tile % nTb) * Tb;
     const int ta0 = (tile / nTb) * Ta;
     const int TS = ps.tile_elems;
-    V* tws = s + TS;
+    V* tws = s + ((TS + 1) & ~1);  // 16-byte aligned: twiddle rows are read as 16-byte vectors
 
     // twiddles of this pass' axes
     {
         const V* twg = reinterpret_cast<const V*>(a.tw);
         int off = 0;
         for (int ax = a0; ax < a1; ++ax) {
-            const int n = st.ax[ax].pow2 ? (st.ax[ax].P >> 1) : st.ax[ax].P;
+            const int n = axis_tw_count(st.ax[ax].P, st.ax[ax].pow2);
             for (int t = threadIdx.x; t < n; t += blockDim.x) tws[off + t] = twg[st.ax[ax].tw_off + t];
-            off += n;
+            off += (n + 1) & ~1;
         }
     }
 
@@ -198,24 +229,50 @@ __global__ void __launch_bounds__(512) bucketize_kernel(const __grid_constant__ 
     const int32_t* nidx = a.nidx + st.bin_base;
     const V* scr = reinterpret_cast<const V*>(a.scratch);
 
-    for (int e = threadIdx.x; e < TS; e += blockDim.x) {
-        const int tb = e % Tb;
-        const int rest = e / Tb;
-        const int g = rest % G;
-        const int ta = rest / G;
-        const int pb = tb0 + tb, pa = ta0 + ta;
-        V v = {0, 0};
-        if (pb < Sb && pa < above) {
-            const int p = pb + Sb * g + Sab * pa;
-            if (ps.src_gather) {
-                int xi = __ldg(nidx + p) * L + tau;
-                if (xi >= N) xi -= N;
-                v = load_sample<XS, V>(x, xi);
-            } else {
-                v = __ldcg(scr + slot + p);
+    // load the tile; 8 independent loads in flight per thread
+    constexpr int U = 8;
+    for (int e0 = threadIdx.x; e0 < TS; e0 += U * blockDim.x) {
+        int pos[U];
+        int32_t src[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            int p = -1;
+            if (e < TS) {
+                if (Tb == 1 && Ta == 1) {
+                    p = e;
+                } else {
+                    const int tb = e % Tb;
+                    const int rest = e / Tb;
+                    const int g = rest % G;
+                    const int ta = rest / G;
+                    const int pb = tb0 + tb, pa = ta0 + ta;
+                    if (pb < Sb && pa < above) p = pb + Sb * g + Sab * pa;
+                }
+            }
+            pos[u] = p;
+            src[u] = 0;
+            if (p >= 0) {
+                if (ps.src_gather) {
+                    int xi = __ldg(nidx + p) * L + tau;
+                    src[u] = xi >= N ? xi - N : xi;
+                } else {
+                    src[u] = p;
+                }
             }
         }
-        s[e] = v;
+        V v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u] = V{0, 0};
+            if (pos[u] >= 0)
+                v[u] = ps.src_gather ? load_sample<XS, V>(x, src[u]) : __ldcg(scr + slot + src[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < TS) s[e] = v[u];
+        }
     }
     __syncthreads();
 
@@ -227,20 +284,24 @@ __global__ void __launch_bounds__(512) bucketize_kernel(const __grid_constant__ 
             axis_fft_pow2<T>(s, tws + off, A.P, A.log2P, LS, TS);
         else if (A.P > 1)
             axis_dft_odd_dispatch<T>(s, tws + off, A.P, LS, TS);
-        off += A.pow2 ? (A.P >> 1) : A.P;
+        off += (axis_tw_count(A.P, A.pow2) + 1) & ~1;
     }
 
     V* dst = reinterpret_cast<V*>(ps.dst_bins ? a.bins : a.scratch);
     for (int e = threadIdx.x; e < TS; e += blockDim.x) {
-        const int tb = e % Tb;
-        const int rest = e / Tb;
-        const int g = rest % G;
-        const int ta = rest / G;
-        const int pb = tb0 + tb, pa = ta0 + ta;
-        if (pb < Sb && pa < above) {
-            const int p = pb + Sb * g + Sab * pa;
-            __stcg(dst + slot + p, s[e]);
+        int p;
+        if (Tb == 1 && Ta == 1) {
+            p = e;
+        } else {
+            const int tb = e % Tb;
+            const int rest = e / Tb;
+            const int g = rest % G;
+            const int ta = rest / G;
+            const int pb = tb0 + tb, pa = ta0 + ta;
+            if (pb >= Sb || pa >= above) continue;
+            p = pb + Sb * g + Sab * pa;
         }
+        __stcg(dst + slot + p, s[e]);
     }
 }
 

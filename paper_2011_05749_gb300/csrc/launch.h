@@ -30,6 +30,7 @@ struct DecodeArgs {
     int32_t pad;
     const int32_t* pbin;  // position -> bin j, per stage at bin_base
     const int32_t* bpos;  // bin j -> position
+    const void* roots;    // L_d roots of unity of every stage, (cos, sin)(2 pi t / L_d)
     void* bins;           // complex, n_sig * y_per_sig, modified in place
 };
 
@@ -51,6 +52,9 @@ struct CompactArgs {
 // precision: 0 = double arithmetic, 1 = float; xdouble: input/output complex128
 cudaError_t launch_bucketize(const BucketArgs& a, int precision, int xdouble, int threads,
                              size_t smem, cudaStream_t st);
+// round 1 of the decoder (classification of every bin) over all signals
+cudaError_t launch_classify(const DecodeArgs& a, int precision, cudaStream_t st);
+// peeling rounds, G CTAs per signal (cooperative when G > 1)
 cudaError_t launch_decode(const DecodeArgs& a, int precision, int threads, bool cooperative,
                           cudaStream_t st);
 cudaError_t launch_compact(const CompactArgs& a, int precision, int xdouble, int threads,

@@ -25,6 +25,7 @@
 #include <mutex>
 
 #include "launch.h"
+#include "pfa_layout.h"
 #include "sfft.h"
 #include "sfft_internal.cuh"
 
@@ -44,77 +45,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
 int g_max_smem[kMaxDevices] = {};
-
-int64_t gcd_i(int64_t a, int64_t b)
-{
-    while (b) {
-        const int64_t t = a % b;
-        a = b;
-        b = t;
-    }
-    return a;
-}
-
-int64_t inv_mod(int64_t a, int64_t m)
-{
-    if (m == 1) return 0;
-    int64_t g = m, x = 0, x1 = 1, b = a % m;
-    while (b) {
-        const int64_t q = g / b;
-        int64_t t = g - q * b;
-        g = b;
-        b = t;
-        t = x - q * x1;
-        x = x1;
-        x1 = t;
-    }
-    x %= m;
-    return x < 0 ? x + m : x;
-}
-
-// Prime-power factors of B, odd ones ascending, the power of two last; fixed arrays only.
-int prime_powers(int64_t B, int32_t* out, int cap)
-{
-    int n = 0, pw2 = 1;
-    while (B % 2 == 0) {
-        B /= 2;
-        pw2 *= 2;
-    }
-    for (int64_t p = 3; p * p <= B; p += 2) {
-        if (B % p) continue;
-        int64_t q = 1;
-        while (B % p == 0) {
-            B /= p;
-            q *= p;
-        }
-        if (n == cap) return -1;
-        out[n++] = (int32_t)q;
-    }
-    if (B > 1) {
-        if (n == cap) return -1;
-        out[n++] = (int32_t)B;
-    }
-    // ascending odd factors (insertion sort)
-    for (int i = 1; i < n; ++i)
-        for (int k = i; k > 0 && out[k - 1] > out[k]; --k) {
-            const int32_t t = out[k];
-            out[k] = out[k - 1];
-            out[k - 1] = t;
-        }
-    if (pw2 > 1) {
-        if (n == cap) return -1;
-        out[n++] = pw2;
-    }
-    if (n == 0) out[n++] = 1;
-    return n;
-}
-
-int ceil_log2(int v)
-{
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
-}
 
 // Tables of one call, computed on the device from the description: input sample index and
 // bin of every storage position, and the twiddles of every axis.
@@ -139,14 +69,15 @@ __global__ void static_tables_kernel(const __grid_constant__ PlanDesc pd, int32_
         pbin[i] = (int32_t)(j % s.B);
     }
     if (i < n_tw) {
-        // locate the axis owning twiddle slot i
+        // the axis owning twiddle slot i (layout of axis_tw_residue)
         for (int d = 0; d < pd.D; ++d)
             for (int a = 0; a < pd.st[d].n_axes; ++a) {
                 const AxisDesc& A = pd.st[d].ax[a];
-                const int cnt = A.pow2 ? A.P / 2 : A.P;
+                const int cnt = axis_tw_count(A.P, A.pow2);
                 if (i >= A.tw_off && i < A.tw_off + cnt) {
                     double sv, cv;
-                    sincospi(2.0 * (double)(i - A.tw_off) / (double)A.P, &sv, &cv);
+                    const int32_t t = axis_tw_residue(A.P, A.pow2, (int)(i - A.tw_off));
+                    sincospi(2.0 * (double)t / (double)A.P, &sv, &cv);
                     tw[i] = typename C2<T>::t{(T)cv, (T)sv};
                 }
             }
@@ -195,7 +126,7 @@ extern "C" int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t*
     for (int d = 0; d < n_stages; ++d) {
         if (f[d] < 1 || N % f[d] != 0) return SFFT_EINVAL;
         for (int e = 0; e < d; ++e)
-            if (gcd_i(f[d], f[e]) != 1) return SFFT_EINVAL;
+            if (pfa_gcd(f[d], f[e]) != 1) return SFFT_EINVAL;
         for (int r = 0; r < n_delays; ++r) {
             const int64_t t = delays[(int64_t)d * n_delays + r];
             if (t < 0 || t >= N) return SFFT_EINVAL;
@@ -207,9 +138,9 @@ extern "C" int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t*
     const size_t esz = prec ? 8 : 16;
     int64_t sumB = 0;
     for (int d = 0; d < n_stages; ++d) sumB += N / f[d];
-    // size check before any device work: tables, twiddles (<= 2 B per stage), two bin arrays
-    const size_t need = up256(4 * (size_t)sumB) * 2 + up256(esz * 2 * (size_t)sumB) +
-                        2 * up256(esz * (size_t)sumB * n_delays);
+    // size check before any device work (index tables and the two bin arrays; the exact
+    // check, twiddles included, follows the layout below)
+    const size_t need = up256(4 * (size_t)sumB) * 2 + 2 * up256(esz * (size_t)sumB * n_delays);
     if (need > kStaticBytes) return SFFT_ETOOBIG;
 
     void* base = nullptr;
@@ -226,102 +157,22 @@ extern "C" int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t*
     pd.D = n_stages;
     pd.R = n_delays;
     pd.K = 1;
-    const int64_t max_elems = ((int64_t)max_smem - 12 * 1024) / (int64_t)esz;
     const int64_t tile_target = prec ? 4096 : 2048;
     int32_t n_tw = 0, bin_base = 0;
-    size_t smem1 = 0, smem2 = 0;
-    int64_t tile1 = 0, tile2 = 0;
+    PassPlan l1, l2;
     bool two = false;
     for (int d = 0; d < n_stages; ++d) {
         StageDesc& s = pd.st[d];
         const int64_t L = f[d], B = N / L;
         s.B = (int32_t)B;
         s.L = (int32_t)L;
-        int32_t Ps[kMaxAxes];
-        const int n = prime_powers(B, Ps, kMaxAxes);
-        if (n < 0) return SFFT_EINVAL;
-        for (int i = 0; i < n; ++i)
-            if ((Ps[i] & (Ps[i] - 1)) != 0 && Ps[i] > 2049) return SFFT_EINVAL;
-        // split: one pass when B fits in shared memory, else the most balanced 2-group split
-        int split = n;
-        int32_t order[kMaxAxes];
-        for (int i = 0; i < n; ++i) order[i] = Ps[i];
-        if (B > max_elems) {
-            int64_t best = -1;
-            unsigned best_mask = 0;
-            for (unsigned mask = 1; mask + 1 < (1u << n); ++mask) {
-                int64_t pi = 1;
-                for (int i = 0; i < n; ++i)
-                    if (mask >> i & 1) pi *= Ps[i];
-                const int64_t po = B / pi;
-                if (pi > max_elems || po > max_elems) continue;
-                const int64_t worst = pi > po ? pi : po;
-                if (best < 0 || worst < best) {
-                    best = worst;
-                    best_mask = mask;
-                }
-            }
-            if (best < 0) return SFFT_EINVAL;
-            int k = 0;
-            for (int i = 0; i < n; ++i)
-                if (best_mask >> i & 1) order[k++] = Ps[i];
-            split = k;
-            for (int i = 0; i < n; ++i)
-                if (!(best_mask >> i & 1)) order[k++] = Ps[i];
-        }
-        s.n_axes = n;
-        s.split = split;
-        int32_t S = 1;
-        for (int i = 0; i < n; ++i) {
-            AxisDesc& A = s.ax[i];
-            A.P = order[i];
-            A.pow2 = (A.P > 1 && (A.P & (A.P - 1)) == 0) ? 1 : 0;
-            A.log2P = A.pow2 ? ceil_log2(A.P) : 0;
-            A.S = S;
-            S *= A.P;
-            const int64_t Bp = B / A.P;
-            A.rur = (int32_t)(Bp % B);
-            A.crt = (int32_t)((Bp * inv_mod(Bp % A.P, A.P)) % B);
-            A.tw_off = n_tw;
-            n_tw += A.pow2 ? A.P / 2 : A.P;
-        }
+        if (!pfa_layout_stage(&s, esz, max_smem, tile_target, &a.pass[d], &pass2[d], &l1, &l2,
+                              &n_tw, &two))
+            return SFFT_EINVAL;
         for (int r = 0; r < n_delays; ++r) s.tau[r] = (int32_t)delays[(int64_t)d * n_delays + r];
         s.r0 = s.r1 = -1;
         s.bin_base = bin_base;
         s.y_off = bin_base * n_delays;
-        int64_t tw_all = 0, tw_in = 0, tw_out = 0;
-        for (int i = 0; i < n; ++i) {
-            const int64_t c = s.ax[i].pow2 ? s.ax[i].P / 2 : s.ax[i].P;
-            tw_all += c;
-            (i < split ? tw_in : tw_out) += c;
-        }
-        PassDesc& p1 = a.pass[d];
-        if (split == n) {
-            p1 = PassDesc{0, n, 1, 1, 1, (int32_t)B, 1, 1};
-            if ((size_t)(B + tw_all) * esz > smem1) smem1 = (size_t)(B + tw_all) * esz;
-            if (B > tile1) tile1 = B;
-        } else {
-            two = true;
-            int64_t inner = 1, outer = 1;
-            for (int i = 0; i < split; ++i) inner *= s.ax[i].P;
-            for (int i = split; i < n; ++i) outer *= s.ax[i].P;
-            int64_t Tb = tile_target / outer;
-            if (Tb < 1) Tb = 1;
-            if (Tb > inner) Tb = inner;
-            while (Tb > 1 && Tb * outer > max_elems) --Tb;
-            int64_t Ta = tile_target / inner;
-            if (Ta < 1) Ta = 1;
-            if (Ta > outer) Ta = outer;
-            while (Ta > 1 && Ta * inner > max_elems) --Ta;
-            p1 = PassDesc{split, n, (int32_t)Tb, 1, (int32_t)((inner + Tb - 1) / Tb),
-                          (int32_t)(Tb * outer), 1, 0};
-            pass2[d] = PassDesc{0, split, 1, (int32_t)Ta, (int32_t)((outer + Ta - 1) / Ta),
-                                (int32_t)(inner * Ta), 0, 1};
-            if ((size_t)(Tb * outer + tw_out) * esz > smem1) smem1 = (size_t)(Tb * outer + tw_out) * esz;
-            if ((size_t)(inner * Ta + tw_in) * esz > smem2) smem2 = (size_t)(inner * Ta + tw_in) * esz;
-            if (Tb * outer > tile1) tile1 = Tb * outer;
-            if (inner * Ta > tile2) tile2 = inner * Ta;
-        }
         bin_base += (int32_t)B;
     }
     pd.sumB = bin_base;
@@ -357,10 +208,6 @@ extern "C" int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t*
     a.x0 = x;
     a.scratch = scratch;
     a.bins = sbins;
-    auto pick_threads = [](int64_t tile) {
-        int64_t t = (tile / 8 + 31) / 32 * 32;
-        return (int)(t < 128 ? 128 : (t > 512 ? 512 : t));
-    };
     for (int pass = 0; pass < (two ? 2 : 1); ++pass) {
         if (pass == 1)
             for (int d = 0; d < kMaxStages; ++d) a.pass[d] = d < n_stages ? pass2[d] : PassDesc{};
@@ -369,7 +216,7 @@ extern "C" int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t*
             a.tile_prefix[d + 1] = a.tile_prefix[d] + (d < n_stages ? a.pass[d].n_tiles * n_delays : 0);
         a.tiles_per_sig = a.tile_prefix[kMaxStages];
         e = launch_bucketize(a, prec, dtype == SFFT_C128 ? 1 : 0,
-                             pick_threads(pass == 0 ? tile1 : tile2), pass == 0 ? smem1 : smem2, st);
+                             pfa_threads(pass == 0 ? l1.tile : l2.tile), pass == 0 ? l1.smem : l2.smem, st);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     e = launch_bins_to_natural(pd, pbin, sbins, bins, prec, 1, st);

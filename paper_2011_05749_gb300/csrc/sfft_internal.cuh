@@ -50,9 +50,13 @@ struct StageDesc {
     int32_t n_axes, split;   // axes [0, split) inner group, [split, n_axes) outer group
     AxisDesc ax[kMaxAxes];
     int32_t tau[kMaxDelays];
+    int32_t tauL[kMaxDelays];  // tau mod L: candidate q of a bin shifts delay r's phase by
+                               // e^{2 pi i q tauL_r / L}
     int32_t bin_base;        // sum of B of earlier stages
     int32_t y_off;           // R * bin_base
     int32_t r0, r1;          // delay slots holding tau = 0 and tau = 1 (-1 if absent)
+    int32_t root_off;        // offset of the L roots of unity (cos, sin)(2 pi t / L)
+    int32_t pad;
     double T0, T1;           // thresholds on sum_r |Y_r|^2 and on the single-tone residual
 };
 
@@ -64,9 +68,36 @@ struct PlanDesc {
     int32_t locate;          // 0 ARG, 1 ML
     int32_t max_rounds;
     int32_t K;
-    int32_t pad;
+    int32_t root_total;      // sum_d L_d: root-table entries (at st[0].root_off onwards)
     StageDesc st[kMaxStages];
 };
+
+// Twiddles of one axis in the plan table, as residues t of e^{2 pi i t / P}:
+//   power of two: W^t for t < P/2 (radix-2 butterflies);
+//   odd P: the (P-1)/2 x KP matrix of t = (n k) mod P, n, k = 1..(P-1)/2, rows padded to
+//   KP = a multiple of the output pairs one thread computes (padding entries t = 0).
+__host__ __device__ __forceinline__ int odd_group_pairs(int P)
+{
+    const int pairs = (P - 1) >> 1;
+    return pairs <= 1 ? 1 : pairs <= 2 ? 2 : pairs <= 4 ? 4 : 8;
+}
+__host__ __device__ __forceinline__ int odd_row_len(int P)
+{
+    const int pairs = (P - 1) >> 1, gp = odd_group_pairs(P);
+    return (pairs + gp - 1) / gp * gp;
+}
+__host__ __device__ __forceinline__ int axis_tw_count(int P, int pow2)
+{
+    if (P <= 1) return 0;
+    return pow2 ? (P >> 1) : ((P - 1) >> 1) * odd_row_len(P);
+}
+__host__ __device__ __forceinline__ int32_t axis_tw_residue(int P, int pow2, int i)
+{
+    if (pow2) return i;
+    const int kp = odd_row_len(P), pairs = (P - 1) >> 1;
+    const int n = i / kp + 1, k = i % kp + 1;
+    return k > pairs ? 0 : (int32_t)(((int64_t)n * k) % P);
+}
 
 // Decode workspace of one signal slot (all arrays sumB entries unless stated).
 struct DecodeWs {
