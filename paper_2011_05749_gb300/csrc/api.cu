@@ -111,6 +111,9 @@ static void free_plan_memory(sfft_plan_s* p)
         cudaEventDestroy(e.b);
     }
     for (auto e : p->prof_pool) cudaEventDestroy(e);
+    for (int i = 0; i < 2; ++i)
+        if (p->aux[i]) cudaStreamDestroy(p->aux[i]);
+    if (p->aux_ev) cudaEventDestroy(p->aux_ev);
 }
 
 extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t n_stages,
@@ -165,6 +168,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     pd.locate = o.locate;
     pd.max_rounds = o.max_rounds;
     pd.K = K;
+    pd.invN = 1.0 / (double)N;
+    pd.mu = ~0ull / (uint64_t)N;
 
     std::vector<int32_t> h_nidx, h_pbin, h_bpos, tw_P, tw_t;
     int64_t bin_base = 0;
@@ -186,7 +191,9 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         for (int r = 0; r < n_delays; ++r) {
             s.tau[r] = (int32_t)delays[(int64_t)d * n_delays + r];
             s.tauL[r] = (int32_t)(delays[(int64_t)d * n_delays + r] % L);
+            s.step32[r] = (int32_t)((32 * (int64_t)s.tauL[r]) % L);
         }
+        s.invL = 1.0f / (float)L;
         s.r0 = s.r1 = -1;
         for (int r = 0; r < n_delays; ++r) {
             if (s.tau[r] == 0 && s.r0 < 0) s.r0 = r;
@@ -204,6 +211,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         const double fl = eta * (double)B * o.a_min;
         s.T0 = (double)n_delays * (o.c0 * sig_y + fl * fl);
         s.T1 = (double)n_delays * (o.c1 * sig_y + fl * fl);
+        s.T0f = (float)s.T0;
+        s.T1f = (float)s.T1;
 
         // index maps
         const size_t base = h_nidx.size();
@@ -259,8 +268,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     pd.y_per_sig = (int64_t)bin_base * n_delays;
     p->smem1 = l1.smem;
     p->smem2 = l2.smem;
-    p->threads1 = pfa_threads(l1.tile);
-    p->threads2 = pfa_threads(l2.tile);
+    p->threads1 = pfa_threads(l1.tile, p->esz);
+    p->threads2 = pfa_threads(l2.tile, p->esz);
 
     // device memory
     const size_t nb = (size_t)pd.sumB, mb = (size_t)p->max_batch;
@@ -397,17 +406,43 @@ struct PhaseScope {
     }
 };
 
-// Enqueue the whole path for n signals of one plan (n <= max_batch).  xs/out pointer
-// tables are already on the device when n > 1 (d_tab != nullptr).
+// Workspace of slots [slot0, slot0 + n): decode arrays, counters
+static DecodeWs ws_at(const sfft_plan_s* p, int slot0)
+{
+    DecodeWs w = p->ws;
+    const size_t so = (size_t)slot0 * p->pd.sumB;
+    w.state += so;
+    w.dirty += so;
+    w.cand += so;
+    w.list0 += so;
+    w.list1 += so;
+    w.nzl += so;
+    w.cbin += so;
+    w.cf += so;
+    w.cv = (unsigned char*)w.cv + so * p->esz;
+    w.rec_f += so;
+    w.rec_v = (unsigned char*)w.rec_v + so * p->esz;
+    w.ctr += (size_t)slot0 * p->ctr_stride;
+    return w;
+}
+
+// Enqueue the whole path for n signals of one plan in workspace slots [slot0, slot0 + n)
+// (slot0 + n <= max_batch).  For n > 1 the signal and output pointers come from device
+// tables d_xs / d_idx / d_val; for n == 1 from x0 / idx0 / val0.  The decode counters of
+// the slots are zero on entry (plan creation zeroes them, every compaction re-zeroes
+// them after reading).
 int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
               int64_t* idx0, void* val0, int64_t* const* d_idx, void* const* d_val,
-              int32_t* infos, const void* bins_in, cudaStream_t st)
+              int32_t* infos, const void* bins_in, cudaStream_t st, int slot0 = 0)
 {
     PlanDesc& pd = p->pd;
-    CK(cudaMemsetAsync(p->ws.ctr, 0, p->ctr_bytes_per_sig * n, st));
+    void* bins = (unsigned char*)p->d_bins + (size_t)slot0 * pd.y_per_sig * p->esz;
+    void* scratch = p->d_scratch ? (unsigned char*)p->d_scratch + (size_t)slot0 * pd.y_per_sig * p->esz
+                                 : nullptr;
+    const DecodeWs ws = ws_at(p, slot0);
     if (bins_in) {
         // caller-supplied natural-order bins (sfft_decode_bins): permute to storage order
-        CK(launch_bins_to_natural(pd, p->d_pbin, bins_in, p->d_bins, p->prec, 0, st));
+        CK(launch_bins_to_natural(pd, p->d_pbin, bins_in, bins, p->prec, 0, st));
     } else {
         PhaseScope ps(p, st, 0, p->need_pass2 ? 2 : 1);
         BucketArgs a;
@@ -418,8 +453,8 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
         a.tw = p->d_tw;
         a.xs = d_xs;
         a.x0 = x0;
-        a.scratch = p->d_scratch;
-        a.bins = p->d_bins;
+        a.scratch = scratch;
+        a.bins = bins;
         for (int pass = 0; pass < (p->need_pass2 ? 2 : 1); ++pass) {
             const PassDesc* src = pass == 0 ? p->pass1 : p->pass2;
             a.tile_prefix[0] = 0;
@@ -435,12 +470,12 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     DecodeArgs da;
     memset(&da, 0, sizeof(da));
     da.pd = pd;
-    da.ws = p->ws;
+    da.ws = ws;
     da.ctr_stride = p->ctr_stride;
     da.n_sig = n;
     da.pbin = p->d_pbin;
     da.bpos = p->d_bpos;
-    da.bins = p->d_bins;
+    da.bins = bins;
     da.roots = (const unsigned char*)p->d_tw + (size_t)pd.st[0].root_off * p->esz;
     const int threads = 512;
     const int total = p->num_sms * p->decode_occ;
@@ -460,12 +495,12 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     CompactArgs ca;
     memset(&ca, 0, sizeof(ca));
     ca.pd = pd;
-    ca.ws = p->ws;
+    ca.ws = ws;
     ca.ctr_stride = p->ctr_stride;
     ca.n_sig = n;
     ca.sort_cap = p->sort_cap;
     ca.smem_cap = p->smem_cap;
-    ca.sortbuf = p->d_sortbuf;
+    ca.sortbuf = p->d_sortbuf + (size_t)slot0 * 2 * p->sort_cap;
     ca.out_idx = d_idx;
     ca.out_val = d_val;
     ca.infos = infos;
@@ -523,60 +558,114 @@ extern "C" int sfft_execute(sfft_plan_t p, const void* x, int64_t* out_idx, void
 }
 
 namespace sfft {
-// n signals of one plan, device buffers; host buffers when `host` (staged per chunk)
-int execute_group(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
-                  void* const* val, int32_t* infos, cudaStream_t st, bool host = false)
+
+static int fill_ptr_table(sfft_plan_s* p, int m, const void* const* xs, int64_t* const* idx,
+                          void* const* val, cudaStream_t st)
+{
+    const int slot = p->ptr_slot;
+    p->ptr_slot ^= 1;
+    CK(cudaEventSynchronize(p->ptr_ev[slot]));
+    void** h = p->h_ptrs[slot];
+    const size_t mb = (size_t)p->max_batch;
+    for (int i = 0; i < m; ++i) {
+        h[i] = (void*)xs[i];
+        h[mb + i] = (void*)idx[i];
+        h[2 * mb + i] = val[i];
+    }
+    CK(cudaMemcpyAsync(p->d_ptrs, h, 3 * sizeof(void*) * mb, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(p->ptr_ev[slot], st));
+    return SFFT_OK;
+}
+
+// n signals of one plan with device buffers, max_batch per launch group
+static int execute_group_device(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
+                                void* const* val, int32_t* infos, cudaStream_t st)
+{
+    const size_t mb = (size_t)p->max_batch;
+    for (int c0 = 0; c0 < n; c0 += p->max_batch) {
+        const int m = std::min(p->max_batch, n - c0);
+        int rc;
+        if (m == 1) {
+            rc = run_chunk(p, 1, xs[c0], nullptr, idx[c0], val[c0], nullptr, nullptr, infos + 4 * c0,
+                           nullptr, st);
+        } else {
+            if ((rc = fill_ptr_table(p, m, xs + c0, idx + c0, val + c0, st))) return rc;
+            rc = run_chunk(p, m, nullptr, (const void* const*)p->d_ptrs, nullptr, nullptr,
+                           (int64_t* const*)(p->d_ptrs + mb), (void* const*)(p->d_ptrs + 2 * mb),
+                           infos + 4 * c0, nullptr, st);
+        }
+        if (rc) return rc;
+    }
+    return SFFT_OK;
+}
+
+// n signals of one plan with host buffers: each launch group is split into sub-batches
+// that alternate between two streams, so the copies of one sub-batch overlap the kernels
+// of the other; the call returns when every output is in host memory.
+static int execute_group_host(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
+                              void* const* val, int32_t* infos, cudaStream_t st)
 {
     const size_t mb = (size_t)p->max_batch;
     const size_t xb = (size_t)p->pd.N * p->xesz;
     const size_t ib = align_up((size_t)p->pd.K * 8, 256), vb = align_up((size_t)p->pd.K * p->xesz, 256);
-    if (host) {
-        if (!p->d_xb_stage) CK(cudaMalloc(&p->d_xb_stage, xb * mb));
-        if (!p->d_ob_stage) CK(cudaMalloc(&p->d_ob_stage, (ib + vb) * mb + 16 * mb));
+    if (!p->d_xb_stage) CK(cudaMalloc(&p->d_xb_stage, xb * mb));
+    if (!p->d_ob_stage) CK(cudaMalloc(&p->d_ob_stage, (ib + vb) * mb + 16 * mb));
+    for (int i = 0; i < 2; ++i)
+        if (!p->aux[i]) CK(cudaStreamCreateWithFlags(&p->aux[i], cudaStreamNonBlocking));
+    if (!p->aux_ev) CK(cudaEventCreateWithFlags(&p->aux_ev, cudaEventDisableTiming));
+    unsigned char* ob = (unsigned char*)p->d_ob_stage;
+    int32_t* dinf = (int32_t*)(ob + (ib + vb) * mb);
+    std::vector<const void*> sx(mb);
+    std::vector<int64_t*> si(mb);
+    std::vector<void*> sv(mb);
+    for (size_t i = 0; i < mb; ++i) {
+        sx[i] = (unsigned char*)p->d_xb_stage + xb * i;
+        si[i] = (int64_t*)(ob + ib * i);
+        sv[i] = ob + ib * mb + vb * i;
     }
+    // the staging pointer table is the same for every group
+    CK(cudaEventRecord(p->aux_ev, st));
+    CK(cudaStreamWaitEvent(p->aux[0], p->aux_ev, 0));
+    CK(cudaStreamWaitEvent(p->aux[1], p->aux_ev, 0));
+    int rc = fill_ptr_table(p, (int)mb, sx.data(), si.data(), sv.data(), p->aux[0]);
+    if (rc) return rc;
+    CK(cudaEventRecord(p->aux_ev, p->aux[0]));
+    CK(cudaStreamWaitEvent(p->aux[1], p->aux_ev, 0));
     for (int c0 = 0; c0 < n; c0 += p->max_batch) {
         const int m = std::min(p->max_batch, n - c0);
-        unsigned char* ob = (unsigned char*)p->d_ob_stage;
-        int32_t* dinf = host ? (int32_t*)(ob + (ib + vb) * mb) : infos + 4 * c0;
-        auto dx = [&](int i) -> const void* {
-            return host ? (const void*)((unsigned char*)p->d_xb_stage + xb * i) : xs[c0 + i];
-        };
-        auto di = [&](int i) -> int64_t* { return host ? (int64_t*)(ob + ib * i) : idx[c0 + i]; };
-        auto dv = [&](int i) -> void* { return host ? (void*)(ob + ib * mb + vb * i) : val[c0 + i]; };
-        if (host)
-            for (int i = 0; i < m; ++i)
-                CK(cudaMemcpyAsync((void*)dx(i), xs[c0 + i], xb, cudaMemcpyHostToDevice, st));
-        int rc;
-        if (m == 1) {
-            rc = run_chunk(p, 1, dx(0), nullptr, di(0), dv(0), nullptr, nullptr, dinf, nullptr, st);
-        } else {
-            const int slot = p->ptr_slot;
-            p->ptr_slot ^= 1;
-            CK(cudaEventSynchronize(p->ptr_ev[slot]));
-            void** h = p->h_ptrs[slot];
-            for (int i = 0; i < m; ++i) {
-                h[i] = (void*)dx(i);
-                h[mb + i] = (void*)di(i);
-                h[2 * mb + i] = dv(i);
+        const int nsub = std::min(m, 4);
+        for (int h = 0; h < nsub; ++h) {
+            const int s0 = m * h / nsub, s1 = m * (h + 1) / nsub, ms = s1 - s0;
+            if (ms <= 0) continue;
+            cudaStream_t ss = p->aux[h & 1];
+            for (int i = s0; i < s1; ++i)
+                CK(cudaMemcpyAsync((void*)sx[i], xs[c0 + i], xb, cudaMemcpyHostToDevice, ss));
+            if (ms == 1)
+                rc = run_chunk(p, 1, sx[s0], nullptr, si[s0], sv[s0], nullptr, nullptr, dinf + 4 * s0,
+                               nullptr, ss, s0);
+            else
+                rc = run_chunk(p, ms, nullptr, (const void* const*)p->d_ptrs + s0, nullptr, nullptr,
+                               (int64_t* const*)(p->d_ptrs + mb + s0), (void* const*)(p->d_ptrs + 2 * mb + s0),
+                               dinf + 4 * s0, nullptr, ss, s0);
+            if (rc) return rc;
+            for (int i = s0; i < s1; ++i) {
+                CK(cudaMemcpyAsync(idx[c0 + i], si[i], (size_t)p->pd.K * 8, cudaMemcpyDeviceToHost, ss));
+                CK(cudaMemcpyAsync(val[c0 + i], sv[i], (size_t)p->pd.K * p->xesz, cudaMemcpyDeviceToHost, ss));
             }
-            CK(cudaMemcpyAsync(p->d_ptrs, h, 3 * sizeof(void*) * mb, cudaMemcpyHostToDevice, st));
-            CK(cudaEventRecord(p->ptr_ev[slot], st));
-            rc = run_chunk(p, m, nullptr, (const void* const*)p->d_ptrs, nullptr, nullptr,
-                           (int64_t* const*)(p->d_ptrs + mb), (void* const*)(p->d_ptrs + 2 * mb),
-                           dinf, nullptr, st);
+            CK(cudaMemcpyAsync(infos + 4 * (c0 + s0), dinf + 4 * s0, 16 * (size_t)ms, cudaMemcpyDeviceToHost, ss));
         }
-        if (rc) return rc;
-        if (host) {
-            for (int i = 0; i < m; ++i) {
-                CK(cudaMemcpyAsync(idx[c0 + i], di(i), (size_t)p->pd.K * 8, cudaMemcpyDeviceToHost, st));
-                CK(cudaMemcpyAsync(val[c0 + i], dv(i), (size_t)p->pd.K * p->xesz, cudaMemcpyDeviceToHost, st));
-            }
-            CK(cudaMemcpyAsync(infos + 4 * c0, dinf, 16 * (size_t)m, cudaMemcpyDeviceToHost, st));
-            // the staging buffers are reused by the next chunk: finish this one first
-            CK(cudaStreamSynchronize(st));
-        }
+        // the staging buffers are reused by the next launch group
+        CK(cudaStreamSynchronize(p->aux[0]));
+        CK(cudaStreamSynchronize(p->aux[1]));
     }
     return SFFT_OK;
+}
+
+int execute_group(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
+                  void* const* val, int32_t* infos, cudaStream_t st, bool host = false)
+{
+    return host ? execute_group_host(p, n, xs, idx, val, infos, st)
+                : execute_group_device(p, n, xs, idx, val, infos, st);
 }
 }  // namespace sfft
 

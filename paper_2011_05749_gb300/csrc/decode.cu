@@ -95,10 +95,35 @@ __device__ __forceinline__ double2 unit_twiddle(int64_t m, int32_t N, double)
     return double2{cv, sv};
 }
 
-template <typename T>
-__device__ __forceinline__ typename C2<T>::t delay_phasor(int64_t f, int32_t tau, int32_t N)
+// (a b) mod N for 0 <= a, b < N < 2^30 by Barrett reduction with mu = floor((2^64-1)/N):
+// the estimated quotient is at most two below the true one, so two corrections suffice
+__device__ __forceinline__ int64_t mulmod(int64_t a, int64_t b, const PlanDesc& pd)
 {
-    return unit_twiddle((f * (int64_t)tau) % N, N, T(0));
+    const uint64_t p = (uint64_t)a * (uint64_t)b;
+    const uint64_t q = __umul64hi(p, pd.mu);
+    uint64_t r = p - q * (uint64_t)pd.N;
+    if (r >= (uint64_t)pd.N) r -= pd.N;
+    if (r >= (uint64_t)pd.N) r -= pd.N;
+    return (int64_t)r;
+}
+
+// threshold test in the path's arithmetic type
+__device__ __forceinline__ bool below(float v, float tf, double) { return v <= tf; }
+__device__ __forceinline__ bool below(double v, float, double td) { return v <= td; }
+
+// v mod L for 0 <= v < 2^20, with a float reciprocal and one correction each way
+__device__ __forceinline__ int small_mod(int v, int L, float invL)
+{
+    int r = v - (int)((float)v * invL) * L;
+    if (r < 0) r += L;
+    if (r >= L) r -= L;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t delay_phasor(const PlanDesc& pd, int64_t f, int32_t tau)
+{
+    return unit_twiddle(mulmod(f, tau, pd), pd.N, T(0));
 }
 
 template <typename T>
@@ -136,33 +161,47 @@ __device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     V z = {0, 0};
     if (lane < R) {
         const V y = __ldcg(Y + st.y_off + (int64_t)lane * B + (b - st.bin_base));
-        const V aj = delay_phasor<T>(j, st.tau[lane], N);
+        const V aj = delay_phasor<T>(pd, j, st.tau[lane]);
         z = V{y.x * aj.x + y.y * aj.y, y.y * aj.x - y.x * aj.y};
     }
     T zx[kMaxDelays], zy[kMaxDelays];
     int idx[kMaxDelays], step[kMaxDelays];
 #pragma unroll
     for (int r = 0; r < kMaxDelays; ++r) {
-        zx[r] = __shfl_sync(0xffffffffu, z.x, r);
-        zy[r] = __shfl_sync(0xffffffffu, z.y, r);
-        const int t = r < R ? st.tauL[r] : 0;
-        idx[r] = (lane * t) % L;
-        step[r] = (32 * t) % L;
+        zx[r] = 0;
+        zy[r] = 0;
+        idx[r] = 0;
+        step[r] = 0;
+        if (r < R) {
+            zx[r] = __shfl_sync(0xffffffffu, z.x, r);
+            zy[r] = __shfl_sync(0xffffffffu, z.y, r);
+            idx[r] = small_mod(lane * st.tauL[r], L, st.invL);
+            step[r] = st.step32[r];
+        }
     }
     T best = (T)-1;
     int bq = 0;
     for (int q = lane; q < L; q += 32) {
-        T cx = 0, cy = 0;
+        // two partial sums (even / odd delays) halve the dependency chain
+        T cx0 = 0, cy0 = 0, cx1 = 0, cy1 = 0;
 #pragma unroll
-        for (int r = 0; r < kMaxDelays; ++r) {
+        for (int r = 0; r < kMaxDelays; r += 2) {
             if (r < R) {
                 const V wv = wl[idx[r]];
-                cx += zx[r] * wv.x + zy[r] * wv.y;
-                cy += zy[r] * wv.x - zx[r] * wv.y;
+                cx0 += zx[r] * wv.x + zy[r] * wv.y;
+                cy0 += zy[r] * wv.x - zx[r] * wv.y;
                 const int ni = idx[r] + step[r];
                 idx[r] = ni >= L ? ni - L : ni;
             }
+            if (r + 1 < R) {
+                const V wv = wl[idx[r + 1]];
+                cx1 += zx[r + 1] * wv.x + zy[r + 1] * wv.y;
+                cy1 += zy[r + 1] * wv.x - zx[r + 1] * wv.y;
+                const int ni = idx[r + 1] + step[r + 1];
+                idx[r + 1] = ni >= L ? ni - L : ni;
+            }
         }
+        const T cx = cx0 + cx1, cy = cy0 + cy1;
         const T sc = cx * cx + cy * cy;
         if (sc > best) {
             best = sc;
@@ -181,7 +220,7 @@ __device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     const int64_t f = (int64_t)j + (int64_t)bq * B;
     V e = {1, 0}, c = {0, 0};
     if (lane < R) {
-        e = wl[(int)(((int64_t)bq * st.tauL[lane]) % L)];
+        e = wl[small_mod(bq * st.tauL[lane], L, st.invL)];
         c = V{z.x * e.x + z.y * e.y, z.y * e.x - z.x * e.y};
     }
 #pragma unroll
@@ -199,7 +238,7 @@ __device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-    if (lane == 0 && (double)e2 <= st.T1) record_candidate<T>(ctr, w, round, b, f, v);
+    if (lane == 0 && below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
 }
 
 // D2, ARG locate (FFAST, Sec. 3.2 subproblem 2): f from the phase of Y(1) conj(Y(0)) in
@@ -227,7 +266,7 @@ __device__ void locate_arg_thread(const DecodeArgs& a, int32_t* ctr, const Decod
     const int64_t f = (int64_t)j + q * B;
     V c = {0, 0};
     for (int r = 0; r < R; ++r) {
-        const V ar = delay_phasor<T>(f, st.tau[r], N);
+        const V ar = delay_phasor<T>(pd, f, st.tau[r]);
         const V y = __ldcg(Yb + (int64_t)r * B);
         c.x += y.x * ar.x + y.y * ar.y;
         c.y += y.y * ar.x - y.x * ar.y;
@@ -236,13 +275,13 @@ __device__ void locate_arg_thread(const DecodeArgs& a, int32_t* ctr, const Decod
     const V v = {c.x * sc, c.y * sc};
     T e2 = 0;
     for (int r = 0; r < R; ++r) {
-        const V ar = delay_phasor<T>(f, st.tau[r], N);
+        const V ar = delay_phasor<T>(pd, f, st.tau[r]);
         const V y = __ldcg(Yb + (int64_t)r * B);
         const T ex = y.x - (T)B * (v.x * ar.x - v.y * ar.y);
         const T ey = y.y - (T)B * (v.x * ar.y + v.y * ar.x);
         e2 += ex * ex + ey * ey;
     }
-    if ((double)e2 <= st.T1) record_candidate<T>(ctr, w, round, b, f, v);
+    if (below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
 }
 
 __device__ __forceinline__ void atomic_sub_c(float2* p, float2 d)
@@ -270,7 +309,7 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     for (int e = 0; e < pd.D; ++e) {
         if (e == d) continue;
         const StageDesc& se = pd.st[e];
-        const int je = (int)(f % se.B);
+        const int je = (int)((uint32_t)f % (uint32_t)se.B);
         const int be = se.bin_base + __ldg(a.bpos + se.bin_base + je);
         const int64_t cw = (int64_t)__ldcg((const long long*)w.cand + be);
         if (cw >= 0 && (cw & kFMask) == f) {
@@ -283,12 +322,12 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     reinterpret_cast<V*>(w.rec_v)[k] = v;
     for (int e = 0; e < pd.D; ++e) {
         const StageDesc& se = pd.st[e];
-        const int je = (int)(f % se.B);
+        const int je = (int)((uint32_t)f % (uint32_t)se.B);
         const int pe = __ldg(a.bpos + se.bin_base + je);
         const int be = se.bin_base + pe;
         const T Bv = (T)se.B;
         for (int r = 0; r < pd.R; ++r) {
-            const V ar = delay_phasor<T>(f, se.tau[r], pd.N);
+            const V ar = delay_phasor<T>(pd, f, se.tau[r]);
             const V dlt = {Bv * (v.x * ar.x - v.y * ar.y), Bv * (v.x * ar.y + v.y * ar.x)};
             atomic_sub_c(Y + se.y_off + (int64_t)r * se.B + pe, dlt);
         }
@@ -316,7 +355,7 @@ __device__ __forceinline__ bool bin_is_zero(const PlanDesc& pd, const typename C
 #pragma unroll
     for (int r = 0; r < kMaxDelays; ++r)
         if (r < pd.R) E += y[r].x * y[r].x + y[r].y * y[r].y;
-    return (double)E <= st.T0;
+    return below(E, st.T0f, st.T0);
 }
 
 template <typename T>
@@ -351,7 +390,7 @@ __device__ __forceinline__ void load_roots(const DecodeArgs& a, typename C2<T>::
 
 // Round 1: classify every bin.  One CTA per tile of kClassifyTile bins of one signal.
 template <typename T>
-__global__ void __launch_bounds__(kClassifyThreads) classify_kernel(const __grid_constant__ DecodeArgs a)
+__global__ void __launch_bounds__(kClassifyThreads, 3) classify_kernel(const __grid_constant__ DecodeArgs a)
 {
     using V = typename C2<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -557,6 +596,11 @@ __global__ void __launch_bounds__(1024) compact_kernel(const __grid_constant__ C
         info[2] = ldv(ctr + kCtrRounds);
         info[3] = ldv(ctr + kCtrIdents);
     }
+    // leave the slot's counters zeroed for the next execution (every thread has read
+    // what it needs above: rec count at the start, the rest by thread 0)
+    __syncthreads();
+    int32_t* wctr = const_cast<int32_t*>(ctr);
+    for (int i = threadIdx.x; i < a.ctr_stride; i += blockDim.x) wctr[i] = 0;
 }
 
 cudaError_t launch_classify(const DecodeArgs& a, int precision, cudaStream_t st)

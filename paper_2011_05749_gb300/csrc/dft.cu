@@ -17,6 +17,22 @@
 
 namespace sfft {
 
+// x / d and x % d for 0 <= x < 2^22 through a float reciprocal, corrected by one step
+__device__ __forceinline__ int fdivmod(int x, int d, float inv, int* rem)
+{
+    int q = (int)((float)x * inv);
+    int r = x - q * d;
+    if (r < 0) {
+        --q;
+        r += d;
+    } else if (r >= d) {
+        ++q;
+        r -= d;
+    }
+    *rem = r;
+    return q;
+}
+
 // In-place P-point DFTs (P odd) along one axis of a shared-memory tile.
 //   sub-DFT m starts at (m % LS) + (m / LS) * LS * P, element n at + n * LS.
 // X_k = x_0 + sum_{n=1}^{(P-1)/2} [ (x_n + x_{P-n}) cos(2 pi n k / P)
@@ -33,17 +49,39 @@ __device__ void axis_dft_odd(typename C2<T>::t* s, const typename C2<T>::t* twm,
     const int pairs = (P - 1) >> 1;
     const int KP = odd_row_len(P);  // row length of the twiddle matrix (a multiple of GP)
     const int NG = KP / GP;
-    const int Mc = max(1, (int)blockDim.x / NG);
+    const float invLS = 1.0f / (float)LS;
+    // pre-pass: (x_n, x_{P-n}) -> (a_n, b_n) = (x_n + x_{P-n}, x_n - x_{P-n}) in place
+    {
+        const int items = M * pairs;
+        const float invp = 1.0f / (float)pairs;
+        for (int w = threadIdx.x; w < items; w += blockDim.x) {
+            int n, lo;
+            const int m = fdivmod(w, pairs, invp, &n);
+            const int hi = fdivmod(m, LS, invLS, &lo);
+            const int base = lo + hi * LS * P;
+            const int pa = base + (n + 1) * LS, pb = base + (P - 1 - n) * LS;
+            const V xa = s[pa], xb = s[pb];
+            s[pa] = V{xa.x + xb.x, xa.y + xb.y};
+            s[pb] = V{xa.x - xb.x, xa.y - xb.y};
+        }
+        __syncthreads();
+    }
+    // column chunks of equal size (at most blockDim / NG columns each)
+    const int Mmax = max(1, (int)blockDim.x / NG);
+    const int nch = (M + Mmax - 1) / Mmax;
+    const int Mc = (M + nch - 1) / nch;
     const int g = threadIdx.x / Mc;
     const int ml = threadIdx.x - g * Mc;
     for (int m0 = 0; m0 < M; m0 += Mc) {
         const int m = m0 + ml;
-        const bool act = g < NG && m < M;
+        const bool act = g < NG && m < M && m < m0 + Mc;
         V acc[GP], sac[GP];
         V x0 = {0, 0}, dc = {0, 0};
         int base = 0;
         if (act) {
-            base = (m % LS) + (m / LS) * LS * P;
+            int lo;
+            const int hi = fdivmod(m, LS, invLS, &lo);
+            base = lo + hi * LS * P;
             x0 = s[base];
             dc = x0;
 #pragma unroll
@@ -52,13 +90,16 @@ __device__ void axis_dft_odd(typename C2<T>::t* s, const typename C2<T>::t* twm,
                 sac[i] = {0, 0};
             }
             const V* row = twm + g * GP;
-            for (int n = 1; n <= pairs; ++n, row += KP) {
-                const V xa = s[base + n * LS];
-                const V xb = s[base + (P - n) * LS];
-                const V av = {xa.x + xb.x, xa.y + xb.y};
-                const V bv = {xa.x - xb.x, xa.y - xb.y};
-                dc.x += av.x;
-                dc.y += av.y;
+            const V* pa = s + base + LS;
+            const V* pb = s + base + (P - 1) * LS;
+#pragma unroll 2
+            for (int n = 1; n <= pairs; ++n, row += KP, pa += LS, pb -= LS) {
+                const V av = *pa;  // x_n + x_{P-n}
+                const V bv = *pb;  // x_n - x_{P-n}
+                if (g == 0) {
+                    dc.x += av.x;
+                    dc.y += av.y;
+                }
                 V w[GP];
                 if constexpr (sizeof(V) == 8 && GP >= 2) {
 #pragma unroll
@@ -114,17 +155,20 @@ __device__ void axis_fft_pow2(typename C2<T>::t* s, const typename C2<T>::t* tw,
         const int h = 1 << lh;
         const int ngrp = P >> c;
         const int nw = M * ngrp;
+        const float invM = 1.0f / (float)M, invLS = 1.0f / (float)LS;
+        const int lg = log2P - c;  // ngrp = 2^lg
         for (int w = threadIdx.x; w < nw; w += blockDim.x) {
             int gi, m;
             if (LS == 1) {
-                gi = w % ngrp;
-                m = w / ngrp;
+                gi = w & (ngrp - 1);
+                m = w >> lg;
             } else {
-                m = w % M;
-                gi = w / M;
+                gi = fdivmod(w, M, invM, &m);
             }
             const int ii = gi & (h - 1), blk = gi >> lh;
-            const int base = (m % LS) + (m / LS) * LS * P;
+            int lo;
+            const int hi = LS == 1 ? m : fdivmod(m, LS, invLS, &lo);
+            const int base = LS == 1 ? m * P : lo + hi * LS * P;
             const int p0 = base + (blk * (G8 * h) + ii) * LS;
             const int st = h * LS;
             V v[8];
@@ -155,19 +199,194 @@ __device__ void axis_fft_pow2(typename C2<T>::t* s, const typename C2<T>::t* tw,
     }
 }
 
+// Odd-axis DFT on columns [c0, c1), each thread computing GP output pairs of CM columns
+// (m and m + Mc, so the lanes of a warp touch consecutive columns).  Expects the
+// (a_n, b_n) pre-pass done.  A chunk holds every group of its columns, so the in-place
+// writes after the barrier cannot clobber inputs another thread still reads.
+// With GP = 8 a thread does 32 FMAs per 2 shared loads of data and 4 (broadcast) of
+// twiddles.  Kept out of line so that each variant gets its own register allocation.
+template <typename T, int GP, int CM>
+__device__ __noinline__ void odd_dft_cols(typename C2<T>::t* s, const typename C2<T>::t* twm, int P, int LS,
+                             int c0, int c1)
+{
+    using V = typename C2<T>::t;
+    const int pairs = (P - 1) >> 1;
+    const int KP = odd_row_len(P);
+    const int NG = KP / GP;
+    const int Mc = max(1, (int)blockDim.x / NG);
+    const int span = Mc * CM;
+    const int g = threadIdx.x / Mc;
+    const int ml = threadIdx.x - g * Mc;
+    const float invLS = 1.0f / (float)LS;
+    for (int m0 = c0; m0 < c1; m0 += span) {
+        const int lim = min(c1, m0 + span);
+        bool act[CM];
+        int base[CM];
+        V x0[CM], dc[CM], acc[CM][GP], sac[CM][GP];
+#pragma unroll
+        for (int c = 0; c < CM; ++c) {
+            const int m = m0 + ml + c * Mc;
+            act[c] = g < NG && m < lim;
+            int lo;
+            const int hi = fdivmod(act[c] ? m : m0, LS, invLS, &lo);
+            base[c] = lo + hi * LS * P;
+        }
+        if (act[0]) {
+#pragma unroll
+            for (int c = 0; c < CM; ++c) {
+                x0[c] = s[base[c]];
+                dc[c] = x0[c];
+#pragma unroll
+                for (int i = 0; i < GP; ++i) {
+                    acc[c][i] = {0, 0};
+                    sac[c][i] = {0, 0};
+                }
+            }
+            const V* row = twm + g * GP;
+            for (int n = 1; n <= pairs; ++n, row += KP) {
+                V w[GP];
+                if constexpr (sizeof(V) == 8 && GP >= 2) {
+#pragma unroll
+                    for (int i = 0; i < GP / 2; ++i) {
+                        const float4 q = reinterpret_cast<const float4*>(row)[i];
+                        w[2 * i] = V{q.x, q.y};
+                        w[2 * i + 1] = V{q.z, q.w};
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < GP; ++i) w[i] = row[i];
+                }
+#pragma unroll
+                for (int c = 0; c < CM; ++c) {
+                    const V av = s[base[c] + n * LS];        // x_n + x_{P-n}
+                    const V bv = s[base[c] + (P - n) * LS];  // x_n - x_{P-n}
+                    if (g == 0) {
+                        dc[c].x += av.x;
+                        dc[c].y += av.y;
+                    }
+#pragma unroll
+                    for (int i = 0; i < GP; ++i) {
+                        acc[c][i].x = fma(av.x, w[i].x, acc[c][i].x);
+                        acc[c][i].y = fma(av.y, w[i].x, acc[c][i].y);
+                        sac[c][i].x = fma(bv.x, w[i].y, sac[c][i].x);
+                        sac[c][i].y = fma(bv.y, w[i].y, sac[c][i].y);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < CM; ++c) {
+            if (!act[c]) continue;
+            if (g == 0) s[base[c]] = dc[c];
+#pragma unroll
+            for (int i = 0; i < GP; ++i) {
+                const int k = g * GP + 1 + i;
+                if (k > pairs) continue;
+                const V cc = {x0[c].x + acc[c][i].x, x0[c].y + acc[c][i].y};
+                s[base[c] + k * LS] = V{cc.x + sac[c][i].y, cc.y - sac[c][i].x};
+                s[base[c] + (P - k) * LS] = V{cc.x - sac[c][i].y, cc.y + sac[c][i].x};
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// (a_n, b_n) pre-pass of an odd axis: (x_n, x_{P-n}) -> (x_n + x_{P-n}, x_n - x_{P-n})
+template <typename T>
+__device__ void odd_prepass(typename C2<T>::t* s, int P, int LS, int TS)
+{
+    using V = typename C2<T>::t;
+    const int M = TS / P, pairs = (P - 1) >> 1;
+    const float invLS = 1.0f / (float)LS, invp = 1.0f / (float)pairs;
+    for (int w = threadIdx.x; w < M * pairs; w += blockDim.x) {
+        int n, lo;
+        const int m = fdivmod(w, pairs, invp, &n);
+        const int hi = fdivmod(m, LS, invLS, &lo);
+        const int base = lo + hi * LS * P;
+        const int pa = base + (n + 1) * LS, pb = base + (P - 1 - n) * LS;
+        const V xa = s[pa], xb = s[pb];
+        s[pa] = V{xa.x + xb.x, xa.y + xb.y};
+        s[pb] = V{xa.x - xb.x, xa.y - xb.y};
+    }
+    __syncthreads();
+}
+
+template <typename T, int G2>
+__device__ __forceinline__ void odd_tail(typename C2<T>::t* s, const typename C2<T>::t* tw, int P,
+                                         int LS, int c0, int c1)
+{
+    // leftover columns: the smallest GP whose groups x columns fit one chunk
+    const int KP = odd_row_len(P), rem = c1 - c0, nt = blockDim.x;
+    if ((KP / 1) * rem <= nt)
+        odd_dft_cols<T, 1, 1>(s, tw, P, LS, c0, c1);
+    else if (G2 >= 2 && (KP / 2) * rem <= nt)
+        odd_dft_cols<T, (G2 >= 2 ? 2 : 1), 1>(s, tw, P, LS, c0, c1);
+    else if (G2 >= 4 && (KP / 4) * rem <= nt)
+        odd_dft_cols<T, (G2 >= 4 ? 4 : 1), 1>(s, tw, P, LS, c0, c1);
+    else
+        odd_dft_cols<T, G2, 1>(s, tw, P, LS, c0, c1);
+}
+
+// FP32 odd axis: pre-pass, then the bulk of the columns in full chunks of GP = odd_group_
+// pairs(P) pairs per thread, then the leftover columns in one small chunk.
+template <int G2>
+__device__ void odd_axis_f32(float2* s, const float2* tw, int P, int LS, int TS)
+{
+    const int M = TS / P, KP = odd_row_len(P);
+    const int span = max(1, (int)blockDim.x / (KP / G2));
+    const int main_end = M / span * span;
+    odd_prepass<float>(s, P, LS, TS);
+    if (main_end > 0) odd_dft_cols<float, G2, 1>(s, tw, P, LS, 0, main_end);
+    if (main_end < M) odd_tail<float, G2>(s, tw, P, LS, main_end, M);
+}
+
+// Output pairs per thread for an odd axis: the twiddle matrix rows are padded for
+// odd_group_pairs(P); any GP dividing that works.  At most 4 pairs per thread keep the
+// 640-thread CTA within its register budget; pick the GP that minimises (balanced column
+// chunks) x GP -- the per-thread work of the axis.
 template <typename T>
 __device__ __forceinline__ void axis_dft_odd_dispatch(typename C2<T>::t* s,
                                                       const typename C2<T>::t* tw, int P,
                                                       int LS, int TS)
 {
-    // FP64 keeps at most 4 output pairs per thread (register pressure); the matrix rows
-    // are padded for 8, which 4 divides
-    switch (odd_group_pairs(P)) {
-        case 1: axis_dft_odd<T, 1>(s, tw, P, LS, TS); break;
-        case 2: axis_dft_odd<T, 2>(s, tw, P, LS, TS); break;
-        case 4: axis_dft_odd<T, 4>(s, tw, P, LS, TS); break;
-        default: axis_dft_odd<T, sizeof(T) == 8 ? 4 : 8>(s, tw, P, LS, TS); break;
+    const int gmax = odd_group_pairs(P);
+    if (gmax < 4) {
+        if (gmax == 1)
+            axis_dft_odd<T, 1>(s, tw, P, LS, TS);
+        else
+            axis_dft_odd<T, 2>(s, tw, P, LS, TS);
+        return;
     }
+    const int KP = odd_row_len(P), M = TS / P, nt = blockDim.x;
+    int best_gp = 0, best_cost = 0;
+    for (int gp = 4; gp >= 2; gp >>= 1) {
+        const int ng = KP / gp;
+        const int mc = max(1, nt / ng);
+        const int cost = (M + mc - 1) / mc * gp;
+        if (best_gp == 0 || cost < best_cost) {
+            best_gp = gp;
+            best_cost = cost;
+        }
+    }
+    if (best_gp == 4)
+        axis_dft_odd<T, 4>(s, tw, P, LS, TS);
+    else
+        axis_dft_odd<T, 2>(s, tw, P, LS, TS);
+}
+
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc, int bytes)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if (bytes == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <typename XS, typename V>
@@ -181,7 +400,7 @@ __device__ __forceinline__ V load_sample(const void* x, int32_t i)
 // One block = one tile of one (signal, stage, delay).  Block order within a signal:
 // (stage, tile, delay), so the delays of a tile run back to back and share x's sectors.
 template <typename T, typename XS>
-__global__ void __launch_bounds__(512) bucketize_kernel(const __grid_constant__ BucketArgs a)
+__global__ void __launch_bounds__(512, 1) bucketize_kernel(const __grid_constant__ BucketArgs a)
 {
     using V = typename C2<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -229,61 +448,102 @@ __global__ void __launch_bounds__(512) bucketize_kernel(const __grid_constant__ 
     const int32_t* nidx = a.nidx + st.bin_base;
     const V* scr = reinterpret_cast<const V*>(a.scratch);
 
-    // load the tile; 8 independent loads in flight per thread
-    constexpr int U = 8;
-    for (int e0 = threadIdx.x; e0 < TS; e0 += U * blockDim.x) {
-        int pos[U];
-        int32_t src[U];
+    if constexpr (sizeof(XS) == sizeof(T)) {
+        if (ps.src_gather && Tb == 1 && Ta == 1) {
+            // whole-stage tile straight from x: sample indices from the table, then
+            // asynchronous 8/16-byte copies into shared memory, all in flight at once
+            constexpr int U = 8;
+            const V* xv = reinterpret_cast<const V*>(x);
+            for (int e0 = threadIdx.x; e0 < TS; e0 += U * blockDim.x) {
+                int src[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + u * blockDim.x;
-            int p = -1;
-            if (e < TS) {
-                if (Tb == 1 && Ta == 1) {
-                    p = e;
-                } else {
-                    const int tb = e % Tb;
-                    const int rest = e / Tb;
-                    const int g = rest % G;
-                    const int ta = rest / G;
-                    const int pb = tb0 + tb, pa = ta0 + ta;
-                    if (pb < Sb && pa < above) p = pb + Sb * g + Sab * pa;
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    src[u] = e < TS ? __ldg(nidx + e) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e < TS) {
+                        int xi = src[u] * L + tau;
+                        xi = xi >= N ? xi - N : xi;
+                        cp_async(s + e, xv + xi, (int)sizeof(V));
+                    }
                 }
             }
-            pos[u] = p;
-            src[u] = 0;
-            if (p >= 0) {
-                if (ps.src_gather) {
-                    int xi = __ldg(nidx + p) * L + tau;
-                    src[u] = xi >= N ? xi - N : xi;
-                } else {
-                    src[u] = p;
-                }
-            }
-        }
-        V v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            v[u] = V{0, 0};
-            if (pos[u] >= 0)
-                v[u] = ps.src_gather ? load_sample<XS, V>(x, src[u]) : __ldcg(scr + slot + src[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + u * blockDim.x;
-            if (e < TS) s[e] = v[u];
+            cp_async_wait_all();
+            goto loaded;
         }
     }
+    {
+        // general tile (two-pass stages, or a conversion of the input type): 8 loads in
+        // flight per thread
+        constexpr int U = 8;
+        for (int e0 = threadIdx.x; e0 < TS; e0 += U * blockDim.x) {
+            int pos[U];
+            int32_t src[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * blockDim.x;
+                int p = -1;
+                if (e < TS) {
+                    if (Tb == 1 && Ta == 1) {
+                        p = e;
+                    } else {
+                        const int tb = e % Tb;
+                        const int rest = e / Tb;
+                        const int g = rest % G;
+                        const int ta = rest / G;
+                        const int pb = tb0 + tb, pa = ta0 + ta;
+                        if (pb < Sb && pa < above) p = pb + Sb * g + Sab * pa;
+                    }
+                }
+                pos[u] = p;
+                src[u] = 0;
+                if (p >= 0) {
+                    if (ps.src_gather) {
+                        const int xi = __ldg(nidx + p) * L + tau;
+                        src[u] = xi >= N ? xi - N : xi;
+                    } else {
+                        src[u] = p;
+                    }
+                }
+            }
+            V v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                v[u] = V{0, 0};
+                if (pos[u] >= 0)
+                    v[u] = ps.src_gather ? load_sample<XS, V>(x, src[u]) : __ldcg(scr + slot + src[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * blockDim.x;
+                if (e < TS) s[e] = v[u];
+            }
+        }
+    }
+loaded:
     __syncthreads();
 
     int off = 0;
     for (int ax = a0; ax < a1; ++ax) {
         const AxisDesc& A = st.ax[ax];
         const int LS = Tb * (A.S / Sb);
-        if (A.pow2)
+        if (A.pow2) {
             axis_fft_pow2<T>(s, tws + off, A.P, A.log2P, LS, TS);
-        else if (A.P > 1)
-            axis_dft_odd_dispatch<T>(s, tws + off, A.P, LS, TS);
+        } else if (A.P > 1) {
+            if constexpr (sizeof(T) == 4) {
+                switch (odd_group_pairs(A.P)) {
+                    case 1: odd_axis_f32<1>(s, tws + off, A.P, LS, TS); break;
+                    case 2: odd_axis_f32<2>(s, tws + off, A.P, LS, TS); break;
+                    case 4: odd_axis_f32<4>(s, tws + off, A.P, LS, TS); break;
+                    default: odd_axis_f32<8>(s, tws + off, A.P, LS, TS); break;
+                }
+            } else {
+                axis_dft_odd_dispatch<T>(s, tws + off, A.P, LS, TS);
+            }
+        }
         off += (axis_tw_count(A.P, A.pow2) + 1) & ~1;
     }
 

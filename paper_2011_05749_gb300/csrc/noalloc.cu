@@ -216,7 +216,7 @@ extern "C" int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t*
             a.tile_prefix[d + 1] = a.tile_prefix[d] + (d < n_stages ? a.pass[d].n_tiles * n_delays : 0);
         a.tiles_per_sig = a.tile_prefix[kMaxStages];
         e = launch_bucketize(a, prec, dtype == SFFT_C128 ? 1 : 0,
-                             pfa_threads(pass == 0 ? l1.tile : l2.tile), pass == 0 ? l1.smem : l2.smem, st);
+                             pfa_threads(pass == 0 ? l1.tile : l2.tile, esz), pass == 0 ? l1.smem : l2.smem, st);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     e = launch_bins_to_natural(pd, pbin, sbins, bins, prec, 1, st);

@@ -182,8 +182,12 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
     return true;
 }
 
-inline int pfa_threads(int64_t tile)
+// threads of a bucketization CTA: whole-stage tiles (one CTA per SM, shared memory bound)
+// get 512 threads (the kernel's launch bound); small two-pass tiles about one thread per 8
+// elements
+inline int pfa_threads(int64_t tile, size_t)
 {
+    if (tile >= 8192) return 512;
     int64_t t = (tile / 8 + 31) / 32 * 32;
     return (int)(t < 128 ? 128 : (t > 512 ? 512 : t));
 }

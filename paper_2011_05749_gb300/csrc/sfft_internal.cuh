@@ -52,12 +52,14 @@ struct StageDesc {
     int32_t tau[kMaxDelays];
     int32_t tauL[kMaxDelays];  // tau mod L: candidate q of a bin shifts delay r's phase by
                                // e^{2 pi i q tauL_r / L}
+    int32_t step32[kMaxDelays];  // (32 tauL_r) mod L: the same for q -> q + 32
     int32_t bin_base;        // sum of B of earlier stages
     int32_t y_off;           // R * bin_base
     int32_t r0, r1;          // delay slots holding tau = 0 and tau = 1 (-1 if absent)
     int32_t root_off;        // offset of the L roots of unity (cos, sin)(2 pi t / L)
-    int32_t pad;
+    float invL;              // 1 / L
     double T0, T1;           // thresholds on sum_r |Y_r|^2 and on the single-tone residual
+    float T0f, T1f;          // the same in FP32 (the FP32 path compares in FP32)
 };
 
 struct PlanDesc {
@@ -69,6 +71,8 @@ struct PlanDesc {
     int32_t max_rounds;
     int32_t K;
     int32_t root_total;      // sum_d L_d: root-table entries (at st[0].root_off onwards)
+    double invN;             // 1 / N
+    uint64_t mu;             // floor((2^64 - 1) / N): Barrett reduction modulo N
     StageDesc st[kMaxStages];
 };
 

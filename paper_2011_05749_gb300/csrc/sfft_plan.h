@@ -45,6 +45,8 @@ struct sfft_plan_s {
     void* d_x_stage = nullptr;
     void* d_out_stage = nullptr;
     void* d_bins_in = nullptr;
+    cudaStream_t aux[2] = {nullptr, nullptr};  // host-buffer batches: copy/compute overlap
+    cudaEvent_t aux_ev = nullptr;
     void* d_xb_stage = nullptr;   // host-buffer batches: max_batch inputs
     void* d_ob_stage = nullptr;   //                      max_batch outputs + infos
     size_t footprint = 0;  // device bytes owned by the plan
