@@ -264,6 +264,22 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         }
         pd.root_total += pd.st[d].L;
     }
+    // ML candidate phasors per stage: W[q][r] = e^{2 pi i (q tauL_r mod L) / L}; padding
+    // columns get P = 0, which the twiddle kernel turns into (0, 0)
+    pd.Rp = (n_delays + 1) & ~1;
+    for (int d = 0; d < n_stages; ++d) {
+        if (tw_P.size() & 1) {  // 16-byte aligned rows
+            tw_P.push_back(0);
+            tw_t.push_back(0);
+        }
+        pd.st[d].wtab_off = (int32_t)tw_P.size();
+        const int64_t L = pd.st[d].L;
+        for (int64_t q = 0; q < L; ++q)
+            for (int r = 0; r < pd.Rp; ++r) {
+                tw_P.push_back(r < n_delays ? (int32_t)L : 0);
+                tw_t.push_back(r < n_delays ? (int32_t)((q * pd.st[d].tauL[r]) % L) : 0);
+            }
+    }
     pd.sumB = (int32_t)bin_base;
     pd.y_per_sig = (int64_t)bin_base * n_delays;
     p->smem1 = l1.smem;
@@ -476,7 +492,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     da.pbin = p->d_pbin;
     da.bpos = p->d_bpos;
     da.bins = bins;
-    da.roots = (const unsigned char*)p->d_tw + (size_t)pd.st[0].root_off * p->esz;
+    da.roots = p->d_tw;
     const int threads = 512;
     const int total = p->num_sms * p->decode_occ;
     // later rounds touch O(K) bins: about one CTA per 256 expected single-tons

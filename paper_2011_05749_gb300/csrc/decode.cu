@@ -140,65 +140,58 @@ __device__ __forceinline__ void record_candidate(int32_t* ctr, const DecodeWs& w
     atomicAdd(ctr + kCtrResolved, 1);
 }
 
-// D2, ML locate: one warp per non-zero bin j of stage d.  Lane r < R forms
-// Z_r = Y_r conj(a_r(j)); lanes then score candidates q = lane, lane + 32, ... by
-// |sum_r Z_r e^{-2 pi i q tauL_r / L}|^2, the warp keeps the best (lowest q on ties) and
-// fits v = sum_r Z_r e^{-2 pi i q tauL_r / L} / (R B) and rho = sum_r |Z_r - B v e^{..}|^2.
+// D2, ML locate: one thread per non-zero bin j of stage d.  Z_r = Y_r conj(a_r(j)); the
+// L candidates q are scored by |sum_r Z_r conj(W[q][r])|^2 with the stage's phasor table
+// W[q][r] = e^{2 pi i (q tauL_r mod L) / L} (a candidate f = j + q B has
+// a_r(f) = a_r(j) W[q][r]); the best (lowest q on ties) gives v = sum_r Z_r conj(W) / (R B)
+// and rho = sum_r |Z_r - B v W[q][r]|^2.  Lanes of a warp scan the same q in lockstep, so
+// the table reads are broadcasts.
 template <typename T>
-__device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
-                               const typename C2<T>::t* Y, const typename C2<T>::t* roots,
-                               int round, int b)
+__device__ void locate_ml_thread(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                                 const typename C2<T>::t* Y, int round, int b)
 {
     using V = typename C2<T>::t;
     const PlanDesc& pd = a.pd;
-    const int lane = threadIdx.x & 31;
     const int d = stage_of(pd, b);
     const StageDesc& st = pd.st[d];
-    const int R = pd.R;
-    const int B = st.B, L = st.L, N = pd.N;
+    const int R = pd.R, Rp = pd.Rp;
+    const int B = st.B, L = st.L;
     const int j = __ldg(a.pbin + b);
-    const V* wl = roots + (st.root_off - pd.st[0].root_off);
-    V z = {0, 0};
-    if (lane < R) {
-        const V y = __ldcg(Y + st.y_off + (int64_t)lane * B + (b - st.bin_base));
-        const V aj = delay_phasor<T>(pd, j, st.tau[lane]);
-        z = V{y.x * aj.x + y.y * aj.y, y.y * aj.x - y.x * aj.y};
-    }
+    const V* Yb = Y + st.y_off + (b - st.bin_base);
     T zx[kMaxDelays], zy[kMaxDelays];
-    int idx[kMaxDelays], step[kMaxDelays];
 #pragma unroll
     for (int r = 0; r < kMaxDelays; ++r) {
         zx[r] = 0;
         zy[r] = 0;
-        idx[r] = 0;
-        step[r] = 0;
         if (r < R) {
-            zx[r] = __shfl_sync(0xffffffffu, z.x, r);
-            zy[r] = __shfl_sync(0xffffffffu, z.y, r);
-            idx[r] = small_mod(lane * st.tauL[r], L, st.invL);
-            step[r] = st.step32[r];
+            const V y = __ldcg(Yb + (int64_t)r * B);
+            const V aj = delay_phasor<T>(pd, j, st.tau[r]);
+            zx[r] = y.x * aj.x + y.y * aj.y;
+            zy[r] = y.y * aj.x - y.x * aj.y;
         }
     }
-    T best = (T)-1;
+    const V* W = reinterpret_cast<const V*>(a.roots) + st.wtab_off;
+    T best = (T)-1, bcx = 0, bcy = 0;
     int bq = 0;
-    for (int q = lane; q < L; q += 32) {
-        // two partial sums (even / odd delays) halve the dependency chain
+    for (int q = 0; q < L; ++q) {
+        const V* Wq = W + q * Rp;
         T cx0 = 0, cy0 = 0, cx1 = 0, cy1 = 0;
 #pragma unroll
         for (int r = 0; r < kMaxDelays; r += 2) {
             if (r < R) {
-                const V wv = wl[idx[r]];
-                cx0 += zx[r] * wv.x + zy[r] * wv.y;
-                cy0 += zy[r] * wv.x - zx[r] * wv.y;
-                const int ni = idx[r] + step[r];
-                idx[r] = ni >= L ? ni - L : ni;
-            }
-            if (r + 1 < R) {
-                const V wv = wl[idx[r + 1]];
-                cx1 += zx[r + 1] * wv.x + zy[r + 1] * wv.y;
-                cy1 += zy[r + 1] * wv.x - zx[r + 1] * wv.y;
-                const int ni = idx[r + 1] + step[r + 1];
-                idx[r + 1] = ni >= L ? ni - L : ni;
+                V w0, w1;
+                if constexpr (sizeof(V) == 8) {
+                    const float4 q4 = __ldg(reinterpret_cast<const float4*>(Wq + r));
+                    w0 = V{q4.x, q4.y};
+                    w1 = V{q4.z, q4.w};
+                } else {
+                    w0 = __ldg(Wq + r);
+                    w1 = __ldg(Wq + r + 1);
+                }
+                cx0 += zx[r] * w0.x + zy[r] * w0.y;
+                cy0 += zy[r] * w0.x - zx[r] * w0.y;
+                cx1 += zx[r + 1] * w1.x + zy[r + 1] * w1.y;
+                cy1 += zy[r + 1] * w1.x - zx[r + 1] * w1.y;
             }
         }
         const T cx = cx0 + cx1, cy = cy0 + cy1;
@@ -206,39 +199,25 @@ __device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs
         if (sc > best) {
             best = sc;
             bq = q;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
-        if (ob > best || (ob == best && oq < bq)) {
-            best = ob;
-            bq = oq;
+            bcx = cx;
+            bcy = cy;
         }
     }
     const int64_t f = (int64_t)j + (int64_t)bq * B;
-    V e = {1, 0}, c = {0, 0};
-    if (lane < R) {
-        e = wl[small_mod(bq * st.tauL[lane], L, st.invL)];
-        c = V{z.x * e.x + z.y * e.y, z.y * e.x - z.x * e.y};
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        c.x += __shfl_xor_sync(0xffffffffu, c.x, o);
-        c.y += __shfl_xor_sync(0xffffffffu, c.y, o);
-    }
     const T sc = (T)1 / ((T)R * (T)B);
-    const V v = {c.x * sc, c.y * sc};
+    const V v = {bcx * sc, bcy * sc};
+    const V* Wb = W + bq * Rp;
     T e2 = 0;
-    if (lane < R) {
-        const T ex = z.x - (T)B * (v.x * e.x - v.y * e.y);
-        const T ey = z.y - (T)B * (v.x * e.y + v.y * e.x);
-        e2 = ex * ex + ey * ey;
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-    if (lane == 0 && below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
+    for (int r = 0; r < kMaxDelays; ++r) {
+        if (r < R) {
+            const V e = __ldg(Wb + r);
+            const T ex = zx[r] - (T)B * (v.x * e.x - v.y * e.y);
+            const T ey = zy[r] - (T)B * (v.x * e.y + v.y * e.x);
+            e2 += ex * ex + ey * ey;
+        }
+    }
+    if (below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
 }
 
 // D2, ARG locate (FFAST, Sec. 3.2 subproblem 2): f from the phase of Y(1) conj(Y(0)) in
@@ -379,22 +358,11 @@ __device__ __forceinline__ DecodeWs slot_ws(const DecodeArgs& a, int sig)
     return w;
 }
 
-template <typename T>
-__device__ __forceinline__ void load_roots(const DecodeArgs& a, typename C2<T>::t* roots_s)
-{
-    using V = typename C2<T>::t;
-    if (a.pd.locate != 1) return;
-    const V* src = reinterpret_cast<const V*>(a.roots);
-    for (int i = threadIdx.x; i < a.pd.root_total; i += blockDim.x) roots_s[i] = src[i];
-}
-
 // Round 1: classify every bin.  One CTA per tile of kClassifyTile bins of one signal.
 template <typename T>
 __global__ void __launch_bounds__(kClassifyThreads, 3) classify_kernel(const __grid_constant__ DecodeArgs a)
 {
     using V = typename C2<T>::t;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* roots_s = reinterpret_cast<V*>(smem_raw);
     __shared__ int s_nz[kClassifyTile];
     __shared__ int s_cnt, s_res;
     const PlanDesc& pd = a.pd;
@@ -405,7 +373,6 @@ __global__ void __launch_bounds__(kClassifyThreads, 3) classify_kernel(const __g
     V* Y = reinterpret_cast<V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
     const int b0 = tile * kClassifyTile;
     const int b1 = min(pd.sumB, b0 + kClassifyTile);
-    load_roots<T>(a, roots_s);
     if (threadIdx.x == 0) {
         s_cnt = 0;
         s_res = 0;
@@ -425,8 +392,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 3) classify_kernel(const __g
     __syncthreads();
     const int n_nz = s_cnt;
     if (pd.locate == 1) {
-        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-        for (int i = warp; i < n_nz; i += nwarps) locate_ml_warp<T>(a, w.ctr, w, Y, roots_s, 1, s_nz[i]);
+        for (int i = threadIdx.x; i < n_nz; i += blockDim.x) locate_ml_thread<T>(a, w.ctr, w, Y, 1, s_nz[i]);
     } else {
         for (int i = threadIdx.x; i < n_nz; i += blockDim.x) locate_arg_thread<T>(a, w.ctr, w, Y, 1, s_nz[i]);
     }
@@ -441,8 +407,6 @@ template <typename T>
 __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ DecodeArgs a)
 {
     using V = typename C2<T>::t;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* roots_s = reinterpret_cast<V*>(smem_raw);
     const PlanDesc& pd = a.pd;
     const int G = a.G;
     const int sig = blockIdx.x / G;
@@ -451,12 +415,8 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
     const DecodeWs w = slot_ws<T>(a, sig);
     int32_t* ctr = w.ctr;
     V* Y = reinterpret_cast<V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
-    load_roots<T>(a, roots_s);
-    __syncthreads();
-
     const int wt = gi * blockDim.x + threadIdx.x;
     const int nw = G * blockDim.x;
-    const int gw = wt >> 5, nwarps = nw >> 5;
 
     int round = 1;
     while (true) {
@@ -484,8 +444,7 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
         // D2: locate, fit, singleton test
         const int n_nz = ldv(ctr + kCtrRoundBase + 3 * round + 1);
         if (pd.locate == 1) {
-            for (int i = gw; i < n_nz; i += nwarps)
-                locate_ml_warp<T>(a, ctr, w, Y, roots_s, round, __ldcg(w.nzl + i));
+            for (int i = wt; i < n_nz; i += nw) locate_ml_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
         } else {
             for (int i = wt; i < n_nz; i += nw) locate_arg_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
         }
@@ -608,11 +567,10 @@ cudaError_t launch_classify(const DecodeArgs& a, int precision, cudaStream_t st)
     const int tiles = (a.pd.sumB + kClassifyTile - 1) / kClassifyTile;
     const unsigned grid = (unsigned)a.n_sig * (unsigned)tiles;
     if (grid == 0) return cudaSuccess;
-    const size_t smem = a.pd.locate == 1 ? (size_t)a.pd.root_total * (precision == 1 ? 8 : 16) : 0;
     if (precision == 1)
-        classify_kernel<float><<<grid, kClassifyThreads, smem, st>>>(a);
+        classify_kernel<float><<<grid, kClassifyThreads, 0, st>>>(a);
     else
-        classify_kernel<double><<<grid, kClassifyThreads, smem, st>>>(a);
+        classify_kernel<double><<<grid, kClassifyThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -621,16 +579,15 @@ cudaError_t launch_decode(const DecodeArgs& a, int precision, int threads, bool 
 {
     const unsigned grid = (unsigned)a.n_sig * (unsigned)a.G;
     if (grid == 0) return cudaSuccess;
-    const size_t smem = a.pd.locate == 1 ? (size_t)a.pd.root_total * (precision == 1 ? 8 : 16) : 0;
     void* fn = precision == 1 ? (void*)peel_kernel<float> : (void*)peel_kernel<double>;
     if (cooperative) {
         void* args[] = {(void*)&a};
-        return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, smem, st);
+        return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, st);
     }
     if (precision == 1)
-        peel_kernel<float><<<grid, threads, smem, st>>>(a);
+        peel_kernel<float><<<grid, threads, 0, st>>>(a);
     else
-        peel_kernel<double><<<grid, threads, smem, st>>>(a);
+        peel_kernel<double><<<grid, threads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -638,7 +595,7 @@ int decode_occupancy(int precision, int threads)
 {
     int nb = 0;
     void* fn = precision == 1 ? (void*)peel_kernel<float> : (void*)peel_kernel<double>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 16 * 1024) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 0) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }

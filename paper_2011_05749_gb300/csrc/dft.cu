@@ -328,6 +328,50 @@ __device__ __forceinline__ void odd_tail(typename C2<T>::t* s, const typename C2
         odd_dft_cols<T, G2, 1>(s, tw, P, LS, c0, c1);
 }
 
+// Odd axis with P <= 9: one thread per column computes the whole P-point DFT in
+// registers (it owns its column, so no barrier is needed until the axis is done).
+template <typename T>
+__device__ __noinline__ void odd_small(typename C2<T>::t* s, const typename C2<T>::t* twm, int P, int LS, int TS)
+{
+    using V = typename C2<T>::t;
+    const int M = TS / P, pairs = (P - 1) >> 1, KP = odd_row_len(P);
+    const float invLS = 1.0f / (float)LS;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        int lo;
+        const int hi = fdivmod(m, LS, invLS, &lo);
+        const int base = lo + hi * LS * P;
+        const V x0 = s[base];
+        V av[4], bv[4], dc = x0;
+#pragma unroll
+        for (int n = 1; n <= 4; ++n) {
+            if (n > pairs) break;
+            const V xa = s[base + n * LS], xb = s[base + (P - n) * LS];
+            av[n - 1] = V{xa.x + xb.x, xa.y + xb.y};
+            bv[n - 1] = V{xa.x - xb.x, xa.y - xb.y};
+            dc.x += av[n - 1].x;
+            dc.y += av[n - 1].y;
+        }
+        s[base] = dc;
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) {
+            if (k > pairs) break;
+            V A = x0, S = {0, 0};
+#pragma unroll
+            for (int n = 1; n <= 4; ++n) {
+                if (n > pairs) break;
+                const V w = twm[(n - 1) * KP + (k - 1)];
+                A.x = fma(av[n - 1].x, w.x, A.x);
+                A.y = fma(av[n - 1].y, w.x, A.y);
+                S.x = fma(bv[n - 1].x, w.y, S.x);
+                S.y = fma(bv[n - 1].y, w.y, S.y);
+            }
+            s[base + k * LS] = V{A.x + S.y, A.y - S.x};
+            s[base + (P - k) * LS] = V{A.x - S.y, A.y + S.x};
+        }
+    }
+    __syncthreads();
+}
+
 // FP32 odd axis: pre-pass, then the bulk of the columns in full chunks of GP = odd_group_
 // pairs(P) pairs per thread, then the leftover columns in one small chunk.
 template <int G2>
@@ -533,15 +577,13 @@ loaded:
         if (A.pow2) {
             axis_fft_pow2<T>(s, tws + off, A.P, A.log2P, LS, TS);
         } else if (A.P > 1) {
-            if constexpr (sizeof(T) == 4) {
-                switch (odd_group_pairs(A.P)) {
-                    case 1: odd_axis_f32<1>(s, tws + off, A.P, LS, TS); break;
-                    case 2: odd_axis_f32<2>(s, tws + off, A.P, LS, TS); break;
-                    case 4: odd_axis_f32<4>(s, tws + off, A.P, LS, TS); break;
-                    default: odd_axis_f32<8>(s, tws + off, A.P, LS, TS); break;
-                }
+            if (A.P <= 9) {
+                odd_small<T>(s, tws + off, A.P, LS, TS);
             } else {
-                axis_dft_odd_dispatch<T>(s, tws + off, A.P, LS, TS);
+                if constexpr (sizeof(T) == 4)
+                    odd_axis_f32<8>(s, tws + off, A.P, LS, TS);
+                else
+                    axis_dft_odd_dispatch<T>(s, tws + off, A.P, LS, TS);
             }
         }
         off += (axis_tw_count(A.P, A.pow2) + 1) & ~1;
@@ -571,6 +613,10 @@ __global__ void twiddle_kernel(typename C2<T>::t* tw, const int32_t* P_of, const
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (P_of[i] == 0) {  // padding entry
+        tw[i] = typename C2<T>::t{(T)0, (T)0};
+        return;
+    }
     double sv, cv;
     sincospi(2.0 * (double)t_of[i] / (double)P_of[i], &sv, &cv);
     tw[i] = typename C2<T>::t{(T)cv, (T)sv};

@@ -30,7 +30,7 @@ struct DecodeArgs {
     int32_t pad;
     const int32_t* pbin;  // position -> bin j, per stage at bin_base
     const int32_t* bpos;  // bin j -> position
-    const void* roots;    // L_d roots of unity of every stage, (cos, sin)(2 pi t / L_d)
+    const void* roots;    // the plan's twiddle table: ML phasor tables at st[d].wtab_off
     void* bins;           // complex, n_sig * y_per_sig, modified in place
 };
 
