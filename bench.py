@@ -45,7 +45,7 @@ N_DISTINCT = 8
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=64, help="signals per step per GPU")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
@@ -53,6 +53,8 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--max-tile", type=int, default=0,
+                    help="largest DFT tile per CTA in elements (0: shared-memory limit)")
     ap.add_argument("--timed-only", action="store_true",
                     help="run only the timed batched loop (for profiler captures)")
     return ap.parse_args()
@@ -92,7 +94,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -193,6 +195,22 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+def max_over_ranks(v: float, world: int, device="cuda") -> float:
+    """Largest value over the ranks (the job is as slow as its slowest replica)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def kernel_traffic(kernel: str, src_files, per_unit_key: str):
     """Traffic per unit from the committed ncu summary, if the kernel source still
     matches the hash recorded there; else None."""
@@ -232,13 +250,6 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     S = args.batch
     N, K, R, f = CFG["N"], CFG["K"], CFG["R"], CFG["f"]
     nv = expected_noise_var()
@@ -250,7 +261,7 @@ def run_gpu(args):
     for i in range(S):
         xs[i].copy_(distinct[i % N_DISTINCT])
     plan = sfft.Plan(N, K, f, delays, precision="fp32", locate="ml", noise_var=nv,
-                     max_batch=S)
+                     max_batch=S, max_tile=args.max_tile)
     out = plan.empty_outputs("cuda", S)
     stream = torch.cuda.current_stream()
 
@@ -273,8 +284,8 @@ def run_gpu(args):
     plan.set_profiling(False)
     prof = plan.profile(reset=True)
     el_ms = ev0.elapsed_time(ev1)
-    el_ms = max_over_ranks(el_ms)
-    value = S * args.steps * world / (el_ms / 1e3)
+    el_ms = max_over_ranks(el_ms, world)
+    value = job_rate(S * args.steps, world, el_ms)
     infos = out[2].cpu().numpy()
 
     # dominant kernel: gather + prime-factor DFTs (bucketization), one launch per step
@@ -367,7 +378,7 @@ def run_gpu(args):
         for _ in range(e_steps):
             sfft.execute_batch([plan] * S, hx, (hidx, hval, hinf))
         torch.cuda.synchronize()
-        e_el = max_over_ranks(time.perf_counter() - t0)
+        e_el = max_over_ranks(time.perf_counter() - t0, world)
         e2e = {"value": S * e_steps * world / e_el, "unit": "signals/s",
                "h2d_bytes_per_step": S * N * 8,
                "d2h_bytes_per_step": S * (K * 8 + K * 8) + S * 16,

@@ -80,7 +80,8 @@ typedef struct {
     int32_t locate;      /* SFFT_LOCATE_ARG or SFFT_LOCATE_ML (default ML) */
     int32_t max_rounds;  /* peeling rounds at most (default 64) */
     int32_t max_batch;   /* signals per execute call at most; sizes the workspace (default 1) */
-    int32_t reserved;
+    int32_t max_tile;    /* largest DFT tile in elements held by one CTA; 0 = whatever shared
+                            memory allows (stages larger than it run as two passes) */
     double noise_var;    /* sigma^2 of the noise per time sample, 0 = exactly sparse */
     double a_min;        /* smallest significant |xhat| (default 1) */
     double eta;          /* relative numerical floor of the thresholds; 0 = default
@@ -88,6 +89,12 @@ typedef struct {
     double c0, c1;       /* zero-ton / single-ton threshold multipliers (default 4, 2):
                             T0_d = R (c0 B_d sigma^2 + (eta B_d a_min)^2),
                             T1_d = R (c1 B_d sigma^2 + (eta B_d a_min)^2) */
+    int32_t wait_limit_log2;  /* a device-side wait gives up after 2^this polls (about
+                                 0.1-0.3 us each) and reports SFFT_ETIMEDOUT; 0 = 22 */
+    int32_t fault_inject;     /* testing only: 0 none; 1 = one CTA of every multi-CTA decode
+                                 group leaves before its first barrier, so the others' wait
+                                 runs out (status SFFT_ETIMEDOUT); 2 = plan creation fails
+                                 with SFFT_ENOMEM before allocating */
 } sfft_opts;
 
 /* Fill *opts with the defaults above. */

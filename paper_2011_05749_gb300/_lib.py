@@ -44,9 +44,10 @@ class SfftError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("locate", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
-                ("max_batch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_tile", ctypes.c_int32),
                 ("noise_var", ctypes.c_double), ("a_min", ctypes.c_double),
-                ("eta", ctypes.c_double), ("c0", ctypes.c_double), ("c1", ctypes.c_double)]
+                ("eta", ctypes.c_double), ("c0", ctypes.c_double), ("c1", ctypes.c_double),
+                ("wait_limit_log2", ctypes.c_int32), ("fault_inject", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

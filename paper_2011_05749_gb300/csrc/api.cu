@@ -131,7 +131,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     if ((o.dtype != SFFT_C64 && o.dtype != SFFT_C128) ||
         (o.precision != SFFT_PREC_FP32 && o.precision != SFFT_PREC_FP64) ||
         (o.locate != SFFT_LOCATE_ARG && o.locate != SFFT_LOCATE_ML) || o.max_rounds < 1 ||
-        o.max_rounds > 4096 || o.max_batch < 1 || o.noise_var < 0 || o.a_min < 0 ||
+        o.max_rounds > 4096 || o.max_batch < 1 || o.max_tile < 0 || o.noise_var < 0 || o.a_min < 0 ||
         o.eta < 0 || o.c0 < 0 || o.c1 < 0)
         return SFFT_EINVAL;
     for (int d = 0; d < n_stages; ++d) {
@@ -145,6 +145,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
                 if (delays[(int64_t)d * n_delays + q] == t) return SFFT_EINVAL;
         }
     }
+    if (o.fault_inject == 2) return SFFT_ENOMEM;  // injected allocation failure (testing)
+    if (o.wait_limit_log2 < 0 || o.fault_inject < 0 || o.fault_inject > 2) return SFFT_EINVAL;
     DevInfo di;
     int rc = device_info(&di);
     if (rc) return rc;
@@ -183,7 +185,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         s.B = (int32_t)B;
         s.L = (int32_t)L;
         if (!pfa_layout_stage(&s, p->esz, di.max_smem, tile_target, &p->pass1[d], &p->pass2[d],
-                              &l1, &l2, &tw_cursor, &p->need_pass2)) {
+                              &l1, &l2, &tw_cursor, &p->need_pass2, o.max_tile)) {
             free_plan_memory(p);
             delete p;
             return SFFT_EINVAL;
@@ -502,6 +504,8 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
         G = std::max(G, 1);
     }
     da.G = G;
+    da.fault = p->opts.fault_inject == 1 ? 1 : 0;
+    da.spin_limit = 1ll << (p->opts.wait_limit_log2 > 0 ? std::min(p->opts.wait_limit_log2, 40) : 22);
     {
         PhaseScope ps(p, st, 1, 2);
         CK(launch_classify(da, p->prec, st));

@@ -27,7 +27,6 @@
 
 namespace sfft {
 
-constexpr long long kSpinLimit = 1ll << 22;  // ~0.3-1 s of polling at 64-256 ns per poll
 constexpr int64_t kFMask = (1ll << 40) - 1;
 constexpr int kClassifyTile = 2048;          // bins per classify CTA
 constexpr int kClassifyThreads = 256;
@@ -36,7 +35,7 @@ __device__ __forceinline__ int ldv(const int32_t* p) { return *(const volatile i
 
 // Barrier of the G CTAs decoding one signal; returns false when the wait ran out (or any
 // CTA of the group saw it run out), in which case the error word is set.
-__device__ bool group_barrier(int32_t* ctr, int G)
+__device__ bool group_barrier(int32_t* ctr, int G, long long spin_limit)
 {
     __shared__ int ok;
     __syncthreads();
@@ -52,7 +51,7 @@ __device__ bool group_barrier(int32_t* ctr, int G)
             } else {
                 long long it = 0;
                 while (ldv(ctr + kCtrBarGen) == gen) {
-                    if (++it > kSpinLimit || ldv(ctr + kCtrErr) != 0) {
+                    if (++it > spin_limit || ldv(ctr + kCtrErr) != 0) {
                         atomicExch(ctr + kCtrErr, 1);
                         good = 0;
                         break;
@@ -218,6 +217,91 @@ __device__ void locate_ml_thread(const DecodeArgs& a, int32_t* ctr, const Decode
         }
     }
     if (below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
+}
+
+// D2, ML locate with one warp per bin (later rounds, where few bins are left and
+// latency matters more than throughput): lane r < R forms Z_r, the lanes split the L
+// candidates, then a warp argmax (lowest q on ties) and warp sums for v and rho.  Same
+// arithmetic as locate_ml_thread.
+template <typename T>
+__device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                               const typename C2<T>::t* Y, int round, int b)
+{
+    using V = typename C2<T>::t;
+    const PlanDesc& pd = a.pd;
+    const int lane = threadIdx.x & 31;
+    const int d = stage_of(pd, b);
+    const StageDesc& st = pd.st[d];
+    const int R = pd.R, Rp = pd.Rp;
+    const int B = st.B, L = st.L;
+    const int j = __ldg(a.pbin + b);
+    V z = {0, 0};
+    if (lane < R) {
+        const V y = __ldcg(Y + st.y_off + (int64_t)lane * B + (b - st.bin_base));
+        const V aj = delay_phasor<T>(pd, j, st.tau[lane]);
+        z = V{y.x * aj.x + y.y * aj.y, y.y * aj.x - y.x * aj.y};
+    }
+    T zx[kMaxDelays], zy[kMaxDelays];
+#pragma unroll
+    for (int r = 0; r < kMaxDelays; ++r) {
+        zx[r] = 0;
+        zy[r] = 0;
+        if (r < R) {
+            zx[r] = __shfl_sync(0xffffffffu, z.x, r);
+            zy[r] = __shfl_sync(0xffffffffu, z.y, r);
+        }
+    }
+    const V* W = reinterpret_cast<const V*>(a.roots) + st.wtab_off;
+    T best = (T)-1;
+    int bq = 0;
+    for (int q = lane; q < L; q += 32) {
+        const V* Wq = W + q * Rp;
+        T cx = 0, cy = 0;
+#pragma unroll
+        for (int r = 0; r < kMaxDelays; ++r) {
+            if (r < R) {
+                const V wv = __ldg(Wq + r);
+                cx += zx[r] * wv.x + zy[r] * wv.y;
+                cy += zy[r] * wv.x - zx[r] * wv.y;
+            }
+        }
+        const T sc = cx * cx + cy * cy;
+        if (sc > best) {
+            best = sc;
+            bq = q;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+        if (ob > best || (ob == best && oq < bq)) {
+            best = ob;
+            bq = oq;
+        }
+    }
+    const int64_t f = (int64_t)j + (int64_t)bq * B;
+    V e = {0, 0}, c = {0, 0};
+    if (lane < R) {
+        e = __ldg(W + bq * Rp + lane);
+        c = V{z.x * e.x + z.y * e.y, z.y * e.x - z.x * e.y};
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c.x += __shfl_xor_sync(0xffffffffu, c.x, o);
+        c.y += __shfl_xor_sync(0xffffffffu, c.y, o);
+    }
+    const T sc = (T)1 / ((T)R * (T)B);
+    const V v = {c.x * sc, c.y * sc};
+    T e2 = 0;
+    if (lane < R) {
+        const T ex = z.x - (T)B * (v.x * e.x - v.y * e.y);
+        const T ey = z.y - (T)B * (v.x * e.y + v.y * e.x);
+        e2 = ex * ex + ey * ey;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    if (lane == 0 && below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
 }
 
 // D2, ARG locate (FFAST, Sec. 3.2 subproblem 2): f from the phase of Y(1) conj(Y(0)) in
@@ -415,6 +499,7 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
     const DecodeWs w = slot_ws<T>(a, sig);
     int32_t* ctr = w.ctr;
     V* Y = reinterpret_cast<V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
+    if (a.fault == 1 && G > 1 && gi == G - 1) return;  // injected loss of a CTA (testing)
     const int wt = gi * blockDim.x + threadIdx.x;
     const int nw = G * blockDim.x;
 
@@ -423,7 +508,7 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
         // P: accept and peel this round's single-tons
         const int n_c = ldv(ctr + kCtrRoundBase + 3 * round + 2);
         for (int i = wt; i < n_c; i += nw) peel_candidate<T>(a, ctr, w, Y, round, i);
-        if (!group_barrier(ctr, G)) break;
+        if (!group_barrier(ctr, G, a.spin_limit)) break;
         const int n_next = ldv(ctr + kCtrRoundBase + 3 * round + 0);
         if (n_next == 0 || round >= pd.max_rounds) break;
         ++round;
@@ -440,15 +525,16 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
             }
         }
         if (wt == 0) atomicAdd(ctr + kCtrIdents, n_next);
-        if (!group_barrier(ctr, G)) break;
+        if (!group_barrier(ctr, G, a.spin_limit)) break;
         // D2: locate, fit, singleton test
         const int n_nz = ldv(ctr + kCtrRoundBase + 3 * round + 1);
         if (pd.locate == 1) {
-            for (int i = wt; i < n_nz; i += nw) locate_ml_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
+            const int gw = wt >> 5, nwarps = nw >> 5;
+            for (int i = gw; i < n_nz; i += nwarps) locate_ml_warp<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
         } else {
             for (int i = wt; i < n_nz; i += nw) locate_arg_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
         }
-        if (!group_barrier(ctr, G)) break;
+        if (!group_barrier(ctr, G, a.spin_limit)) break;
     }
     if (gi == 0 && threadIdx.x == 0) ctr[kCtrRounds] = round;
 }

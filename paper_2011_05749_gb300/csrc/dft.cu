@@ -243,6 +243,7 @@ __device__ __noinline__ void odd_dft_cols(typename C2<T>::t* s, const typename C
                 }
             }
             const V* row = twm + g * GP;
+#pragma unroll 2
             for (int n = 1; n <= pairs; ++n, row += KP) {
                 V w[GP];
                 if constexpr (sizeof(V) == 8 && GP >= 2) {

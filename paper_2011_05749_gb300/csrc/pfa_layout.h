@@ -88,7 +88,7 @@ struct PassPlan {
 // twiddles.  Returns false when an axis is not supported or no split fits.
 inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t tile_target,
                              PassDesc* p1, PassDesc* p2, PassPlan* l1, PassPlan* l2,
-                             int32_t* tw_cursor, bool* two_pass)
+                             int32_t* tw_cursor, bool* two_pass, int64_t max_tile = 0)
 {
     const int64_t B = s->B;
     int32_t Ps[kMaxAxes];
@@ -97,7 +97,9 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
     for (int i = 0; i < n; ++i)
         if (!pfa_is_pow2(Ps[i]) && Ps[i] > 2049) return false;  // direct DFT: <= 1024 pairs
     const int64_t cap = (int64_t)max_smem - 1024;                // bytes for tile + twiddles
-    auto fits = [&](int64_t elems, int64_t tw) { return (pfa_even(elems) + tw) * (int64_t)esz <= cap; };
+    auto fits = [&](int64_t elems, int64_t tw) {
+        return (pfa_even(elems) + tw) * (int64_t)esz <= cap && (max_tile <= 0 || elems <= max_tile);
+    };
     int64_t tw_all = 0;
     for (int i = 0; i < n; ++i) tw_all += pfa_tw_elems(Ps[i]);
     int32_t order[kMaxAxes];
@@ -167,6 +169,7 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
     int64_t inner = 1, outer = 1;
     for (int i = 0; i < split; ++i) inner *= s->ax[i].P;
     for (int i = split; i < n; ++i) outer *= s->ax[i].P;
+    if (max_tile > 0 && max_tile < tile_target) tile_target = max_tile;
     int64_t Tb = tile_target / outer;
     if (Tb < 1) Tb = 1;
     if (Tb > inner) Tb = inner;
@@ -183,12 +186,12 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
 }
 
 // threads of a bucketization CTA: whole-stage tiles (one CTA per SM, shared memory bound)
-// get 512 threads (the kernel's launch bound); small two-pass tiles about one thread per 8
-// elements
+// get 512 threads (the kernel's launch bound); smaller two-pass tiles one thread per 16
+// elements, so that two CTAs fit an SM's registers
 inline int pfa_threads(int64_t tile, size_t)
 {
     if (tile >= 8192) return 512;
-    int64_t t = (tile / 8 + 31) / 32 * 32;
+    int64_t t = (tile / 16 + 31) / 32 * 32;
     return (int)(t < 128 ? 128 : (t > 512 ? 512 : t));
 }
 

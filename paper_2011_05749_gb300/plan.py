@@ -22,7 +22,8 @@ class Plan:
     def __init__(self, N: int, K: int, f, delays, *, dtype: str = "c64",
                  precision: str = "fp32", locate: str = "ml", noise_var: float = 0.0,
                  a_min: float = 1.0, eta: float = 0.0, c0: float = 4.0, c1: float = 2.0,
-                 max_rounds: int = 64, max_batch: int = 1):
+                 max_rounds: int = 64, max_batch: int = 1, max_tile: int = 0,
+                 wait_limit_log2: int = 0, fault_inject: int = 0):
         lib = load()
         f = np.ascontiguousarray(f, dtype=np.int64)
         delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -33,6 +34,9 @@ class Plan:
         o.locate = {"arg": _lib.LOCATE_ARG, "ml": _lib.LOCATE_ML}[locate]
         o.max_rounds = max_rounds
         o.max_batch = max_batch
+        o.max_tile = max_tile
+        o.wait_limit_log2 = wait_limit_log2
+        o.fault_inject = fault_inject
         o.noise_var = noise_var
         o.a_min = a_min
         o.eta = eta
