@@ -22,6 +22,7 @@ using namespace sfft;
 namespace sfft {
 cudaError_t set_bucketize_smem_limit(int max_smem);
 cudaError_t set_compact_smem_limit(int max_smem);
+cudaError_t set_classify_smem_limit(int max_smem);
 
 static thread_local char g_last_cuda[256] = "no error";
 
@@ -31,10 +32,17 @@ int cuda_fail(cudaError_t e)
     return SFFT_ECUDA;
 }
 
-#define CK(call)                               \
-    do {                                       \
-        cudaError_t e_ = (call);               \
-        if (e_ != cudaSuccess) return cuda_fail(e_); \
+static int cuda_fail_at(cudaError_t e, const char* what, int line)
+{
+    snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s (api.cu:%d %s)", cudaGetErrorName(e),
+             cudaGetErrorString(e), line, what);
+    return SFFT_ECUDA;
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail_at(e_, #call, __LINE__); \
     } while (0)
 
 static int64_t gcd64(int64_t a, int64_t b)
@@ -68,6 +76,7 @@ static int device_info(DevInfo* out)
         CK(cudaDeviceGetAttribute(&di.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         CK(set_bucketize_smem_limit(di.max_smem));
         CK(set_compact_smem_limit(di.max_smem));
+        CK(set_classify_smem_limit(di.max_smem - 16 * 1024));
         di.ok = true;
         cache[dev] = di;
     }
@@ -282,6 +291,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
                 tw_t.push_back(r < n_delays ? (int32_t)((q * pd.st[d].tauL[r]) % L) : 0);
             }
     }
+    p->wtab_elems = (int32_t)tw_P.size() - pd.st[0].wtab_off;
     pd.sumB = (int32_t)bin_base;
     pd.y_per_sig = (int64_t)bin_base * n_delays;
     p->smem1 = l1.smem;
@@ -495,6 +505,9 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     da.bpos = p->d_bpos;
     da.bins = bins;
     da.roots = p->d_tw;
+    da.wtab_elems = p->wtab_elems;
+    // phasor tables up to 96 KB go to shared memory (two classify CTAs per SM still fit)
+    da.wtab_smem = (size_t)p->wtab_elems * p->esz <= 96 * 1024 ? 1 : 0;
     const int threads = 512;
     const int total = p->num_sms * p->decode_occ;
     // later rounds touch O(K) bins: about one CTA per 256 expected single-tons

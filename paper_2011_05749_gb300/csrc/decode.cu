@@ -147,7 +147,8 @@ __device__ __forceinline__ void record_candidate(int32_t* ctr, const DecodeWs& w
 // the table reads are broadcasts.
 template <typename T>
 __device__ void locate_ml_thread(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
-                                 const typename C2<T>::t* Y, int round, int b)
+                                 const typename C2<T>::t* Y, const typename C2<T>::t* wtab,
+                                 int round, int b)
 {
     using V = typename C2<T>::t;
     const PlanDesc& pd = a.pd;
@@ -169,7 +170,7 @@ __device__ void locate_ml_thread(const DecodeArgs& a, int32_t* ctr, const Decode
             zy[r] = y.y * aj.x - y.x * aj.y;
         }
     }
-    const V* W = reinterpret_cast<const V*>(a.roots) + st.wtab_off;
+    const V* W = wtab + (st.wtab_off - pd.st[0].wtab_off);
     T best = (T)-1, bcx = 0, bcy = 0;
     int bq = 0;
     for (int q = 0; q < L; ++q) {
@@ -180,17 +181,18 @@ __device__ void locate_ml_thread(const DecodeArgs& a, int32_t* ctr, const Decode
             if (r < R) {
                 V w0, w1;
                 if constexpr (sizeof(V) == 8) {
-                    const float4 q4 = __ldg(reinterpret_cast<const float4*>(Wq + r));
+                    const float4 q4 = *reinterpret_cast<const float4*>(Wq + r);
                     w0 = V{q4.x, q4.y};
                     w1 = V{q4.z, q4.w};
                 } else {
-                    w0 = __ldg(Wq + r);
-                    w1 = __ldg(Wq + r + 1);
+                    w0 = Wq[r];
+                    w1 = Wq[r + 1];
                 }
-                cx0 += zx[r] * w0.x + zy[r] * w0.y;
-                cy0 += zy[r] * w0.x - zx[r] * w0.y;
-                cx1 += zx[r + 1] * w1.x + zy[r + 1] * w1.y;
-                cy1 += zy[r + 1] * w1.x - zx[r + 1] * w1.y;
+                // Z_r conj(w): (zx wx + zy wy, zy wx - zx wy), as fused multiply-adds
+                cx0 = fma(zx[r], w0.x, fma(zy[r], w0.y, cx0));
+                cy0 = fma(zy[r], w0.x, fma(-zx[r], w0.y, cy0));
+                cx1 = fma(zx[r + 1], w1.x, fma(zy[r + 1], w1.y, cx1));
+                cy1 = fma(zy[r + 1], w1.x, fma(-zx[r + 1], w1.y, cy1));
             }
         }
         const T cx = cx0 + cx1, cy = cy0 + cy1;
@@ -210,7 +212,7 @@ __device__ void locate_ml_thread(const DecodeArgs& a, int32_t* ctr, const Decode
 #pragma unroll
     for (int r = 0; r < kMaxDelays; ++r) {
         if (r < R) {
-            const V e = __ldg(Wb + r);
+            const V e = Wb[r];
             const T ex = zx[r] - (T)B * (v.x * e.x - v.y * e.y);
             const T ey = zy[r] - (T)B * (v.x * e.y + v.y * e.x);
             e2 += ex * ex + ey * ey;
@@ -261,8 +263,8 @@ __device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs
         for (int r = 0; r < kMaxDelays; ++r) {
             if (r < R) {
                 const V wv = __ldg(Wq + r);
-                cx += zx[r] * wv.x + zy[r] * wv.y;
-                cy += zy[r] * wv.x - zx[r] * wv.y;
+                cx = fma(zx[r], wv.x, fma(zy[r], wv.y, cx));
+                cy = fma(zy[r], wv.x, fma(-zx[r], wv.y, cy));
             }
         }
         const T sc = cx * cx + cy * cy;
@@ -444,9 +446,10 @@ __device__ __forceinline__ DecodeWs slot_ws(const DecodeArgs& a, int sig)
 
 // Round 1: classify every bin.  One CTA per tile of kClassifyTile bins of one signal.
 template <typename T>
-__global__ void __launch_bounds__(kClassifyThreads, 3) classify_kernel(const __grid_constant__ DecodeArgs a)
+__global__ void __launch_bounds__(kClassifyThreads, 2) classify_kernel(const __grid_constant__ DecodeArgs a)
 {
     using V = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_nz[kClassifyTile];
     __shared__ int s_cnt, s_res;
     const PlanDesc& pd = a.pd;
@@ -457,26 +460,46 @@ __global__ void __launch_bounds__(kClassifyThreads, 3) classify_kernel(const __g
     V* Y = reinterpret_cast<V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
     const int b0 = tile * kClassifyTile;
     const int b1 = min(pd.sumB, b0 + kClassifyTile);
+    // the stages' ML phasor tables, in shared memory when the launch gave room for them
+    const V* wtab = reinterpret_cast<const V*>(a.roots) + pd.st[0].wtab_off;
+    if (pd.locate == 1 && a.wtab_smem) {
+        V* ws = reinterpret_cast<V*>(smem_raw);
+        for (int i = threadIdx.x; i < a.wtab_elems; i += blockDim.x) ws[i] = wtab[i];
+        wtab = ws;
+    }
     if (threadIdx.x == 0) {
         s_cnt = 0;
         s_res = 0;
     }
     __syncthreads();
-    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+    // D1, two bins per thread in flight
+    for (int b = b0 + threadIdx.x; b < b1; b += 2 * blockDim.x) {
+        const int bb = b + blockDim.x;
+        const bool two = bb < b1;
+        const bool z0 = bin_is_zero<T>(pd, Y, b);
+        const bool z1 = two ? bin_is_zero<T>(pd, Y, bb) : true;
         __stcg((long long*)w.cand + b, -1ll);
         __stcg(w.dirty + b, 0u);
-        if (bin_is_zero<T>(pd, Y, b)) {
-            __stcg(w.state + b, (uint8_t)1);
+        __stcg(w.state + b, (uint8_t)(z0 ? 1 : 0));
+        if (z0)
             atomicAdd(&s_res, 1);
-        } else {
-            __stcg(w.state + b, (uint8_t)0);
+        else
             s_nz[atomicAdd(&s_cnt, 1)] = b;
+        if (two) {
+            __stcg((long long*)w.cand + bb, -1ll);
+            __stcg(w.dirty + bb, 0u);
+            __stcg(w.state + bb, (uint8_t)(z1 ? 1 : 0));
+            if (z1)
+                atomicAdd(&s_res, 1);
+            else
+                s_nz[atomicAdd(&s_cnt, 1)] = bb;
         }
     }
     __syncthreads();
     const int n_nz = s_cnt;
     if (pd.locate == 1) {
-        for (int i = threadIdx.x; i < n_nz; i += blockDim.x) locate_ml_thread<T>(a, w.ctr, w, Y, 1, s_nz[i]);
+        for (int i = threadIdx.x; i < n_nz; i += blockDim.x)
+            locate_ml_thread<T>(a, w.ctr, w, Y, wtab, 1, s_nz[i]);
     } else {
         for (int i = threadIdx.x; i < n_nz; i += blockDim.x) locate_arg_thread<T>(a, w.ctr, w, Y, 1, s_nz[i]);
     }
@@ -653,10 +676,11 @@ cudaError_t launch_classify(const DecodeArgs& a, int precision, cudaStream_t st)
     const int tiles = (a.pd.sumB + kClassifyTile - 1) / kClassifyTile;
     const unsigned grid = (unsigned)a.n_sig * (unsigned)tiles;
     if (grid == 0) return cudaSuccess;
+    const size_t smem = a.wtab_smem ? (size_t)a.wtab_elems * (precision == 1 ? 8 : 16) : 0;
     if (precision == 1)
-        classify_kernel<float><<<grid, kClassifyThreads, 0, st>>>(a);
+        classify_kernel<float><<<grid, kClassifyThreads, smem, st>>>(a);
     else
-        classify_kernel<double><<<grid, kClassifyThreads, 0, st>>>(a);
+        classify_kernel<double><<<grid, kClassifyThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -703,6 +727,16 @@ cudaError_t launch_compact(const CompactArgs& a, int precision, int xdouble, int
             compact_kernel<double, float><<<grid, threads, smem, st>>>(a);
     }
     return cudaGetLastError();
+}
+
+cudaError_t set_classify_smem_limit(int max_smem)
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(classify_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  max_smem)))
+        return e;
+    return cudaFuncSetAttribute(classify_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_smem);
 }
 
 cudaError_t set_compact_smem_limit(int max_smem)

@@ -185,7 +185,7 @@ __device__ void axis_fft_pow2(typename C2<T>::t* s, const typename C2<T>::t* tw,
                     const int t = (ii + (i & (hs - 1)) * h) << (log2P - 1 - lh - sg);
                     const V wv = tw[t];
                     const V u = v[i], x = v[i + hs];
-                    const V xt = {x.x * wv.x + x.y * wv.y, x.y * wv.x - x.x * wv.y};
+                    const V xt = {fma(x.x, wv.x, x.y * wv.y), fma(x.y, wv.x, -(x.x * wv.y))};
                     v[i] = V{u.x + xt.x, u.y + xt.y};
                     v[i + hs] = V{u.x - xt.x, u.y - xt.y};
                 }

@@ -29,6 +29,8 @@ struct DecodeArgs {
     int32_t n_sig;
     int32_t fault;        // 1: one CTA per group leaves before its first barrier (testing)
     long long spin_limit; // polls before a device-side wait gives up
+    int32_t wtab_elems;   // entries of all stages' ML phasor tables (from st[0].wtab_off)
+    int32_t wtab_smem;    // 1: classify stages them in shared memory
     const int32_t* pbin;  // position -> bin j, per stage at bin_base
     const int32_t* bpos;  // bin j -> position
     const void* roots;    // the plan's twiddle table: ML phasor tables at st[d].wtab_off

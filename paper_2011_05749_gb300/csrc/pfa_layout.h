@@ -37,7 +37,7 @@ inline int64_t pfa_inv_mod(int64_t a, int64_t m)
 // even number of elements, so every twiddle block starts on a 16-byte boundary
 inline int64_t pfa_even(int64_t n) { return (n + 1) & ~(int64_t)1; }
 
-// Prime-power factors of B: odd ones ascending, then the power of two.  -1 if more than cap.
+// Prime-power factors of B: odd ones descending, then the power of two.  -1 if more than cap.
 inline int pfa_prime_powers(int64_t B, int32_t* out, int cap)
 {
     int n = 0;
@@ -60,8 +60,10 @@ inline int pfa_prime_powers(int64_t B, int32_t* out, int cap)
         if (n == cap) return -1;
         out[n++] = (int32_t)B;
     }
+    // largest odd factor first (innermost): every other odd axis then has a stride of at
+    // least that factor, so the lanes of a warp walk consecutive shared-memory words
     for (int i = 1; i < n; ++i)
-        for (int k = i; k > 0 && out[k - 1] > out[k]; --k) {
+        for (int k = i; k > 0 && out[k - 1] < out[k]; --k) {
             const int32_t t = out[k];
             out[k] = out[k - 1];
             out[k - 1] = t;

@@ -182,20 +182,25 @@ def test_execute_rffast_124950(sfft, oracle_mod, prec, snr):
     assert_matches_oracle(idx, val, info, ref, prec)
 
 
-def test_execute_rffast_full_size_2097024(sfft, oracle_mod):
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_execute_rffast_full_size_2097024(sfft, oracle_mod, prec):
     """The benchmark workload (N = 127*128*129, R = 8, K = 1000, U[1,10], 20 dB) on the
-    FP32 path, against a full oracle decode of the same complex64 input."""
+    FP32 path and on the plain FP64 path, against a full oracle decode of the same
+    complex64 input."""
     p = synth.config_problem("rffast_2097024", seed=2)
     x64 = p.x.astype(np.complex64)
     Y = oracle_mod.bucketize(p.N, p.f, p.delays, x64.astype(np.complex128))
-    kw = dict(precision="fp32", locate="ml", noise_var=p.noise_var)
+    kw = dict(precision=prec, locate="ml", noise_var=p.noise_var)
     ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
-    plan = sfft.Plan(p.N, p.K, p.f, p.delays, **kw)
-    idx, val, info = plan.execute(to_dev(x64, np.complex64))
+    # the FP64 path returns complex128 values (same samples, widened)
+    dt = "c64" if prec == "fp32" else "c128"
+    plan = sfft.Plan(p.N, p.K, p.f, p.delays, dtype=dt, **kw)
+    xd = to_dev(x64, np.complex64) if prec == "fp32" else to_dev(x64.astype(np.complex128), np.complex128)
+    idx, val, info = plan.execute(xd)
     torch.cuda.synchronize()
     info = info.cpu().numpy()
     n = int(info[0])
-    assert_matches_oracle(idx[:n].cpu().numpy(), val[:n].cpu().numpy(), info, ref, "fp32")
+    assert_matches_oracle(idx[:n].cpu().numpy(), val[:n].cpu().numpy(), info, ref, prec)
     np.testing.assert_array_equal(idx[:n].cpu().numpy(), p.support)
 
 
