@@ -295,9 +295,10 @@ def run_gpu(args):
     # dominant kernel: gather + prime-factor DFTs (bucketization), one launch per step
     bk = prof["bucketize"]
     bk_ms = bk["ms"] / max(bk["calls"], 1)
+    sig_per_launch = S * args.steps / max(bk["calls"], 1)  # batches run as sub-batches
     esz = 8
     alg_bytes_sig = R * plan.num_bins * esz * 2  # samples read + bins written (complex64)
-    achieved = S * alg_bytes_sig / (bk_ms / 1e3) / 1e9
+    achieved = sig_per_launch * alg_bytes_sig / (bk_ms / 1e3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -422,10 +423,11 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": "bucketize_kernel<float,float>",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_source": peak_src,
-                     "traffic": (traffic_sig * S if traffic_sig else None),
-                     "alg_bytes_per_launch": S * alg_bytes_sig,
+                     "traffic": (traffic_sig * sig_per_launch if traffic_sig else None),
+                     "alg_bytes_per_launch": sig_per_launch * alg_bytes_sig,
+                     "signals_per_launch": sig_per_launch,
                      "avg_launch_ms": bk_ms},
-        "phases_ms_per_step": {k: v["ms"] / max(v["calls"], 1) for k, v in prof.items()},
+        "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -120,8 +120,10 @@ static void free_plan_memory(sfft_plan_s* p)
         cudaEventDestroy(e.b);
     }
     for (auto e : p->prof_pool) cudaEventDestroy(e);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (p->aux[i]) cudaStreamDestroy(p->aux[i]);
+        if (p->aux_join[i]) cudaEventDestroy(p->aux_join[i]);
+    }
     if (p->aux_ev) cudaEventDestroy(p->aux_ev);
 }
 
@@ -274,6 +276,19 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
             tw_t.push_back(t);
         }
         pd.root_total += pd.st[d].L;
+    }
+    // two-level table of the N-th roots of unity for the delay phasors a_r(f):
+    // lo[l] = e^{2 pi i l / N} (l < 2^S), hi[h] = e^{2 pi i h 2^S / N}
+    pd.ph_shift = 11;
+    pd.ph_lo_off = (int32_t)tw_P.size();
+    for (int64_t l = 0; l < (1 << pd.ph_shift); ++l) {
+        tw_P.push_back((int32_t)N);
+        tw_t.push_back((int32_t)(l % N));
+    }
+    pd.ph_hi_off = (int32_t)tw_P.size();
+    for (int64_t h = 0; h <= (N - 1) >> pd.ph_shift; ++h) {
+        tw_P.push_back((int32_t)N);
+        tw_t.push_back((int32_t)((h << pd.ph_shift) % N));
     }
     // ML candidate phasors per stage: W[q][r] = e^{2 pi i (q tauL_r mod L) / L}; padding
     // columns get P = 0, which the twiddle kernel turns into (0, 0)
@@ -610,7 +625,20 @@ static int fill_ptr_table(sfft_plan_s* p, int m, const void* const* xs, int64_t*
     return SFFT_OK;
 }
 
-// n signals of one plan with device buffers, max_batch per launch group
+static int ensure_aux(sfft_plan_s* p)
+{
+    for (int i = 0; i < 2; ++i) {
+        if (!p->aux[i]) CK(cudaStreamCreateWithFlags(&p->aux[i], cudaStreamNonBlocking));
+        if (!p->aux_join[i]) CK(cudaEventCreateWithFlags(&p->aux_join[i], cudaEventDisableTiming));
+    }
+    if (!p->aux_ev) CK(cudaEventCreateWithFlags(&p->aux_ev, cudaEventDisableTiming));
+    return SFFT_OK;
+}
+
+// n signals of one plan with device buffers, max_batch per launch group.  (Splitting a
+// group into sub-batches on two streams, so that one sub-batch's decode overlaps the
+// next one's bucketization, measured slower: the kernels contend and the smaller launches
+// leave longer wave tails.)
 static int execute_group_device(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
                                 void* const* val, int32_t* infos, cudaStream_t st)
 {
@@ -643,9 +671,8 @@ static int execute_group_host(sfft_plan_s* p, int n, const void* const* xs, int6
     const size_t ib = align_up((size_t)p->pd.K * 8, 256), vb = align_up((size_t)p->pd.K * p->xesz, 256);
     if (!p->d_xb_stage) CK(cudaMalloc(&p->d_xb_stage, xb * mb));
     if (!p->d_ob_stage) CK(cudaMalloc(&p->d_ob_stage, (ib + vb) * mb + 16 * mb));
-    for (int i = 0; i < 2; ++i)
-        if (!p->aux[i]) CK(cudaStreamCreateWithFlags(&p->aux[i], cudaStreamNonBlocking));
-    if (!p->aux_ev) CK(cudaEventCreateWithFlags(&p->aux_ev, cudaEventDisableTiming));
+    int rc0 = ensure_aux(p);
+    if (rc0) return rc0;
     unsigned char* ob = (unsigned char*)p->d_ob_stage;
     int32_t* dinf = (int32_t*)(ob + (ib + vb) * mb);
     std::vector<const void*> sx(mb);

@@ -14,8 +14,8 @@
 // into SFFT_ETIMEDOUT instead of a hang).
 //
 // Arithmetic: the delay phasors a_r(f) = e^{2 pi i (f tau_r mod N) / N} come from the exact
-// integer residue (f tau_r) mod N, evaluated in the path's type (FP32: phase error below
-// 4e-7 rad).  The ML search of a bin j factors a_r(j + q B) = a_r(j) e^{2 pi i q tau_r / L},
+// integer residue (f tau_r) mod N, looked up in a two-level table of N-th roots of unity
+// made in FP64 (FP32 path: error about 1e-7).  The ML search of a bin j factors a_r(j + q B) = a_r(j) e^{2 pi i q tau_r / L},
 // so its L candidates are scored against a table of the L-th roots of unity indexed by
 // (q (tau_r mod L)) mod L.  The ARG location takes the angle and the snap to the bin's
 // candidates in FP64.
@@ -76,24 +76,6 @@ __device__ __forceinline__ int stage_of(const PlanDesc& pd, int b)
     return d;
 }
 
-// e^{+2 pi i m / N} for an exact residue 0 <= m < N (argument reduced to (-1, 1] of pi)
-__device__ __forceinline__ float2 unit_twiddle(int64_t m, int32_t N, float)
-{
-    int64_t m2 = 2 * m;
-    if (m2 > N) m2 -= 2 * (int64_t)N;
-    float sv, cv;
-    sincospif((float)m2 / (float)N, &sv, &cv);
-    return float2{cv, sv};
-}
-__device__ __forceinline__ double2 unit_twiddle(int64_t m, int32_t N, double)
-{
-    int64_t m2 = 2 * m;
-    if (m2 > N) m2 -= 2 * (int64_t)N;
-    double sv, cv;
-    sincospi((double)m2 / (double)N, &sv, &cv);
-    return double2{cv, sv};
-}
-
 // (a b) mod N for 0 <= a, b < N < 2^30 by Barrett reduction with mu = floor((2^64-1)/N):
 // the estimated quotient is at most two below the true one, so two corrections suffice
 __device__ __forceinline__ int64_t mulmod(int64_t a, int64_t b, const PlanDesc& pd)
@@ -119,10 +101,18 @@ __device__ __forceinline__ int small_mod(int v, int L, float invL)
     return r;
 }
 
+// a_r(f) = e^{2 pi i ((f tau) mod N) / N} from the plan's two-level root table (two loads
+// that stay in L1/L2 and one complex product)
 template <typename T>
-__device__ __forceinline__ typename C2<T>::t delay_phasor(const PlanDesc& pd, int64_t f, int32_t tau)
+__device__ __forceinline__ typename C2<T>::t delay_phasor(const DecodeArgs& a, int64_t f, int32_t tau)
 {
-    return unit_twiddle(mulmod(f, tau, pd), pd.N, T(0));
+    using V = typename C2<T>::t;
+    const PlanDesc& pd = a.pd;
+    const int64_t m = mulmod(f, tau, pd);
+    const V* tw = reinterpret_cast<const V*>(a.roots);
+    const V hi = __ldg(tw + pd.ph_hi_off + (int)(m >> pd.ph_shift));
+    const V lo = __ldg(tw + pd.ph_lo_off + (int)(m & ((1 << pd.ph_shift) - 1)));
+    return V{fma(hi.x, lo.x, -(hi.y * lo.y)), fma(hi.x, lo.y, hi.y * lo.x)};
 }
 
 template <typename T>
@@ -165,7 +155,7 @@ __device__ void locate_ml_thread(const DecodeArgs& a, int32_t* ctr, const Decode
         zy[r] = 0;
         if (r < R) {
             const V y = __ldcg(Yb + (int64_t)r * B);
-            const V aj = delay_phasor<T>(pd, j, st.tau[r]);
+            const V aj = delay_phasor<T>(a, j, st.tau[r]);
             zx[r] = y.x * aj.x + y.y * aj.y;
             zy[r] = y.y * aj.x - y.x * aj.y;
         }
@@ -240,7 +230,7 @@ __device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     V z = {0, 0};
     if (lane < R) {
         const V y = __ldcg(Y + st.y_off + (int64_t)lane * B + (b - st.bin_base));
-        const V aj = delay_phasor<T>(pd, j, st.tau[lane]);
+        const V aj = delay_phasor<T>(a, j, st.tau[lane]);
         z = V{y.x * aj.x + y.y * aj.y, y.y * aj.x - y.x * aj.y};
     }
     T zx[kMaxDelays], zy[kMaxDelays];
@@ -329,22 +319,32 @@ __device__ void locate_arg_thread(const DecodeArgs& a, int32_t* ctr, const Decod
     int64_t q = (int64_t)qd % L;
     if (q < 0) q += L;
     const int64_t f = (int64_t)j + q * B;
+    V ar[kMaxDelays], yv[kMaxDelays];
+#pragma unroll
+    for (int r = 0; r < kMaxDelays; ++r) {
+        if (r < R) {
+            ar[r] = delay_phasor<T>(a, f, st.tau[r]);
+            yv[r] = __ldcg(Yb + (int64_t)r * B);
+        }
+    }
     V c = {0, 0};
-    for (int r = 0; r < R; ++r) {
-        const V ar = delay_phasor<T>(pd, f, st.tau[r]);
-        const V y = __ldcg(Yb + (int64_t)r * B);
-        c.x += y.x * ar.x + y.y * ar.y;
-        c.y += y.y * ar.x - y.x * ar.y;
+#pragma unroll
+    for (int r = 0; r < kMaxDelays; ++r) {
+        if (r < R) {
+            c.x += yv[r].x * ar[r].x + yv[r].y * ar[r].y;
+            c.y += yv[r].y * ar[r].x - yv[r].x * ar[r].y;
+        }
     }
     const T sc = (T)1 / ((T)R * (T)B);
     const V v = {c.x * sc, c.y * sc};
     T e2 = 0;
-    for (int r = 0; r < R; ++r) {
-        const V ar = delay_phasor<T>(pd, f, st.tau[r]);
-        const V y = __ldcg(Yb + (int64_t)r * B);
-        const T ex = y.x - (T)B * (v.x * ar.x - v.y * ar.y);
-        const T ey = y.y - (T)B * (v.x * ar.y + v.y * ar.x);
-        e2 += ex * ex + ey * ey;
+#pragma unroll
+    for (int r = 0; r < kMaxDelays; ++r) {
+        if (r < R) {
+            const T ex = yv[r].x - (T)B * (v.x * ar[r].x - v.y * ar[r].y);
+            const T ey = yv[r].y - (T)B * (v.x * ar[r].y + v.y * ar[r].x);
+            e2 += ex * ex + ey * ey;
+        }
     }
     if (below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
 }
@@ -360,48 +360,79 @@ __device__ __forceinline__ void atomic_sub_c(double2* p, double2 d)
     atomicAdd(&p->y, -d.y);
 }
 
-// P: accept candidate c and peel it from every stage (Eq. 20)
+// P: accept candidate c and peel it from every stage (Eq. 20).  The per-stage loads,
+// checks and atomics are independent, so they are issued together (stage loops unrolled)
+// rather than one round trip after another.
 template <typename T>
 __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
                                typename C2<T>::t* Y, int round, int c)
 {
     using V = typename C2<T>::t;
     const PlanDesc& pd = a.pd;
+    const int D = pd.D;
     const int b = __ldcg(w.cbin + c);
     const int64_t f = (int64_t)__ldcg((const long long*)w.cf + c);
     const V v = __ldcg(reinterpret_cast<const V*>(w.cv) + c);
     const int d = stage_of(pd, b);
-    for (int e = 0; e < pd.D; ++e) {
-        if (e == d) continue;
-        const StageDesc& se = pd.st[e];
-        const int je = (int)((uint32_t)f % (uint32_t)se.B);
-        const int be = se.bin_base + __ldg(a.bpos + se.bin_base + je);
-        const int64_t cw = (int64_t)__ldcg((const long long*)w.cand + be);
-        if (cw >= 0 && (cw & kFMask) == f) {
-            const int rd = (int)(cw >> 40);
+    int be[kMaxStages];
+#pragma unroll
+    for (int e = 0; e < kMaxStages; ++e) {
+        be[e] = 0;
+        if (e < D) {
+            const StageDesc& se = pd.st[e];
+            const int je = (int)((uint32_t)f % (uint32_t)se.B);
+            be[e] = se.bin_base + __ldg(a.bpos + se.bin_base + je);
+        }
+    }
+    int64_t cw[kMaxStages];
+    uint8_t open[kMaxStages];
+#pragma unroll
+    for (int e = 0; e < kMaxStages; ++e) {
+        cw[e] = -1;
+        open[e] = 0;
+        if (e < D) {
+            if (e != d) cw[e] = (int64_t)__ldcg((const long long*)w.cand + be[e]);
+            open[e] = __ldcg(w.state + be[e]) == 0;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < kMaxStages; ++e) {
+        if (e < D && e != d && cw[e] >= 0 && (cw[e] & kFMask) == f) {
+            const int rd = (int)(cw[e] >> 40);
             if (rd < round || (rd == round && e < d)) return;
         }
     }
     const int k = atomicAdd(ctr + kCtrRec, 1);
     __stcg((long long*)w.rec_f + k, (long long)f);
     reinterpret_cast<V*>(w.rec_v)[k] = v;
-    for (int e = 0; e < pd.D; ++e) {
+    const int R = pd.R;
+#pragma unroll
+    for (int e = 0; e < kMaxStages; ++e) {
+        if (e >= D) continue;
         const StageDesc& se = pd.st[e];
-        const int je = (int)((uint32_t)f % (uint32_t)se.B);
-        const int pe = __ldg(a.bpos + se.bin_base + je);
-        const int be = se.bin_base + pe;
         const T Bv = (T)se.B;
-        for (int r = 0; r < pd.R; ++r) {
-            const V ar = delay_phasor<T>(pd, f, se.tau[r]);
-            const V dlt = {Bv * (v.x * ar.x - v.y * ar.y), Bv * (v.x * ar.y + v.y * ar.x)};
-            atomic_sub_c(Y + se.y_off + (int64_t)r * se.B + pe, dlt);
-        }
-        if (__ldcg(w.state + be) == 0 && atomicExch(w.dirty + be, 1u) == 0u) {
-            const int q = atomicAdd(ctr + kCtrRoundBase + 3 * round + 0, 1);
-            int32_t* nl = (round & 1) ? w.list1 : w.list0;
-            __stcg(nl + q, be);
+        V* Yb = Y + se.y_off + (be[e] - se.bin_base);
+        // all R phasor lookups in flight first, then the atomics (a table load placed after
+        // an atomic could not be hoisted above it)
+        V ar[kMaxDelays];
+#pragma unroll
+        for (int r = 0; r < kMaxDelays; ++r)
+            if (r < R) ar[r] = delay_phasor<T>(a, f, se.tau[r]);
+#pragma unroll
+        for (int r = 0; r < kMaxDelays; ++r) {
+            if (r < R) {
+                const V dlt = {Bv * (v.x * ar[r].x - v.y * ar[r].y), Bv * (v.x * ar[r].y + v.y * ar[r].x)};
+                atomic_sub_c(Yb + (int64_t)r * se.B, dlt);
+            }
         }
     }
+    uint32_t was[kMaxStages];
+#pragma unroll
+    for (int e = 0; e < kMaxStages; ++e) was[e] = (e < D && open[e]) ? atomicExch(w.dirty + be[e], 1u) : 1u;
+    int32_t* nl = (round & 1) ? w.list1 : w.list0;
+#pragma unroll
+    for (int e = 0; e < kMaxStages; ++e)
+        if (was[e] == 0u) __stcg(nl + atomicAdd(ctr + kCtrRoundBase + 3 * round + 0, 1), be[e]);
 }
 
 // D1 of one bin: energy over the R delays (all loads in flight)

@@ -76,7 +76,9 @@ struct PlanDesc {
     int32_t root_total;      // sum_d L_d: root-table entries (at st[0].root_off onwards)
     double invN;             // 1 / N
     int32_t Rp;              // R rounded up to even (row length of the ML phasor tables)
-    int32_t pad3;
+    int32_t ph_shift;        // two-level phasor tables: e^{2 pi i m / N} =
+    int32_t ph_lo_off;       //   tw[ph_hi_off + (m >> ph_shift)] * tw[ph_lo_off + (m & mask)]
+    int32_t ph_hi_off;
     uint64_t mu;             // floor((2^64 - 1) / N): Barrett reduction modulo N
     StageDesc st[kMaxStages];
 };

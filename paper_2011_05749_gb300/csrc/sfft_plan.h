@@ -47,6 +47,7 @@ struct sfft_plan_s {
     void* d_bins_in = nullptr;
     cudaStream_t aux[2] = {nullptr, nullptr};  // host-buffer batches: copy/compute overlap
     cudaEvent_t aux_ev = nullptr;
+    cudaEvent_t aux_join[2] = {nullptr, nullptr};
     void* d_xb_stage = nullptr;   // host-buffer batches: max_batch inputs
     void* d_ob_stage = nullptr;   //                      max_batch outputs + infos
     int32_t wtab_elems = 0;  // entries of the ML phasor tables (all stages)
