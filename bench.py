@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--max-tile", type=int, default=0,
                     help="largest DFT tile per CTA in elements (0: shared-memory limit)")
+    ap.add_argument("--serve-rate", type=float, default=20000.0,
+                    help="mean Poisson arrival rate of the serving measurement (requests/s)")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip sfft_autotune and use the default schedule")
     ap.add_argument("--timed-only", action="store_true",
                     help="run only the timed batched loop (for profiler captures)")
     return ap.parse_args()
@@ -235,6 +240,40 @@ def kernel_traffic(kernel: str, src_files, per_unit_key: str):
     return rec.get(per_unit_key)
 
 
+def measure_serving(sfft, plan, signals, rate, seconds, seed):
+    """Submit requests (one workload signal each) at Poisson arrival times for `seconds`,
+    then drain; latency = submit to completion, as the server measures it."""
+    import torch
+    rng = np.random.default_rng(seed + 99)
+    n = max(1, int(rate * seconds))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    srv = sfft.Server(hbm_budget=16 << 30, max_slots=16)
+    ring = 4096
+    outs = [plan.empty_outputs() for _ in range(min(ring, n))]
+    slot_ticket = [0] * len(outs)
+    tickets = []
+    t0 = time.perf_counter()
+    for i in range(n):
+        while time.perf_counter() - t0 < arrivals[i]:
+            pass
+        k = i % len(outs)
+        if slot_ticket[k]:
+            while srv.poll(slot_ticket[k])[0] == 1:  # ring slot still in use
+                pass
+        t = srv.submit(plan, signals[i % len(signals)], outs[k])
+        slot_ticket[k] = t
+        tickets.append(t)
+    srv.drain()
+    t1 = time.perf_counter()
+    torch.cuda.synchronize()
+    lat = sorted(srv.poll(t)[1] for t in tickets)
+    srv.close()
+    return {"offered_rate": rate, "requests": n, "completed_rate": n / (t1 - t0),
+            "p50_us": lat[len(lat) // 2], "p99_us": lat[int(len(lat) * 0.99) - 1],
+            "workload": "one rffast_2097024 signal per request, continuous batching, "
+                        "up to 32 requests per launch group, 16 groups in flight"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -264,8 +303,14 @@ def run_gpu(args):
     xs = torch.empty((S, N), dtype=torch.complex64, device=dev)
     for i in range(S):
         xs[i].copy_(distinct[i % N_DISTINCT])
-    plan = sfft.Plan(N, K, f, delays, precision="fp32", locate="ml", noise_var=nv,
-                     max_batch=S, max_tile=args.max_tile)
+    plan_kw = dict(precision="fp32", locate="ml", noise_var=nv, max_batch=S,
+                   max_tile=args.max_tile)
+    tune_rate = None
+    if not args.no_autotune and args.max_tile == 0:
+        # schedule chosen by the library's autotuner on this batch (untimed)
+        plan_kw, tune_rate = sfft.autotune(N, K, f, delays, list(xs), precision="fp32",
+                                           locate="ml", noise_var=nv)
+    plan = sfft.Plan(N, K, f, delays, **plan_kw)
     out = plan.empty_outputs("cuda", S)
     stream = torch.cuda.current_stream()
 
@@ -391,6 +436,14 @@ def run_gpu(args):
         e2e = {"value": None, "unit": "signals/s", "error": repr(exc)[:200],
                "h2d_bytes_per_step": S * N * 8, "d2h_bytes_per_step": S * (K * 16 + 16)}
 
+    # serving: Poisson arrivals into the continuous-batching server (sfft_submit/poll)
+    serving = None
+    try:
+        serving = measure_serving(sfft, plan1, distinct, args.serve_rate, args.serve_seconds,
+                                  args.seed)
+    except Exception as exc:  # report, never fall back
+        serving = {"error": repr(exc)[:200]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, nsig, secs = oracle_rate(args.seed, args.cpu_seconds)
@@ -408,7 +461,10 @@ def run_gpu(args):
                                "K=1000, |xhat|~U[1,10], SNR 20 dB; FP32 bulk, FP64 locate/fit",
                    "global_batch": S * world, "signals_per_step_per_gpu": S,
                    "distinct_signals": N_DISTINCT, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (S x 16.8 MB resident), no flush"},
+                   "l2": "inputs larger than L2 (S x 16.8 MB resident), no flush",
+                   "schedule": {"decode_ctas": plan_kw.get("decode_ctas", 0),
+                                "max_tile": plan_kw.get("max_tile", 0),
+                                "autotuned": tune_rate is not None}},
         "latency_us": {"p50": lat[len(lat) // 2], "p99": lat[int(len(lat) * 0.99) - 1],
                        "path": "sfft_execute, one signal per call, device buffers"},
         "accuracy": {"support_equal_fp64_plain": f"{sup_eq}/{len(probs)}",
@@ -431,6 +487,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "serving": serving,
         "clocks": clk,
     }
     if rank == 0:

@@ -95,6 +95,8 @@ typedef struct {
                                  group leaves before its first barrier, so the others' wait
                                  runs out (status SFFT_ETIMEDOUT); 2 = plan creation fails
                                  with SFFT_ENOMEM before allocating */
+    int32_t decode_ctas;      /* CTAs per signal in the peeling rounds; 0 = automatic */
+    int32_t reserved;
 } sfft_opts;
 
 /* Fill *opts with the defaults above. */
@@ -164,6 +166,16 @@ int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t* f, int32_t
  * not modified).  Outputs as sfft_execute.  Device pointers only.                         */
 int sfft_decode_bins(sfft_plan_t plan, const void* bins, int64_t* out_idx, void* out_val,
                      int32_t* out_info, void* stream);
+
+/* Autotuning (no counterpart in the paper).  Times sfft_execute_batch on the caller's n
+ * sample signals (device pointers, dtype of *base) for a set of schedules -- the CTAs per
+ * signal of the peeling rounds and the largest DFT tile per CTA -- and writes the fastest
+ * into *best (a copy of *base with those fields set, max_batch = n) and its rate in
+ * signals/s into *best_rate (may be NULL).  Creates and destroys its own plans; the
+ * stream is synchronised.                                                                 */
+int sfft_autotune(int64_t N, int32_t K, int32_t n_stages, const int64_t* f, int32_t n_delays,
+                  const int64_t* delays, const sfft_opts* base, int32_t n, const void* const* xs,
+                  void* stream, sfft_opts* best, double* best_rate);
 
 /* Phase timing.  While enabled, every execute call brackets its bucketization, decode and
  * compaction launches with CUDA events on the launch stream.  sfft_plan_profile waits for

@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
                 ("max_batch", ctypes.c_int32), ("max_tile", ctypes.c_int32),
                 ("noise_var", ctypes.c_double), ("a_min", ctypes.c_double),
                 ("eta", ctypes.c_double), ("c0", ctypes.c_double), ("c1", ctypes.c_double),
-                ("wait_limit_log2", ctypes.c_int32), ("fault_inject", ctypes.c_int32)]
+                ("wait_limit_log2", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
+                ("decode_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -78,6 +79,10 @@ EXPORTS = {
                                              ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                              ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p]),
+    "sfft_autotune": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(Opts),
+                                     ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double)]),
     "sfft_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sfft_last_cuda_error": (ctypes.c_char_p, []),
 }

@@ -157,7 +157,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         }
     }
     if (o.fault_inject == 2) return SFFT_ENOMEM;  // injected allocation failure (testing)
-    if (o.wait_limit_log2 < 0 || o.fault_inject < 0 || o.fault_inject > 2) return SFFT_EINVAL;
+    if (o.wait_limit_log2 < 0 || o.fault_inject < 0 || o.fault_inject > 2 || o.decode_ctas < 0)
+        return SFFT_EINVAL;
     DevInfo di;
     int rc = device_info(&di);
     if (rc) return rc;
@@ -529,6 +530,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     int G = 1;
     if (n < total) {
         G = (int)std::min<int64_t>(total / n, ((int64_t)pd.K + 255) / 256);
+        if (p->opts.decode_ctas > 0) G = (int)std::min<int64_t>(total / n, p->opts.decode_ctas);
         G = std::max(G, 1);
     }
     da.G = G;
@@ -777,6 +779,75 @@ extern "C" int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const voi
             }
         }
     }
+    return SFFT_OK;
+}
+
+extern "C" int sfft_autotune(int64_t N, int32_t K, int32_t n_stages, const int64_t* f,
+                             int32_t n_delays, const int64_t* delays, const sfft_opts* base,
+                             int32_t n, const void* const* xs, void* stream, sfft_opts* best,
+                             double* best_rate)
+{
+    if (!base || !best || !xs || n < 1) return SFFT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ctas[] = {0, 1, 2, 4, 8};
+    const int tiles[] = {0, 8192};
+    double best_v = -1;
+    sfft_opts bo = *base;
+    std::vector<int64_t*> idx(n);
+    std::vector<void*> val(n);
+    int32_t* infos = nullptr;
+    void* outbuf = nullptr;
+    const size_t xesz = base->dtype == SFFT_C128 ? 16 : 8;
+    const size_t per = align_up((size_t)K * 8, 256) + align_up((size_t)K * xesz, 256);
+    CK(cudaMalloc(&outbuf, per * n));
+    CK(cudaMalloc((void**)&infos, 16 * (size_t)n));
+    for (int i = 0; i < n; ++i) {
+        idx[i] = (int64_t*)((unsigned char*)outbuf + per * i);
+        val[i] = (unsigned char*)outbuf + per * i + align_up((size_t)K * 8, 256);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = SFFT_OK;
+    for (int tile : tiles) {
+        for (int g : ctas) {
+            sfft_opts o = *base;
+            o.max_batch = n;
+            o.decode_ctas = g;
+            o.max_tile = tile;
+            sfft_plan_t p = nullptr;
+            if (sfft_plan_create(&p, N, K, n_stages, f, n_delays, delays, &o) != SFFT_OK) continue;
+            std::vector<sfft_plan_t> ps(n, p);
+            int r = SFFT_OK;
+            for (int w = 0; w < 2 && r == SFFT_OK; ++w)
+                r = sfft_execute_batch(n, ps.data(), xs, idx.data(), val.data(), infos, st);
+            const int reps = 3;
+            cudaEventRecord(e0, st);
+            for (int w = 0; w < reps && r == SFFT_OK; ++w)
+                r = sfft_execute_batch(n, ps.data(), xs, idx.data(), val.data(), infos, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            sfft_plan_destroy(p);
+            if (r != SFFT_OK) {
+                rc = r;
+                continue;
+            }
+            const double v = (double)n * reps / (ms / 1e3);
+            if (v > best_v) {
+                best_v = v;
+                bo = o;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(outbuf);
+    cudaFree(infos);
+    if (best_v < 0) return rc ? rc : SFFT_EINVAL;
+    *best = bo;
+    if (best_rate) *best_rate = best_v;
     return SFFT_OK;
 }
 

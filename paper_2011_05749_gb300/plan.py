@@ -23,7 +23,7 @@ class Plan:
                  precision: str = "fp32", locate: str = "ml", noise_var: float = 0.0,
                  a_min: float = 1.0, eta: float = 0.0, c0: float = 4.0, c1: float = 2.0,
                  max_rounds: int = 64, max_batch: int = 1, max_tile: int = 0,
-                 wait_limit_log2: int = 0, fault_inject: int = 0):
+                 wait_limit_log2: int = 0, fault_inject: int = 0, decode_ctas: int = 0):
         lib = load()
         f = np.ascontiguousarray(f, dtype=np.int64)
         delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -37,6 +37,7 @@ class Plan:
         o.max_tile = max_tile
         o.wait_limit_log2 = wait_limit_log2
         o.fault_inject = fault_inject
+        o.decode_ctas = decode_ctas
         o.noise_var = noise_var
         o.a_min = a_min
         o.eta = eta
@@ -158,6 +159,36 @@ def execute_batch(plans, xs, out, stream=None):
                                     ctypes.cast(hv, ctypes.c_void_p), ptr_of(infos),
                                     stream_handle(stream)), "sfft_execute_batch")
     return out
+
+
+def autotune(N: int, K: int, f, delays, xs, stream=None, **plan_kw):
+    """sfft_autotune: time the schedules on the sample signals xs (device tensors) and return
+    (plan keyword arguments of the fastest, its signals/s).  plan_kw as for Plan."""
+    lib = load()
+    tmp = Plan(N, K, f, delays, **{**plan_kw, "max_batch": 1})  # validates and fills opts
+    o = _lib.Opts()
+    lib.sfft_opts_default(ctypes.byref(o))
+    o.dtype = {"c64": _lib.C64, "c128": _lib.C128}[tmp.dtype]
+    o.precision = {"fp32": _lib.PREC_FP32, "fp64": _lib.PREC_FP64}[tmp.precision]
+    o.locate = {"arg": _lib.LOCATE_ARG, "ml": _lib.LOCATE_ML}[tmp.locate]
+    for k in ("noise_var", "a_min", "eta", "c0", "c1", "max_rounds"):
+        if k in plan_kw:
+            setattr(o, k, plan_kw[k])
+    tmp.close()
+    f = np.ascontiguousarray(f, dtype=np.int64)
+    delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
+    n = len(xs)
+    P = ctypes.c_void_p * n
+    hx = P(*[ptr_of(x) for x in xs])
+    best = _lib.Opts()
+    rate = ctypes.c_double()
+    check(lib.sfft_autotune(N, K, f.size, f.ctypes.data, delays.shape[1], delays.ctypes.data,
+                            ctypes.byref(o), n, ctypes.cast(hx, ctypes.c_void_p),
+                            stream_handle(stream), ctypes.byref(best), ctypes.byref(rate)),
+          "sfft_autotune")
+    kw = dict(plan_kw)
+    kw.update(max_batch=best.max_batch, decode_ctas=best.decode_ctas, max_tile=best.max_tile)
+    return kw, rate.value
 
 
 def bucketize_static(N: int, f, delays, x, bins, precision: str = "fp32",

@@ -308,3 +308,71 @@ def test_server_matches_direct(sfft):
         np.testing.assert_array_equal(o[0][:n].cpu().numpy(), i1[:n].cpu().numpy())
         assert rel_l2(o[1][:n].cpu().numpy(), v1[:n].cpu().numpy()) <= 1e-6
     srv.close()
+
+
+def test_large_signal_exact_recovery_134217216(sfft):
+    """N = 511*512*513 (1.07 GB of complex64), ten delays, K = 10,000 exactly sparse:
+    every stage is two-pass in FP32.  Too large for a full oracle decode, so the check is a
+    property that holds at any size: exact support and values to FP32 rounding against
+    the generator's truth (the oracle pins the bins by sampled dot products in
+    test_bucketize_large_sampled)."""
+    p = synth.config_problem("rffast_134217216", seed=5, snr_db=None)
+    plan = sfft.Plan(p.N, p.K, p.f, p.delays, precision="fp32", locate="ml")
+    x = to_dev(p.x, np.complex64)
+    idx, val, info = plan.execute(x)
+    torch.cuda.synchronize()
+    info = info.cpu().numpy()
+    n = int(info[0])
+    assert info[1] == 0 and n == p.K, info
+    np.testing.assert_array_equal(idx[:n].cpu().numpy(), p.support)
+    assert rel_l2(val[:n].cpu().numpy(), p.values) <= 1e-5
+
+
+def test_mixed_batch_matches_single(sfft):
+    """Batched mix in one sfft_execute_batch call: three signal lengths (9660, 124950,
+    2097024) x two SNR classes, interleaved; each signal's result equals its single-signal
+    result and recovers the truth."""
+    shapes = [(9660, (20, 21, 23), 6, 20), (124950, (49, 50, 51), 6, 100),
+              (2097024, (127, 128, 129), 6, 300)]
+    plans, probs = [], []
+    for N, f, R, K in shapes:
+        rng = np.random.default_rng(N)
+        delays = synth.draw_delays(N, 3, R, rng)
+        for snr in (40.0, 25.0):
+            ps = [synth.make_problem(N, f, K, seed=N % 97 + 10 * i + int(snr), R=R,
+                                     delays=delays, mag=(1.0, 10.0), snr_db=snr)
+                  for i in range(3)]
+            nv = float(np.mean([q.noise_var for q in ps]))
+            pl = sfft.Plan(N, K, f, delays, precision="fp32", noise_var=nv, max_batch=4)
+            plans += [pl] * len(ps)
+            probs += ps
+    order = np.random.default_rng(0).permutation(len(probs))
+    plans = [plans[i] for i in order]
+    probs = [probs[i] for i in order]
+    xs = [to_dev(q.x, np.complex64) for q in probs]
+    outs = [pl.empty_outputs() for pl in plans]
+    infos = torch.zeros((len(plans), 4), dtype=torch.int32, device="cuda")
+    sfft.execute_batch(plans, xs, ([o[0] for o in outs], [o[1] for o in outs], infos))
+    torch.cuda.synchronize()
+    for i, (pl, q) in enumerate(zip(plans, probs)):
+        i1, v1, f1 = pl.execute(xs[i])
+        torch.cuda.synchronize()
+        n = int(f1[0])
+        assert int(infos[i, 0]) == n
+        np.testing.assert_array_equal(outs[i][0][:n].cpu().numpy(), i1[:n].cpu().numpy())
+        assert rel_l2(outs[i][1][:n].cpu().numpy(), v1[:n].cpu().numpy()) <= 1e-6
+        np.testing.assert_array_equal(i1[:n].cpu().numpy(), q.support)
+
+
+def test_autotune_returns_working_schedule(sfft):
+    probs = [synth.make_problem(124950, (49, 50, 51), 60, seed=300 + i, R=6,
+                                delays=np.array([[0, 1, 11, 222, 3333, 44444]] * 3),
+                                mag=(1.0, 10.0)) for i in range(4)]
+    xs = [to_dev(p.x, np.complex64) for p in probs]
+    kw, rate = sfft.autotune(124950, 60, (49, 50, 51), probs[0].delays, xs, precision="fp32")
+    assert rate > 0 and kw["max_batch"] == 4 and kw["decode_ctas"] >= 0
+    plan = sfft.Plan(124950, 60, (49, 50, 51), probs[0].delays, **kw)
+    idx, val, infos = plan.execute_many(torch.stack(xs))
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        np.testing.assert_array_equal(idx[i, :int(infos[i, 0])].cpu().numpy(), p.support)
