@@ -291,24 +291,28 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         tw_P.push_back((int32_t)N);
         tw_t.push_back((int32_t)((h << pd.ph_shift) % N));
     }
-    // ML candidate phasors per stage: W[q][r] = e^{2 pi i (q tauL_r mod L) / L}; padding
-    // columns get P = 0, which the twiddle kernel turns into (0, 0)
-    pd.Rp = (n_delays + 1) & ~1;
+    // ML candidate phasors per stage: W[r][q] = e^{2 pi i (q tauL_r mod L) / L}, a row of L
+    // candidates per delay
     for (int d = 0; d < n_stages; ++d) {
-        if (tw_P.size() & 1) {  // 16-byte aligned rows
-            tw_P.push_back(0);
-            tw_t.push_back(0);
-        }
         pd.st[d].wtab_off = (int32_t)tw_P.size();
         const int64_t L = pd.st[d].L;
-        for (int64_t q = 0; q < L; ++q)
-            for (int r = 0; r < pd.Rp; ++r) {
-                tw_P.push_back(r < n_delays ? (int32_t)L : 0);
-                tw_t.push_back(r < n_delays ? (int32_t)((q * pd.st[d].tauL[r]) % L) : 0);
+        for (int r = 0; r < n_delays; ++r)
+            for (int64_t q = 0; q < L; ++q) {
+                tw_P.push_back((int32_t)L);
+                tw_t.push_back((int32_t)((q * pd.st[d].tauL[r]) % L));
             }
     }
-    p->wtab_elems = (int32_t)tw_P.size() - pd.st[0].wtab_off;
     pd.sumB = (int32_t)bin_base;
+    // largest window of phasor tables one classify tile needs: its stages' tables
+    p->wtab_elems = 0;
+    for (int64_t b0 = 0; b0 < pd.sumB; b0 += kClassifyTile) {
+        const int64_t b1 = std::min<int64_t>(pd.sumB, b0 + kClassifyTile) - 1;
+        int d0 = 0, d1 = 0;
+        while (d0 + 1 < n_stages && b0 >= pd.st[d0 + 1].bin_base) ++d0;
+        while (d1 + 1 < n_stages && b1 >= pd.st[d1 + 1].bin_base) ++d1;
+        const int32_t n = pd.st[d1].wtab_off + n_delays * pd.st[d1].L - pd.st[d0].wtab_off;
+        p->wtab_elems = std::max(p->wtab_elems, n);
+    }
     pd.y_per_sig = (int64_t)bin_base * n_delays;
     p->smem1 = l1.smem;
     p->smem2 = l2.smem;
@@ -321,7 +325,12 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     p->ctr_stride = (int32_t)align_up((size_t)ctr_words(pd.max_rounds), 64);
     p->sort_cap = 1;
     while ((size_t)p->sort_cap < nb) p->sort_cap <<= 1;
-    p->smem_cap = std::min(p->sort_cap, 4096);
+    {
+        // shared-memory keys of the compaction sort: a power of two within the device limit
+        int cap = 1;
+        while ((size_t)cap * 2 * sizeof(uint64_t) <= (size_t)di.max_smem - 1024) cap <<= 1;
+        p->smem_cap = std::min(2 * p->sort_cap, cap);
+    }
     // decode workspace, one block carved into arrays
     size_t off = 0;
     auto carve = [&](size_t bytes) {
@@ -522,8 +531,9 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     da.bins = bins;
     da.roots = p->d_tw;
     da.wtab_elems = p->wtab_elems;
-    // phasor tables up to 96 KB go to shared memory (two classify CTAs per SM still fit)
-    da.wtab_smem = (size_t)p->wtab_elems * p->esz <= 96 * 1024 ? 1 : 0;
+    // a tile's phasor tables go to shared memory up to 160 KB (up to 96 KB two classify
+    // CTAs still fit an SM)
+    da.wtab_smem = (size_t)p->wtab_elems * p->esz <= 160 * 1024 ? 1 : 0;
     const int threads = 512;
     const int total = p->num_sms * p->decode_occ;
     // later rounds touch O(K) bins: about one CTA per 256 expected single-tons
@@ -558,7 +568,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     ca.val0 = val0;
     {
         PhaseScope ps(p, st, 2, 1);
-        CK(launch_compact(ca, p->prec, p->xdouble, 1024, 2 * sizeof(uint64_t) * (size_t)p->smem_cap, st));
+        CK(launch_compact(ca, p->prec, p->xdouble, 1024, sizeof(uint64_t) * (size_t)p->smem_cap, st));
     }
     return SFFT_OK;
 }

@@ -28,7 +28,6 @@
 namespace sfft {
 
 constexpr int64_t kFMask = (1ll << 40) - 1;
-constexpr int kClassifyTile = 2048;          // bins per classify CTA
 constexpr int kClassifyThreads = 256;
 
 __device__ __forceinline__ int ldv(const int32_t* p) { return *(const volatile int32_t*)p; }
@@ -129,58 +128,79 @@ __device__ __forceinline__ void record_candidate(int32_t* ctr, const DecodeWs& w
     atomicAdd(ctr + kCtrResolved, 1);
 }
 
-// D2, ML locate: one thread per non-zero bin j of stage d.  Z_r = Y_r conj(a_r(j)); the
-// L candidates q are scored by |sum_r Z_r conj(W[q][r])|^2 with the stage's phasor table
-// W[q][r] = e^{2 pi i (q tauL_r mod L) / L} (a candidate f = j + q B has
-// a_r(f) = a_r(j) W[q][r]); the best (lowest q on ties) gives v = sum_r Z_r conj(W) / (R B)
-// and rho = sum_r |Z_r - B v W[q][r]|^2.  Lanes of a warp scan the same q in lockstep, so
-// the table reads are broadcasts.
-template <typename T>
-__device__ void locate_ml_thread(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
-                                 const typename C2<T>::t* Y, const typename C2<T>::t* wtab,
-                                 int round, int b)
+// D2, ML locate for non-zero bin j of stage d, by a group of G lanes (G a power of two
+// <= 32, groups aligned within the warp; every lane of the warp calls this in lockstep).
+// Groups without a bin of their own pass valid = false and some other bin of the same
+// tile as b, whose stage's table is within wtab, and record nothing.  Z_r = Y_r conj(a_r(j)); the L
+// candidates q are scored by |sum_r Z_r conj(W[r][q])|^2 with the stage's phasor table
+// W[r][q] = e^{2 pi i (q tauL_r mod L) / L} (a candidate f = j + q B has
+// a_r(f) = a_r(j) W[r][q]); the lanes of the group split the candidates (consecutive q on
+// consecutive lanes, so the table reads are conflict-free), then a group argmax (lowest q
+// on ties).  The best q gives v = sum_r Z_r conj(W[r][q]) / (R B) and
+// rho = sum_r |Z_r - B v W[r][q]|^2; lane 0 of the group records a single-ton.
+// RT > 0: the number of delays as a compile-time constant (R = RT); RT = 0: R = pd.R.
+// wtab holds the tables from plan-table offset wtab_base on.
+template <typename T, int RT>
+__device__ void locate_ml_group(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                                const typename C2<T>::t* Y, const typename C2<T>::t* wtab,
+                                int32_t wtab_base, int round, int b, bool valid, int G)
 {
     using V = typename C2<T>::t;
+    constexpr int RM = RT > 0 ? RT : kMaxDelays;  // delay slots the loops unroll over
     const PlanDesc& pd = a.pd;
+    const int li = threadIdx.x & (G - 1);
     const int d = stage_of(pd, b);
     const StageDesc& st = pd.st[d];
-    const int R = pd.R, Rp = pd.Rp;
+    const int R = RT > 0 ? RT : pd.R;
     const int B = st.B, L = st.L;
     const int j = __ldg(a.pbin + b);
     const V* Yb = Y + st.y_off + (b - st.bin_base);
-    T zx[kMaxDelays], zy[kMaxDelays];
+    T zx[RM], zy[RM];
+    if (G >= R) {
+        // lane r of the group forms Z_r, the group shares them
+        V z = {0, 0};
+        if (li < R) {
+            const V y = __ldcg(Yb + (int64_t)li * B);
+            const V aj = delay_phasor<T>(a, j, st.tau[li]);
+            z = V{y.x * aj.x + y.y * aj.y, y.y * aj.x - y.x * aj.y};
+        }
 #pragma unroll
-    for (int r = 0; r < kMaxDelays; ++r) {
-        zx[r] = 0;
-        zy[r] = 0;
-        if (r < R) {
-            const V y = __ldcg(Yb + (int64_t)r * B);
-            const V aj = delay_phasor<T>(a, j, st.tau[r]);
-            zx[r] = y.x * aj.x + y.y * aj.y;
-            zy[r] = y.y * aj.x - y.x * aj.y;
+        for (int r = 0; r < RM; ++r) {
+            zx[r] = 0;
+            zy[r] = 0;
+            if (r < R) {
+                zx[r] = __shfl_sync(0xffffffffu, z.x, r, G);
+                zy[r] = __shfl_sync(0xffffffffu, z.y, r, G);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            zx[r] = 0;
+            zy[r] = 0;
+            if (r < R) {
+                const V y = __ldcg(Yb + (int64_t)r * B);
+                const V aj = delay_phasor<T>(a, j, st.tau[r]);
+                zx[r] = y.x * aj.x + y.y * aj.y;
+                zy[r] = y.y * aj.x - y.x * aj.y;
+            }
         }
     }
-    const V* W = wtab + (st.wtab_off - pd.st[0].wtab_off);
-    T best = (T)-1, bcx = 0, bcy = 0;
+    const V* W = wtab + (st.wtab_off - wtab_base);
+    T best = (T)-1;
     int bq = 0;
-    for (int q = 0; q < L; ++q) {
-        const V* Wq = W + q * Rp;
+    for (int q = li; q < L; q += G) {
         T cx0 = 0, cy0 = 0, cx1 = 0, cy1 = 0;
 #pragma unroll
-        for (int r = 0; r < kMaxDelays; r += 2) {
+        for (int r = 0; r < RM; r += 2) {
             if (r < R) {
-                V w0, w1;
-                if constexpr (sizeof(V) == 8) {
-                    const float4 q4 = *reinterpret_cast<const float4*>(Wq + r);
-                    w0 = V{q4.x, q4.y};
-                    w1 = V{q4.z, q4.w};
-                } else {
-                    w0 = Wq[r];
-                    w1 = Wq[r + 1];
-                }
                 // Z_r conj(w): (zx wx + zy wy, zy wx - zx wy), as fused multiply-adds
+                const V w0 = W[r * L + q];
                 cx0 = fma(zx[r], w0.x, fma(zy[r], w0.y, cx0));
                 cy0 = fma(zy[r], w0.x, fma(-zx[r], w0.y, cy0));
+            }
+            if (r + 1 < R) {
+                const V w1 = W[(r + 1) * L + q];
                 cx1 = fma(zx[r + 1], w1.x, fma(zy[r + 1], w1.y, cx1));
                 cy1 = fma(zy[r + 1], w1.x, fma(-zx[r + 1], w1.y, cy1));
             }
@@ -190,19 +210,34 @@ __device__ void locate_ml_thread(const DecodeArgs& a, int32_t* ctr, const Decode
         if (sc > best) {
             best = sc;
             bq = q;
-            bcx = cx;
-            bcy = cy;
+        }
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o, G);
+        const int oq = __shfl_xor_sync(0xffffffffu, bq, o, G);
+        if (ob > best || (ob == best && oq < bq)) {
+            best = ob;
+            bq = oq;
+        }
+    }
+    if (!valid || li != 0) return;
+    T cx = 0, cy = 0;
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        if (r < R) {
+            const V e = W[r * L + bq];
+            cx = fma(zx[r], e.x, fma(zy[r], e.y, cx));
+            cy = fma(zy[r], e.x, fma(-zx[r], e.y, cy));
         }
     }
     const int64_t f = (int64_t)j + (int64_t)bq * B;
     const T sc = (T)1 / ((T)R * (T)B);
-    const V v = {bcx * sc, bcy * sc};
-    const V* Wb = W + bq * Rp;
+    const V v = {cx * sc, cy * sc};
     T e2 = 0;
 #pragma unroll
-    for (int r = 0; r < kMaxDelays; ++r) {
+    for (int r = 0; r < RM; ++r) {
         if (r < R) {
-            const V e = Wb[r];
+            const V e = W[r * L + bq];
             const T ex = zx[r] - (T)B * (v.x * e.x - v.y * e.y);
             const T ey = zy[r] - (T)B * (v.x * e.y + v.y * e.x);
             e2 += ex * ex + ey * ey;
@@ -211,89 +246,23 @@ __device__ void locate_ml_thread(const DecodeArgs& a, int32_t* ctr, const Decode
     if (below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
 }
 
-// D2, ML locate with one warp per bin (later rounds, where few bins are left and
-// latency matters more than throughput): lane r < R forms Z_r, the lanes split the L
-// candidates, then a warp argmax (lowest q on ties) and warp sums for v and rho.  Same
-// arithmetic as locate_ml_thread.
-template <typename T>
-__device__ void locate_ml_warp(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
-                               const typename C2<T>::t* Y, int round, int b)
+// Lanes per bin for the ML search of n bins with at most Lmax candidates by nt threads:
+// the G that minimises (bins per lane) x (work per bin and lane), where a bin costs every
+// lane of its group ~4 R FMAs per candidate it scans, forming Z (shared when G >= R) and
+// the log2 G reduction steps.
+__device__ __forceinline__ int ml_group_size(int n, int Lmax, int R, int nt)
 {
-    using V = typename C2<T>::t;
-    const PlanDesc& pd = a.pd;
-    const int lane = threadIdx.x & 31;
-    const int d = stage_of(pd, b);
-    const StageDesc& st = pd.st[d];
-    const int R = pd.R, Rp = pd.Rp;
-    const int B = st.B, L = st.L;
-    const int j = __ldg(a.pbin + b);
-    V z = {0, 0};
-    if (lane < R) {
-        const V y = __ldcg(Y + st.y_off + (int64_t)lane * B + (b - st.bin_base));
-        const V aj = delay_phasor<T>(a, j, st.tau[lane]);
-        z = V{y.x * aj.x + y.y * aj.y, y.y * aj.x - y.x * aj.y};
-    }
-    T zx[kMaxDelays], zy[kMaxDelays];
-#pragma unroll
-    for (int r = 0; r < kMaxDelays; ++r) {
-        zx[r] = 0;
-        zy[r] = 0;
-        if (r < R) {
-            zx[r] = __shfl_sync(0xffffffffu, z.x, r);
-            zy[r] = __shfl_sync(0xffffffffu, z.y, r);
+    int best_g = 1, best = 0x7fffffff;
+    for (int g = 1, lg = 0; g <= 32; g <<= 1, ++lg) {
+        const int per = nt / g;
+        const int rounds = (n + per - 1) / per;
+        const int cost = rounds * (((Lmax + g - 1) / g) * 4 * R + (g >= R ? 40 : 20 * R) + 12 * lg);
+        if (cost < best) {
+            best = cost;
+            best_g = g;
         }
     }
-    const V* W = reinterpret_cast<const V*>(a.roots) + st.wtab_off;
-    T best = (T)-1;
-    int bq = 0;
-    for (int q = lane; q < L; q += 32) {
-        const V* Wq = W + q * Rp;
-        T cx = 0, cy = 0;
-#pragma unroll
-        for (int r = 0; r < kMaxDelays; ++r) {
-            if (r < R) {
-                const V wv = __ldg(Wq + r);
-                cx = fma(zx[r], wv.x, fma(zy[r], wv.y, cx));
-                cy = fma(zy[r], wv.x, fma(-zx[r], wv.y, cy));
-            }
-        }
-        const T sc = cx * cx + cy * cy;
-        if (sc > best) {
-            best = sc;
-            bq = q;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
-        if (ob > best || (ob == best && oq < bq)) {
-            best = ob;
-            bq = oq;
-        }
-    }
-    const int64_t f = (int64_t)j + (int64_t)bq * B;
-    V e = {0, 0}, c = {0, 0};
-    if (lane < R) {
-        e = __ldg(W + bq * Rp + lane);
-        c = V{z.x * e.x + z.y * e.y, z.y * e.x - z.x * e.y};
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        c.x += __shfl_xor_sync(0xffffffffu, c.x, o);
-        c.y += __shfl_xor_sync(0xffffffffu, c.y, o);
-    }
-    const T sc = (T)1 / ((T)R * (T)B);
-    const V v = {c.x * sc, c.y * sc};
-    T e2 = 0;
-    if (lane < R) {
-        const T ex = z.x - (T)B * (v.x * e.x - v.y * e.y);
-        const T ey = z.y - (T)B * (v.x * e.y + v.y * e.x);
-        e2 = ex * ex + ey * ey;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-    if (lane == 0 && below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
+    return best_g;
 }
 
 // D2, ARG locate (FFAST, Sec. 3.2 subproblem 2): f from the phase of Y(1) conj(Y(0)) in
@@ -475,6 +444,20 @@ __device__ __forceinline__ DecodeWs slot_ws(const DecodeArgs& a, int sig)
     return w;
 }
 
+// locate_ml_group with the delay count as a constant for the common R
+template <typename T>
+__device__ __forceinline__ void locate_ml(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                                          const typename C2<T>::t* Y, const typename C2<T>::t* wtab,
+                                          int32_t wtab_base, int round, int b, bool valid, int G)
+{
+    switch (a.pd.R) {
+    case 6: locate_ml_group<T, 6>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G); break;
+    case 8: locate_ml_group<T, 8>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G); break;
+    case 10: locate_ml_group<T, 10>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G); break;
+    default: locate_ml_group<T, 0>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G); break;
+    }
+}
+
 // Round 1: classify every bin.  One CTA per tile of kClassifyTile bins of one signal.
 template <typename T>
 __global__ void __launch_bounds__(kClassifyThreads, 2) classify_kernel(const __grid_constant__ DecodeArgs a)
@@ -491,11 +474,24 @@ __global__ void __launch_bounds__(kClassifyThreads, 2) classify_kernel(const __g
     V* Y = reinterpret_cast<V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
     const int b0 = tile * kClassifyTile;
     const int b1 = min(pd.sumB, b0 + kClassifyTile);
-    // the stages' ML phasor tables, in shared memory when the launch gave room for them
-    const V* wtab = reinterpret_cast<const V*>(a.roots) + pd.st[0].wtab_off;
+    // the ML phasor tables of the tile's stages (consecutive in the plan table), in shared
+    // memory when the launch gave room for them
+    const V* wtab = reinterpret_cast<const V*>(a.roots);
+    int32_t wtab_base = 0;
     if (pd.locate == 1 && a.wtab_smem) {
+        const int d0 = stage_of(pd, b0), d1 = stage_of(pd, b1 - 1);
+        wtab_base = pd.st[d0].wtab_off;
+        const int n = pd.st[d1].wtab_off + pd.R * pd.st[d1].L - wtab_base;
         V* ws = reinterpret_cast<V*>(smem_raw);
-        for (int i = threadIdx.x; i < a.wtab_elems; i += blockDim.x) ws[i] = wtab[i];
+        // asynchronous copies, all in flight at once
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(ws + i);
+            if constexpr (sizeof(V) == 16)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(wtab + wtab_base + i) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(wtab + wtab_base + i) : "memory");
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
         wtab = ws;
     }
     if (threadIdx.x == 0) {
@@ -503,34 +499,39 @@ __global__ void __launch_bounds__(kClassifyThreads, 2) classify_kernel(const __g
         s_res = 0;
     }
     __syncthreads();
-    // D1, two bins per thread in flight
-    for (int b = b0 + threadIdx.x; b < b1; b += 2 * blockDim.x) {
-        const int bb = b + blockDim.x;
-        const bool two = bb < b1;
-        const bool z0 = bin_is_zero<T>(pd, Y, b);
-        const bool z1 = two ? bin_is_zero<T>(pd, Y, bb) : true;
-        __stcg((long long*)w.cand + b, -1ll);
-        __stcg(w.dirty + b, 0u);
-        __stcg(w.state + b, (uint8_t)(z0 ? 1 : 0));
-        if (z0)
-            atomicAdd(&s_res, 1);
-        else
-            s_nz[atomicAdd(&s_cnt, 1)] = b;
-        if (two) {
-            __stcg((long long*)w.cand + bb, -1ll);
-            __stcg(w.dirty + bb, 0u);
-            __stcg(w.state + bb, (uint8_t)(z1 ? 1 : 0));
-            if (z1)
+    // D1, four bins per thread in flight
+    constexpr int NB = 4;
+    for (int b = b0 + threadIdx.x; b < b1; b += NB * blockDim.x) {
+        bool z[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int bu = b + u * blockDim.x;
+            z[u] = bu < b1 ? bin_is_zero<T>(pd, Y, bu) : true;
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int bu = b + u * blockDim.x;
+            if (bu >= b1) continue;
+            __stcg((long long*)w.cand + bu, -1ll);
+            __stcg(w.dirty + bu, 0u);
+            __stcg(w.state + bu, (uint8_t)(z[u] ? 1 : 0));
+            if (z[u])
                 atomicAdd(&s_res, 1);
             else
-                s_nz[atomicAdd(&s_cnt, 1)] = bb;
+                s_nz[atomicAdd(&s_cnt, 1)] = bu;
         }
     }
     __syncthreads();
     const int n_nz = s_cnt;
     if (pd.locate == 1) {
-        for (int i = threadIdx.x; i < n_nz; i += blockDim.x)
-            locate_ml_thread<T>(a, w.ctr, w, Y, wtab, 1, s_nz[i]);
+        int Lmax = 0;
+        for (int d = 0; d < pd.D; ++d) Lmax = max(Lmax, pd.st[d].L);
+        const int G = ml_group_size(n_nz, Lmax, pd.R, blockDim.x);
+        const int per = blockDim.x / G;
+        for (int k = 0; k < (n_nz + per - 1) / per; ++k) {
+            const int i = k * per + threadIdx.x / G;
+            locate_ml<T>(a, w.ctr, w, Y, wtab, wtab_base, 1, s_nz[i < n_nz ? i : 0], i < n_nz, G);
+        }
     } else {
         for (int i = threadIdx.x; i < n_nz; i += blockDim.x) locate_arg_thread<T>(a, w.ctr, w, Y, 1, s_nz[i]);
     }
@@ -584,7 +585,9 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
         const int n_nz = ldv(ctr + kCtrRoundBase + 3 * round + 1);
         if (pd.locate == 1) {
             const int gw = wt >> 5, nwarps = nw >> 5;
-            for (int i = gw; i < n_nz; i += nwarps) locate_ml_warp<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
+            const V* wtab = reinterpret_cast<const V*>(a.roots);
+            for (int i = gw; i < n_nz; i += nwarps)
+                locate_ml<T>(a, ctr, w, Y, wtab, 0, round, __ldcg(w.nzl + i), true, 32);
         } else {
             for (int i = wt; i < n_nz; i += nw) locate_arg_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
         }
@@ -602,15 +605,15 @@ __device__ void bitonic_sort(uint64_t* key, int n_pad)
 {
     for (int k = 2; k <= n_pad; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n_pad; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t x = key[i], y = key[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) {
-                        key[i] = y;
-                        key[ixj] = x;
-                    }
+            // pair q: i has bit j clear, partner i + j
+            for (int q = threadIdx.x; q < (n_pad >> 1); q += blockDim.x) {
+                const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+                const int ixj = i + j;
+                const uint64_t x = key[i], y = key[ixj];
+                const bool up = (i & k) == 0;
+                if ((x > y) == up) {
+                    key[i] = y;
+                    key[ixj] = x;
                 }
             }
             __syncthreads();
@@ -643,15 +646,11 @@ __global__ void __launch_bounds__(1024) compact_kernel(const __grid_constant__ C
     const int K = pd.K;
     int n_pad = 1;
     while (n_pad < n) n_pad <<= 1;
-    uint64_t* k1;
-    uint64_t* k2;
-    if (n_pad <= a.smem_cap) {
-        k1 = reinterpret_cast<uint64_t*>(smem_raw);
-        k2 = k1 + a.smem_cap;
-    } else {
-        k1 = a.sortbuf + (int64_t)sig * 2 * a.sort_cap;
-        k2 = k1 + a.sort_cap;
-    }
+    // keys in shared memory where they fit (smem_cap keys), else in the slot's sort buffer
+    uint64_t* const kg = a.sortbuf + (int64_t)sig * 2 * a.sort_cap;
+    uint64_t* const ks = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* k1 = n_pad <= a.smem_cap ? ks : kg;
+    uint64_t* k2 = 2 * n_pad <= a.smem_cap ? ks + n_pad : kg + a.sort_cap;
     for (int i = threadIdx.x; i < n_pad; i += blockDim.x)
         k1[i] = i < n ? (((uint64_t)__ldcg((const long long*)rec_f + i) << 32) | (uint32_t)i)
                       : ~0ull;

@@ -554,19 +554,35 @@ __global__ void __launch_bounds__(512, 1) bucketize_kernel(const __grid_constant
                     }
                 }
             }
-            V v[U];
+            if constexpr (sizeof(XS) == sizeof(T)) {
+                // samples of the arithmetic type: asynchronous copies straight into shared
+                // memory (positions outside the stage are zero)
+                const V* xv = reinterpret_cast<const V*>(x);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                v[u] = V{0, 0};
-                if (pos[u] >= 0)
-                    v[u] = ps.src_gather ? load_sample<XS, V>(x, src[u]) : __ldcg(scr + slot + src[u]);
-            }
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e >= TS) continue;
+                    if (pos[u] < 0)
+                        s[e] = V{0, 0};
+                    else
+                        cp_async(s + e, ps.src_gather ? xv + src[u] : scr + slot + src[u], (int)sizeof(V));
+                }
+            } else {
+                V v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * blockDim.x;
-                if (e < TS) s[e] = v[u];
+                for (int u = 0; u < U; ++u) {
+                    v[u] = V{0, 0};
+                    if (pos[u] >= 0)
+                        v[u] = ps.src_gather ? load_sample<XS, V>(x, src[u]) : __ldcg(scr + slot + src[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e < TS) s[e] = v[u];
+                }
             }
         }
+        if constexpr (sizeof(XS) == sizeof(T)) cp_async_wait_all();
     }
 loaded:
     __syncthreads();

@@ -6,6 +6,8 @@
 
 namespace sfft {
 
+constexpr int kClassifyTile = 2048;  // bins per classify CTA
+
 // Arguments of one bucketization launch (gather + prime-factor DFT passes).
 struct BucketArgs {
     PlanDesc pd;
@@ -29,7 +31,7 @@ struct DecodeArgs {
     int32_t n_sig;
     int32_t fault;        // 1: one CTA per group leaves before its first barrier (testing)
     long long spin_limit; // polls before a device-side wait gives up
-    int32_t wtab_elems;   // entries of all stages' ML phasor tables (from st[0].wtab_off)
+    int32_t wtab_elems;   // largest window of ML phasor tables a classify tile stages
     int32_t wtab_smem;    // 1: classify stages them in shared memory
     const int32_t* pbin;  // position -> bin j, per stage at bin_base
     const int32_t* bpos;  // bin j -> position
@@ -43,7 +45,7 @@ struct CompactArgs {
     int32_t ctr_stride;
     int32_t n_sig;
     int32_t sort_cap;           // pow2 capacity of sortbuf per slot
-    int32_t smem_cap;           // pow2 capacity of the shared-memory sort
+    int32_t smem_cap;           // pow2 capacity (keys) of the shared-memory sort area
     uint64_t* sortbuf;          // 2 * sort_cap per slot
     int64_t* const* out_idx;    // device array of n_sig pointers, or nullptr
     void* const* out_val;

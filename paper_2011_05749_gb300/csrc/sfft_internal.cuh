@@ -58,8 +58,7 @@ struct StageDesc {
     int32_t r0, r1;          // delay slots holding tau = 0 and tau = 1 (-1 if absent)
     int32_t root_off;        // offset of the L roots of unity (cos, sin)(2 pi t / L)
     float invL;              // 1 / L
-    int32_t wtab_off;        // offset of the [L][Rp] table (cos, sin)(2 pi (q tauL_r mod L) / L),
-                             // rows padded to Rp = even R with zero entries
+    int32_t wtab_off;        // offset of the [R][L] table W[r][q] = (cos, sin)(2 pi (q tauL_r mod L) / L)
     int32_t pad2;
     double T0, T1;           // thresholds on sum_r |Y_r|^2 and on the single-tone residual
     float T0f, T1f;          // the same in FP32 (the FP32 path compares in FP32)
@@ -75,7 +74,7 @@ struct PlanDesc {
     int32_t K;
     int32_t root_total;      // sum_d L_d: root-table entries (at st[0].root_off onwards)
     double invN;             // 1 / N
-    int32_t Rp;              // R rounded up to even (row length of the ML phasor tables)
+    int32_t pad0;
     int32_t ph_shift;        // two-level phasor tables: e^{2 pi i m / N} =
     int32_t ph_lo_off;       //   tw[ph_hi_off + (m >> ph_shift)] * tw[ph_lo_off + (m & mask)]
     int32_t ph_hi_off;

@@ -50,7 +50,7 @@ struct sfft_plan_s {
     cudaEvent_t aux_join[2] = {nullptr, nullptr};
     void* d_xb_stage = nullptr;   // host-buffer batches: max_batch inputs
     void* d_ob_stage = nullptr;   //                      max_batch outputs + infos
-    int32_t wtab_elems = 0;  // entries of the ML phasor tables (all stages)
+    int32_t wtab_elems = 0;  // largest window of ML phasor tables one classify tile needs
     size_t footprint = 0;  // device bytes owned by the plan
     // phase timing (sfft_plan_set_profiling): CUDA events recorded on the launch stream
     bool prof = false;
