@@ -86,6 +86,18 @@ def draw_delays(N: int, n_stages: int, R: int, rng: np.random.Generator, fixed=(
     return out
 
 
+def oneshot_delays(N: int, a_m: int, P: int, rng: np.random.Generator) -> np.ndarray:
+    """Delays of the one-shot decoder's single stage: the consecutive set -a_m .. 2 a_m - 1
+    (mod N), then P distinct uniform draws outside it (Sec. 4.1, Stage 1)."""
+    cons = [(k - a_m) % N for k in range(3 * a_m)]
+    pick = []
+    while len(pick) < P:
+        c = int(rng.integers(0, N))
+        if c not in pick and c not in cons:
+            pick.append(c)
+    return np.array([cons + pick], dtype=np.int64)
+
+
 def make_problem(N, f, K, seed, R=3, delays="ffast", mag=(1.0, 1.0), snr_db=None,
                  support=None, values=None) -> Problem:
     """One seeded problem.  delays="ffast" gives {0, 1, 2} in every stage (Sec. 4.2, exactly
