@@ -74,6 +74,12 @@ typedef struct sfft_server_s* sfft_server_t;
 #define SFFT_LOCATE_ML 1     /* best delay-phasor correlation over the L_d candidates
                                 {j, j + B_d, ...} of the bin (random delays, R-FFAST) */
 
+/* decoder (Sec. 3) */
+#define SFFT_DECODER_PEEL 0     /* FFAST / R-FFAST peeling across stages (Sec. 3.2) */
+#define SFFT_DECODER_ONESHOT 1  /* sFFT-DT one-shot decoder on a single stage (Sec. 3.1):
+                                   Hankel singular-value count, Prony enumeration of the
+                                   positions, subspace-pursuit values */
+
 typedef struct {
     int32_t dtype;       /* SFFT_C64 or SFFT_C128 (default C64) */
     int32_t precision;   /* SFFT_PREC_FP32 or SFFT_PREC_FP64 (default FP32) */
@@ -96,6 +102,9 @@ typedef struct {
                                  runs out (status SFFT_ETIMEDOUT); 2 = plan creation fails
                                  with SFFT_ENOMEM before allocating */
     int32_t decode_ctas;      /* CTAs per signal in the peeling rounds; 0 = automatic */
+    int32_t decoder;          /* SFFT_DECODER_PEEL (default) or SFFT_DECODER_ONESHOT */
+    int32_t oneshot_am;       /* one-shot decoder: a_m, the most frequencies one bucket may
+                                 hold (1..3, default 3) */
     int32_t reserved;
 } sfft_opts;
 
@@ -108,10 +117,13 @@ void sfft_opts_default(sfft_opts* opts);
  *   delays[n_stages * n_delays]  tau_{d,r} at [d * n_delays + r], distinct within a stage,
  *                        0 <= tau < N (1 <= n_delays <= 16)
  *   K                    output size: the K largest recovered coefficients (Sec. 2.1)
+ * With opts->decoder = SFFT_DECODER_ONESHOT (Sec. 3.1, Sec. 4.1): one stage, K <= B, and
+ * the delays are the consecutive set -a_m .. 2 a_m - 1 (mod N) in slots 0 .. 3 a_m - 1
+ * followed by P >= 2 a_m distinct random delays (a_m = opts->oneshot_am).
  * Host arrays; the plan copies them.  N < 2^30.  The plan owns device tables (twiddles,
  * index maps) and the workspace for opts->max_batch signals until sfft_plan_destroy.
- * Errors: SFFT_EINVAL (bad sizes, factors, delays, ARG without delays 0 and 1),
- * SFFT_ENOMEM, SFFT_ECUDA.                                                                */
+ * Errors: SFFT_EINVAL (bad sizes, factors, delays, ARG without delays 0 and 1, a one-shot
+ * plan breaking the rules above), SFFT_ENOMEM, SFFT_ECUDA.                                */
 int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t n_stages, const int64_t* f,
                      int32_t n_delays, const int64_t* delays, const sfft_opts* opts);
 void sfft_plan_destroy(sfft_plan_t plan);

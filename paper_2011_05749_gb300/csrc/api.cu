@@ -102,6 +102,8 @@ extern "C" void sfft_opts_default(sfft_opts* o)
     o->eta = 0.0;
     o->c0 = 4.0;
     o->c1 = 2.0;
+    o->decoder = SFFT_DECODER_PEEL;
+    o->oneshot_am = 3;
 }
 
 static void free_plan_memory(sfft_plan_s* p)
@@ -156,6 +158,15 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
                 if (delays[(int64_t)d * n_delays + q] == t) return SFFT_EINVAL;
         }
     }
+    if (o.decoder != SFFT_DECODER_PEEL && o.decoder != SFFT_DECODER_ONESHOT) return SFFT_EINVAL;
+    if (o.decoder == SFFT_DECODER_ONESHOT) {
+        // one stage; slots 0 .. 3 a_m - 1 hold -a_m .. 2 a_m - 1 (mod N), then at least 2 a_m
+        // random delays (Sec. 4.1, Stage 1); the output holds at most one value per bucket
+        const int am = o.oneshot_am;
+        if (n_stages != 1 || am < 1 || am > 3 || n_delays < 5 * am || K > N / f[0]) return SFFT_EINVAL;
+        for (int r = 0; r < 3 * am; ++r)
+            if (delays[r] != ((int64_t)r - am + N) % N) return SFFT_EINVAL;
+    }
     if (o.fault_inject == 2) return SFFT_ENOMEM;  // injected allocation failure (testing)
     if (o.wait_limit_log2 < 0 || o.fault_inject < 0 || o.fault_inject > 2 || o.decode_ctas < 0)
         return SFFT_EINVAL;
@@ -184,6 +195,17 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     pd.K = K;
     pd.invN = 1.0 / (double)N;
     pd.mu = ~0ull / (uint64_t)N;
+    pd.mode = o.decoder == SFFT_DECODER_ONESHOT ? 1 : 0;
+    if (pd.mode == 1) {
+        // the vote's floor: a_m times the per-delay zero-ton level of a bucket in moment
+        // units, sqrt(c0 B sigma^2 + (eta B a_min)^2) / B; the pursuit's residual tolerance
+        // P (c1 sigma^2 / B + (eta a_min)^2)
+        const double B = (double)(N / f[0]);
+        const int am = o.oneshot_am, P = n_delays - 3 * am;
+        pd.am = am;
+        pd.sv_floor = am * sqrt(o.c0 * B * o.noise_var + (eta * B * o.a_min) * (eta * B * o.a_min)) / B;
+        pd.sp_tol2 = P * (o.c1 * o.noise_var / B + (eta * o.a_min) * (eta * o.a_min));
+    }
 
     std::vector<int32_t> h_nidx, h_pbin, h_bpos, tw_P, tw_t;
     int64_t bin_base = 0;
@@ -350,6 +372,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     const size_t o_rf = carve(8 * nb * mb);
     const size_t o_rv = carve(p->esz * nb * mb);
     const size_t o_ctr = carve(4 * (size_t)p->ctr_stride * mb);
+    const size_t o_sv = pd.mode == 1 ? carve(8 * (nb * pd.am + 1) * mb) : 0;
     p->dec_bytes = off;
     p->ctr_bytes_per_sig = 4 * (size_t)p->ctr_stride;
 
@@ -404,6 +427,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     w.rec_f = (int64_t*)(base + o_rf);
     w.rec_v = base + o_rv;
     w.ctr = (int32_t*)(base + o_ctr);
+    w.sv = pd.mode == 1 ? (double*)(base + o_sv) : nullptr;
     p->footprint = 4 * 3 * h_nidx.size() + p->esz * tw_P.size() + ybytes * (p->need_pass2 ? 2 : 1) +
                    p->dec_bytes + 2 * sizeof(uint64_t) * (size_t)p->sort_cap * mb;
     p->decode_occ = decode_occupancy(p->prec, 512);
@@ -476,6 +500,7 @@ static DecodeWs ws_at(const sfft_plan_s* p, int slot0)
     w.rec_f += so;
     w.rec_v = (unsigned char*)w.rec_v + so * p->esz;
     w.ctr += (size_t)slot0 * p->ctr_stride;
+    if (w.sv) w.sv += (size_t)slot0 * ((size_t)p->pd.sumB * p->pd.am + 1);
     return w;
 }
 
@@ -546,7 +571,10 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     da.G = G;
     da.fault = p->opts.fault_inject == 1 ? 1 : 0;
     da.spin_limit = 1ll << (p->opts.wait_limit_log2 > 0 ? std::min(p->opts.wait_limit_log2, 40) : 22);
-    {
+    if (pd.mode == 1) {
+        PhaseScope ps(p, st, 1, 3);
+        CK(launch_oneshot(da, p->prec, st));
+    } else {
         PhaseScope ps(p, st, 1, 2);
         CK(launch_classify(da, p->prec, st));
         CK(launch_decode(da, p->prec, threads, G > 1, st));

@@ -1,0 +1,531 @@
+// oneshot.cu -- the sFFT-DT one-shot decoder (Sec. 3.1, Eq. 7-18; Sec. 4.1, Stage 2) on the
+// bins of a single stage of B buckets (L = N / B candidates per bucket).
+//
+// Delay slots: r = 0 .. 3 a_m - 1 hold tau = r - a_m (mod N), so bucket i's moments are
+// m_k = Y[k + a_m][i] / B = sum_{f = i mod B} xhat_f z_f^k, z_f = e^{2 pi i f / N}
+// (Eq. 7-8); the remaining P slots hold the random delays of Step 3.
+//
+//   DT1  Step 1: singular values of each bucket's Hankel matrix M_{a_m} = [m_{r+c}]
+//        (Eq. 10-11), as square roots of the eigenvalues of M^H M (cyclic complex Jacobi).
+//   DT2  the vote: per signal, the K-th largest singular value above the floor, by an
+//        8-bit radix select on the FP64 bit patterns (one CTA per signal).
+//   DT3  Steps 2-3, one warp per bucket with a > 0 votes: C = M_a^{-1} M_s (Eq. 14), |P(z)|
+//        (Eq. 12) at every candidate (the lanes split them) and the a smallest; then
+//        subspace pursuit over the atoms {f, f + B, f - B} with the P random-delay
+//        measurements (Eq. 18), lane r holding measurement r.
+// The per-bucket arithmetic is FP64 whatever the bins' type (position and value
+// estimation).  Results go to the slot's recovered list; compaction follows as for the
+// peeling decoder.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "launch.h"
+#include "sfft_internal.cuh"
+
+namespace sfft {
+
+namespace {
+
+constexpr int kSolveThreads = 256;           // 8 warps, one bucket each
+constexpr int kMaxAtoms = 9;                 // 3 a_m
+constexpr int kMaxFit = 6;                   // 2 a_m atoms in a union fit
+
+struct Cd {
+    double x, y;
+};
+__device__ __forceinline__ Cd cd(double x, double y) { return Cd{x, y}; }
+__device__ __forceinline__ Cd operator+(Cd a, Cd b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ Cd operator-(Cd a, Cd b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ Cd operator*(Cd a, Cd b)
+{
+    return {fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)};
+}
+__device__ __forceinline__ Cd conjd(Cd a) { return {a.x, -a.y}; }
+__device__ __forceinline__ double abs2(Cd a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ Cd divd(Cd a, Cd b)
+{
+    const double d = 1.0 / abs2(b);
+    return {(a.x * b.x + a.y * b.y) * d, (a.y * b.x - a.x * b.y) * d};
+}
+
+// e^{2 pi i t / N} for 0 <= t < N
+__device__ __forceinline__ Cd root_n(int64_t t, int32_t N)
+{
+    double s, c;
+    sincospi(2.0 * (double)t / (double)N, &s, &c);
+    return {c, s};
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ Cd warp_sum(Cd v) { return {warp_sum(v.x), warp_sum(v.y)}; }
+
+// Solve A x = b (n <= kMaxFit, complex, row-major n x n in shared memory) by Gaussian
+// elimination with partial pivoting, as LAPACK's gesv does; false on an exactly zero pivot.
+// One lane works; A and b are overwritten, x replaces b.
+__device__ bool solve_lane(Cd* A, Cd* b, int n)
+{
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        double best = abs2(A[k * n + k]);
+        for (int i = k + 1; i < n; ++i) {
+            const double v = abs2(A[i * n + k]);
+            if (v > best) {
+                best = v;
+                piv = i;
+            }
+        }
+        if (best == 0.0) return false;
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) {
+                const Cd t = A[k * n + j];
+                A[k * n + j] = A[piv * n + j];
+                A[piv * n + j] = t;
+            }
+            const Cd t = b[k];
+            b[k] = b[piv];
+            b[piv] = t;
+        }
+        for (int i = k + 1; i < n; ++i) {
+            const Cd l = divd(A[i * n + k], A[k * n + k]);
+            for (int j = k + 1; j < n; ++j) A[i * n + j] = A[i * n + j] - l * A[k * n + j];
+            b[i] = b[i] - l * b[k];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        Cd s = b[k];
+        for (int j = k + 1; j < n; ++j) s = s - A[k * n + j] * b[j];
+        b[k] = divd(s, A[k * n + k]);
+    }
+    return true;
+}
+
+// Eigenvalues of a Hermitian n x n matrix (n <= 3) by cyclic Jacobi rotations: for the
+// pivot g = G[p][q] = |g| e^{i phi}, the phase e^{-i phi} on coordinate q makes the 2 x 2
+// block real symmetric, and the rotation with t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// zeta = (G_qq - G_pp) / (2 |g|), annihilates it.
+__device__ void hermitian_eigenvalues(Cd G[3][3], int n, double* ev)
+{
+    for (int sweep = 0; sweep < 10; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int p = 0; p < n; ++p) {
+            diag += fabs(G[p][p].x);
+            for (int q = p + 1; q < n; ++q) off += abs2(G[p][q]);
+        }
+        if (off <= 1e-36 * diag * diag) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double ag = sqrt(abs2(G[p][q]));
+                const double a = G[p][p].x, b = G[q][q].x;
+                if (ag <= 1e-300 || ag <= 1e-18 * (fabs(a) + fabs(b))) {
+                    G[p][q] = G[q][p] = cd(0, 0);
+                    continue;
+                }
+                const Cd e = {G[p][q].x / ag, G[p][q].y / ag};  // e^{i phi}
+                const double zeta = (b - a) / (2.0 * ag);
+                const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
+                                                    : (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int r = 0; r < n; ++r) {
+                    if (r == p || r == q) continue;
+                    const Cd grp = G[r][p], grq = G[r][q];
+                    const Cd eg = conjd(e) * grq;
+                    const Cd nrp = {c * grp.x - s * eg.x, c * grp.y - s * eg.y};
+                    const Cd nrq = {s * grp.x + c * eg.x, s * grp.y + c * eg.y};
+                    G[r][p] = nrp;
+                    G[p][r] = conjd(nrp);
+                    G[r][q] = nrq;
+                    G[q][r] = conjd(nrq);
+                }
+                G[p][p] = cd(a - t * ag, 0);
+                G[q][q] = cd(b + t * ag, 0);
+                G[p][q] = G[q][p] = cd(0, 0);
+            }
+    }
+    for (int p = 0; p < n; ++p) ev[p] = G[p][p].x;
+}
+
+}  // namespace
+
+// DT1: one thread per (signal, bin position b); writes the a_m singular values of the
+// bucket, descending, at sv[b * a_m ..].
+template <typename T>
+__global__ void dt_sv_kernel(const __grid_constant__ DecodeArgs a)
+{
+    using V = typename C2<T>::t;
+    const PlanDesc& pd = a.pd;
+    const int B = pd.sumB, am = pd.am;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)a.n_sig * B) return;
+    const int sig = (int)(gid / B), b = (int)(gid - (int64_t)sig * B);
+    const V* Y = reinterpret_cast<const V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
+    const double invB = 1.0 / (double)B;
+    Cd m[5];  // m_0 .. m_{2 a_m - 2}
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        m[k] = cd(0, 0);
+        if (k < 2 * am - 1) {
+            const V y = __ldcg(Y + (int64_t)(k + am) * B + b);
+            m[k] = cd((double)y.x * invB, (double)y.y * invB);
+        }
+    }
+    // G = M^H M with M[r][c] = m_{r+c}: G[p][q] = sum_r conj(m_{r+p}) m_{r+q}
+    Cd G[3][3];
+    for (int p = 0; p < am; ++p)
+        for (int q = 0; q < am; ++q) {
+            Cd s = cd(0, 0);
+            for (int r = 0; r < am; ++r) s = s + conjd(m[r + p]) * m[r + q];
+            G[p][q] = s;
+        }
+    double ev[3] = {0, 0, 0};
+    hermitian_eigenvalues(G, am, ev);
+    double sv[3];
+    for (int t = 0; t < am; ++t) sv[t] = sqrt(fmax(ev[t], 0.0));
+    for (int i = 1; i < am; ++i)  // descending
+        for (int k = i; k > 0 && sv[k - 1] < sv[k]; --k) {
+            const double t = sv[k];
+            sv[k] = sv[k - 1];
+            sv[k - 1] = t;
+        }
+    double* out = a.ws.sv + (int64_t)sig * ((int64_t)B * am + 1) + (int64_t)b * am;
+    for (int t = 0; t < am; ++t) out[t] = sv[t];
+}
+
+// DT2: one CTA per signal.  theta = the K-th largest singular value among those above the
+// floor (the smallest passing one when fewer), stored after the signal's singular values;
+// +inf when none passes.  Also sets the signal's counters: every bin resolved (a bucket
+// whose Eq. 14 turns out singular takes one back), one round, B identifications.
+__global__ void __launch_bounds__(1024) dt_vote_kernel(const __grid_constant__ DecodeArgs a)
+{
+    const PlanDesc& pd = a.pd;
+    const int sig = blockIdx.x;
+    const int n = pd.sumB * pd.am;
+    double* sv = a.ws.sv + (int64_t)sig * ((int64_t)n + 1);
+    const double floor_v = pd.sv_floor;
+    __shared__ unsigned int hist[256];
+    __shared__ unsigned long long s_prefix;
+    __shared__ int s_need, s_total;
+    if (threadIdx.x == 0) {
+        s_total = 0;
+        s_prefix = 0;
+    }
+    __syncthreads();
+    int cnt = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) cnt += __ldcg(sv + i) > floor_v;
+    atomicAdd(&s_total, cnt);
+    __syncthreads();
+    const int total = s_total;
+    if (threadIdx.x == 0) s_need = min(pd.K, total);
+    unsigned long long mask = 0;
+    for (int shift = 56; shift >= 0 && total > 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        const unsigned long long prefix = s_prefix;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const double v = __ldcg(sv + i);
+            if (!(v > floor_v)) continue;
+            const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+            if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int cum = 0, need = s_need;
+            for (int d = 255; d >= 0; --d) {
+                if (cum + (int)hist[d] >= need) {
+                    s_prefix = prefix | ((unsigned long long)d << shift);
+                    s_need = need - cum;
+                    break;
+                }
+                cum += (int)hist[d];
+            }
+        }
+        mask |= 255ull << shift;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sv[n] = total > 0 ? __longlong_as_double((long long)s_prefix) : __longlong_as_double(0x7ff0000000000000ll);
+        int32_t* ctr = a.ws.ctr + (int64_t)sig * a.ctr_stride;
+        ctr[kCtrResolved] = pd.sumB;
+        ctr[kCtrIdents] = pd.sumB;
+        ctr[kCtrRounds] = 1;
+    }
+}
+
+// DT3: one warp per (signal, bin position b); buckets with no vote leave at once.
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads) dt_solve_kernel(const __grid_constant__ DecodeArgs a)
+{
+    using V = typename C2<T>::t;
+    const PlanDesc& pd = a.pd;
+    const StageDesc& st = pd.st[0];
+    const int B = pd.sumB, am = pd.am, L = st.L;
+    const int32_t N = pd.N;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= (int64_t)a.n_sig * B) return;
+    const int sig = (int)(gw / B), b = (int)(gw - (int64_t)sig * B);
+    const double* sv = a.ws.sv + (int64_t)sig * ((int64_t)B * am + 1);
+    const double theta = __ldcg(sv + (int64_t)B * am);
+    int na = 0;
+    for (int t = 0; t < am; ++t) {
+        const double v = __ldcg(sv + (int64_t)b * am + t);
+        na += (v >= theta && v > pd.sv_floor) ? 1 : 0;
+    }
+    if (na == 0) return;
+
+    __shared__ Cd s_A[kSolveThreads / 32][kMaxFit * kMaxFit];
+    __shared__ Cd s_b[kSolveThreads / 32][kMaxFit];
+    __shared__ int s_ok[kSolveThreads / 32];
+    Cd* A = s_A[wib];
+    Cd* rhs = s_b[wib];
+    int32_t* ctr = a.ws.ctr + (int64_t)sig * a.ctr_stride;
+    const V* Y = reinterpret_cast<const V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
+    const double invB = 1.0 / (double)B;
+    const int j = __ldg(a.pbin + b);
+
+    // moments m_0 .. m_{2a-1}, lane k loads m_k
+    Cd mk = cd(0, 0);
+    if (lane < 2 * na) {
+        const V y = __ldcg(Y + (int64_t)(lane + am) * B + b);
+        mk = cd((double)y.x * invB, (double)y.y * invB);
+    }
+    // Eq. 14: M_a C = M_s, M_a[r][c] = m_{r+c}, M_s[r] = -m_{a+r}
+    for (int idx = 0; idx < na * na; ++idx) {
+        const int r = idx / na, c = idx - r * na;
+        const double x = __shfl_sync(0xffffffffu, mk.x, r + c), y = __shfl_sync(0xffffffffu, mk.y, r + c);
+        if (lane == 0) A[idx] = cd(x, y);
+    }
+    for (int r = 0; r < na; ++r) {
+        const double x = __shfl_sync(0xffffffffu, mk.x, na + r), y = __shfl_sync(0xffffffffu, mk.y, na + r);
+        if (lane == 0) rhs[r] = cd(-x, -y);
+    }
+    __syncwarp();
+    if (lane == 0) s_ok[wib] = solve_lane(A, rhs, na) ? 1 : 0;
+    __syncwarp();
+    if (!s_ok[wib]) {
+        if (lane == 0) atomicSub(ctr + kCtrResolved, 1);
+        return;
+    }
+    Cd c[3];
+    for (int t = 0; t < 3; ++t) c[t] = t < na ? rhs[t] : cd(0, 0);
+    __syncwarp();
+
+    // Step 2 (enumeration): candidates q = lane, lane + 32, ...; z = e^{2 pi i (j + q B) / N}
+    // by a rotation e^{2 pi i 32 / L} per step from z_lane
+    double bv[3];
+    int bq[3];
+    for (int t = 0; t < 3; ++t) {
+        bv[t] = 1e300;
+        bq[t] = 0x7fffffff;
+    }
+    {
+        Cd z = root_n(((int64_t)j + (int64_t)lane * B) % N, N);
+        double s, cc;
+        sincospi(2.0 * 32.0 / (double)L, &s, &cc);
+        const Cd w = cd(cc, s);
+        for (int q = lane; q < L; q += 32) {
+            if (((q - lane) & 1023) == 0 && q != lane) z = root_n(((int64_t)j + (int64_t)q * B) % N, N);
+            Cd pz = cd(1, 0);
+            for (int t = na - 1; t >= 0; --t) pz = pz * z + c[t];
+            const double v = abs2(pz);
+            // keep the na smallest (v, q), lower q first on ties; q only grows
+            int k = na;
+            while (k > 0 && v < bv[k - 1]) --k;
+            if (k < na) {
+                for (int t = na - 1; t > k; --t) {
+                    bv[t] = bv[t - 1];
+                    bq[t] = bq[t - 1];
+                }
+                bv[k] = v;
+                bq[k] = q;
+            }
+            z = z * w;
+        }
+    }
+    // merge across lanes: na rounds of a warp argmin over (v, q)
+    int pos_q[3];
+    for (int t = 0; t < na; ++t) {
+        double v = bv[0];
+        int q = bq[0];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int oq = __shfl_xor_sync(0xffffffffu, q, o);
+            if (ov < v || (ov == v && oq < q)) {
+                v = ov;
+                q = oq;
+            }
+        }
+        pos_q[t] = q;
+        if (bq[0] == q) {  // the owner pops its head
+            for (int u = 0; u + 1 < 3; ++u) {
+                bv[u] = bv[u + 1];
+                bq[u] = bq[u + 1];
+            }
+            bv[2] = 1e300;
+            bq[2] = 0x7fffffff;
+        }
+    }
+    // positions ascending
+    for (int i = 1; i < na; ++i)
+        for (int k = i; k > 0 && pos_q[k - 1] > pos_q[k]; --k) {
+            const int t = pos_q[k];
+            pos_q[k] = pos_q[k - 1];
+            pos_q[k - 1] = t;
+        }
+
+    // Step 3: subspace pursuit.  Dictionary: for each position f, the atoms f, f + B, f - B
+    // (mod N) in that order, duplicates dropped.
+    int64_t dic[kMaxAtoms];
+    int nd = 0;
+    for (int t = 0; t < na; ++t) {
+        const int64_t f = (int64_t)j + (int64_t)pos_q[t] * B;
+        const int64_t cand[3] = {f, (f + B) % N, (f - B + N) % N};
+        for (int s = 0; s < 3; ++s) {
+            bool dup = false;
+            for (int u = 0; u < nd; ++u) dup |= dic[u] == cand[s];
+            if (!dup) dic[nd++] = cand[s];
+        }
+    }
+    const int P = pd.R - 3 * am;
+    const bool mine = lane < P;
+    Cd y = cd(0, 0);
+    Cd phi[kMaxAtoms];
+    if (mine) {
+        const V v = __ldcg(Y + (int64_t)(3 * am + lane) * B + b);
+        y = cd((double)v.x * invB, (double)v.y * invB);
+    }
+    const int64_t tau = mine ? (int64_t)st.tau[3 * am + lane] : 0;
+    for (int d = 0; d < kMaxAtoms; ++d) phi[d] = (mine && d < nd) ? root_n((dic[d] * tau) % N, N) : cd(0, 0);
+
+    // least squares on the atoms sup[0..ns) by the normal equations; returns the residual
+    // energy, the coefficients in p[], and this lane's residual in *r
+    auto fit = [&](const int* sup, int ns, Cd* p, Cd* r, bool* ok) -> double {
+        for (int u = 0; u < ns; ++u) {
+            Cd pu = cd(0, 0), hu = cd(0, 0);
+            for (int d = 0; d < kMaxAtoms; ++d)
+                if (d == sup[u]) pu = phi[d];
+            hu = warp_sum(conjd(pu) * y);
+            if (lane == 0) rhs[u] = hu;
+            for (int v = 0; v < ns; ++v) {
+                Cd pv = cd(0, 0);
+                for (int d = 0; d < kMaxAtoms; ++d)
+                    if (d == sup[v]) pv = phi[d];
+                const Cd g = warp_sum(conjd(pu) * pv);
+                if (lane == 0) A[u * ns + v] = g;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) s_ok[wib] = solve_lane(A, rhs, ns) ? 1 : 0;
+        __syncwarp();
+        *ok = s_ok[wib] != 0;
+        for (int u = 0; u < ns; ++u) p[u] = rhs[u];
+        __syncwarp();
+        Cd res = y;
+        for (int u = 0; u < ns; ++u) {
+            Cd pu = cd(0, 0);
+            for (int d = 0; d < kMaxAtoms; ++d)
+                if (d == sup[u]) pu = phi[d];
+            res = res - pu * p[u];
+        }
+        if (!mine) res = cd(0, 0);
+        *r = res;
+        return warp_sum(abs2(res));
+    };
+
+    int S[3];
+    for (int t = 0; t < na; ++t) {
+        const int64_t f = (int64_t)j + (int64_t)pos_q[t] * B;
+        for (int d = 0; d < nd; ++d)
+            if (dic[d] == f) S[t] = d;
+    }
+    Cd p[kMaxFit], r;
+    bool ok = true;
+    double res = fit(S, na, p, &r, &ok);
+    for (int it = 0; it < 8 && ok; ++it) {
+        if (res <= pd.sp_tol2) break;
+        // the na atoms outside S most correlated with the residual (lower index on ties)
+        double corr[kMaxAtoms];
+        for (int d = 0; d < kMaxAtoms; ++d) corr[d] = d < nd ? abs2(warp_sum(conjd(phi[d]) * r)) : -1.0;
+        int Tu[kMaxFit], nt = 0;
+        for (int t = 0; t < na; ++t) Tu[nt++] = S[t];
+        for (int e = 0; e < na; ++e) {
+            int bestd = -1;
+            for (int d = 0; d < nd; ++d) {
+                bool used = false;
+                for (int u = 0; u < nt; ++u) used |= Tu[u] == d;
+                if (!used && (bestd < 0 || corr[d] > corr[bestd])) bestd = d;
+            }
+            if (bestd < 0) break;
+            Tu[nt++] = bestd;
+        }
+        Cd pT[kMaxFit], rT;
+        bool okT = true;
+        fit(Tu, nt, pT, &rT, &okT);
+        if (!okT) break;
+        // keep the na largest |p| of the union (lower position on ties), in union order
+        bool keep[kMaxFit] = {false, false, false, false, false, false};
+        for (int e = 0; e < na; ++e) {
+            int bi = -1;
+            for (int u = 0; u < nt; ++u)
+                if (!keep[u] && (bi < 0 || abs2(pT[u]) > abs2(pT[bi]))) bi = u;
+            keep[bi] = true;
+        }
+        int S2[3], n2 = 0;
+        for (int u = 0; u < nt; ++u)
+            if (keep[u]) S2[n2++] = Tu[u];
+        Cd p2[kMaxFit], r2;
+        bool ok2 = true;
+        const double res2 = fit(S2, na, p2, &r2, &ok2);
+        if (!ok2 || res2 >= res) break;
+        for (int t = 0; t < na; ++t) {
+            S[t] = S2[t];
+            p[t] = p2[t];
+        }
+        res = res2;
+        r = r2;
+    }
+    if (!ok) {
+        if (lane == 0) atomicSub(ctr + kCtrResolved, 1);
+        return;
+    }
+    if (lane == 0) {
+        const int k0 = atomicAdd(ctr + kCtrRec, na);
+        int64_t* rf = a.ws.rec_f + (int64_t)sig * pd.sumB;
+        V* rv = reinterpret_cast<V*>(a.ws.rec_v) + (int64_t)sig * pd.sumB;
+        for (int t = 0; t < na; ++t) {
+            if (k0 + t >= pd.sumB) {  // more votes than buckets: cannot store
+                atomicSub(ctr + kCtrResolved, 1);
+                break;
+            }
+            rf[k0 + t] = dic[S[t]];
+            rv[k0 + t] = V{(T)p[t].x, (T)p[t].y};
+        }
+    }
+}
+
+cudaError_t launch_oneshot(const DecodeArgs& a, int precision, cudaStream_t st)
+{
+    if (a.n_sig == 0) return cudaSuccess;
+    const int64_t n = (int64_t)a.n_sig * a.pd.sumB;
+    const unsigned g1 = (unsigned)((n + 255) / 256);
+    if (precision == 1)
+        dt_sv_kernel<float><<<g1, 256, 0, st>>>(a);
+    else
+        dt_sv_kernel<double><<<g1, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dt_vote_kernel<<<(unsigned)a.n_sig, 1024, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const unsigned g3 = (unsigned)((n * 32 + kSolveThreads - 1) / kSolveThreads);
+    if (precision == 1)
+        dt_solve_kernel<float><<<g3, kSolveThreads, 0, st>>>(a);
+    else
+        dt_solve_kernel<double><<<g3, kSolveThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sfft

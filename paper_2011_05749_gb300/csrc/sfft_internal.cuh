@@ -74,11 +74,15 @@ struct PlanDesc {
     int32_t K;
     int32_t root_total;      // sum_d L_d: root-table entries (at st[0].root_off onwards)
     double invN;             // 1 / N
-    int32_t pad0;
+    int32_t mode;            // 0 peeling (Sec. 3.2), 1 one-shot (Sec. 3.1, one stage)
     int32_t ph_shift;        // two-level phasor tables: e^{2 pi i m / N} =
     int32_t ph_lo_off;       //   tw[ph_hi_off + (m >> ph_shift)] * tw[ph_lo_off + (m & mask)]
     int32_t ph_hi_off;
     uint64_t mu;             // floor((2^64 - 1) / N): Barrett reduction modulo N
+    int32_t am;              // one-shot: a_m (delay slots 0 .. 3 a_m - 1 hold -a_m .. 2 a_m - 1)
+    int32_t pad1;
+    double sv_floor;         // one-shot: singular values at or below this are not counted
+    double sp_tol2;          // one-shot: residual tolerance of the subspace pursuit
     StageDesc st[kMaxStages];
 };
 
@@ -123,6 +127,7 @@ struct DecodeWs {
     int64_t* rec_f;      // recovered frequencies
     void* rec_v;         // recovered values
     int32_t* ctr;        // counters, see Ctr
+    double* sv;          // one-shot: sumB * a_m singular values, then the vote threshold
 };
 
 // counter words of a signal slot

@@ -23,7 +23,8 @@ class Plan:
                  precision: str = "fp32", locate: str = "ml", noise_var: float = 0.0,
                  a_min: float = 1.0, eta: float = 0.0, c0: float = 4.0, c1: float = 2.0,
                  max_rounds: int = 64, max_batch: int = 1, max_tile: int = 0,
-                 wait_limit_log2: int = 0, fault_inject: int = 0, decode_ctas: int = 0):
+                 wait_limit_log2: int = 0, fault_inject: int = 0, decode_ctas: int = 0,
+                 decoder: str = "peel", a_m: int = 3):
         lib = load()
         f = np.ascontiguousarray(f, dtype=np.int64)
         delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -38,6 +39,8 @@ class Plan:
         o.wait_limit_log2 = wait_limit_log2
         o.fault_inject = fault_inject
         o.decode_ctas = decode_ctas
+        o.decoder = {"peel": _lib.DECODER_PEEL, "oneshot": _lib.DECODER_ONESHOT}[decoder]
+        o.oneshot_am = a_m
         o.noise_var = noise_var
         o.a_min = a_min
         o.eta = eta
@@ -53,6 +56,7 @@ class Plan:
         self.delays = delays.copy()
         self.R = int(delays.shape[1])
         self.dtype, self.precision, self.locate = dtype, precision, locate
+        self.decoder, self.a_m = decoder, a_m
         self.max_batch = max_batch
         self.num_bins = int(lib.sfft_plan_num_bins(h))
 

@@ -55,3 +55,44 @@ def test_product_code_never_imports_the_oracle():
                         assert (node.module or "").split(".")[0] != "oracle", path
             if fn.endswith((".cu", ".cuh", ".h", ".cpp")):
                 assert "sfft_oracle" not in open(path).read(), path
+
+
+def test_opts_layout_and_defaults_without_gpu():
+    """The binding's mirror of sfft_opts matches the C layout: the defaults written by the
+    library land in the right fields."""
+    import ctypes as ct
+    from paper_2011_05749_gb300 import _lib
+    o = _lib.Opts()
+    for name, _ in _lib.Opts._fields_:
+        setattr(o, name, 77)
+    _lib.load().sfft_opts_default(ct.byref(o))
+    assert (o.dtype, o.precision, o.locate, o.max_rounds, o.max_batch) == (0, 1, 1, 64, 1)
+    assert (o.a_min, o.c0, o.c1) == (1.0, 4.0, 2.0)
+    assert (o.decoder, o.oneshot_am, o.reserved) == (_lib.DECODER_PEEL, 3, 0)
+
+
+def test_oneshot_plan_rules_checked_without_gpu():
+    """One-shot plans (Sec. 3.1): one stage, K <= B, slots 0 .. 3 a_m - 1 = -a_m .. 2 a_m - 1
+    (mod N), at least 2 a_m random delays; violations fail before any device work."""
+    import ctypes as ct
+    import numpy as np
+    from paper_2011_05749_gb300 import _lib
+    lib = _lib.load()
+    N, am = 4096, 3
+    good = [(k - am) % N for k in range(3 * am)] + [100, 200, 300, 400, 500, 600, 700]
+
+    def create(f, delays, K=10, a_m=am):
+        o = _lib.Opts()
+        lib.sfft_opts_default(ct.byref(o))
+        o.decoder, o.oneshot_am = _lib.DECODER_ONESHOT, a_m
+        f = np.ascontiguousarray(f, dtype=np.int64)
+        d = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
+        h = ct.c_void_p()
+        return lib.sfft_plan_create(ct.byref(h), N, K, f.size, f.ctypes.data, d.shape[1],
+                                    d.ctypes.data, ct.byref(o))
+    inval = _lib.SFFT_EINVAL
+    assert create([16, 1], good + good) == inval                      # two stages
+    assert create([16], [0] + good[1:]) == inval                      # wrong consecutive set
+    assert create([16], good[:13]) == inval                           # P = 4 < 2 a_m
+    assert create([16], good, K=N // 16 + 1) == inval                  # K > B
+    assert create([16], good, a_m=4) == inval                          # a_m > 3
