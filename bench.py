@@ -287,6 +287,54 @@ def measure_large(sfft, hbm_peak, reps=10):
                        "peak_gbs": hbm_peak}}
 
 
+def measure_oneshot(sfft, batch=64, steps=20, warmup=3):
+    """The one-shot (sFFT-DT) decoder, Sec. 3.1: N = 2^21 complex64, one stage of B = 8192
+    = 32 K buckets (L = 256), K = 256 with |xhat| ~ U[1,10], a_m = 3, delays -3 .. 5 and 7
+    random (R = 16); exactly sparse and 30 dB.  Batches of `batch` signals (8 distinct, repeated)
+    through sfft_execute_batch; reports signals/s, the phases and the recovery."""
+    import torch
+    out = {"workload": "oneshot_2097152: N=2^21 complex64, B=8192 (L=256), K=256, "
+                       "|xhat|~U[1,10], a_m=3, R=16 (9 consecutive + 7 random delays)"}
+    for snr in (None, 30.0):
+        probs = [synth.config_problem("oneshot_2097152", seed=60 + i, snr_db=snr) for i in range(8)]
+        dl = probs[0].delays  # one plan: the same delays for every signal
+        probs = [synth.make_problem(p.N, p.f, p.K, seed=60 + i, delays=dl, mag=(1.0, 10.0),
+                                    snr_db=snr) for i, p in enumerate(probs)]
+        nv = float(np.mean([p.noise_var for p in probs]))
+        plan = sfft.Plan(probs[0].N, probs[0].K, probs[0].f, dl, decoder="oneshot", a_m=3,
+                         noise_var=nv, max_batch=batch)
+        dev = [torch.from_numpy(p.x.astype(np.complex64)).cuda() for p in probs]
+        xs = torch.stack([dev[i % len(dev)] for i in range(batch)])
+        res = plan.empty_outputs("cuda", batch)
+        for _ in range(warmup):
+            plan.execute_many(xs, res)
+        torch.cuda.synchronize()
+        plan.profile(reset=True)
+        plan.set_profiling(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.execute_many(xs, res)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = plan.profile(reset=True)
+        idx, val, info = (t.cpu().numpy() for t in res)
+        sup_ok, l2 = 0, []
+        for i, p in enumerate(probs):
+            n = int(info[i, 0])
+            sup_ok += int(n == p.K and np.array_equal(idx[i, :n], p.support))
+            if n == p.K:
+                l2.append(float(np.linalg.norm(val[i, :n] - p.values) / np.linalg.norm(p.values)))
+        plan.close()
+        out["exact" if snr is None else f"snr_{int(snr)}db"] = {
+            "signals_per_s": batch * 1e3 / ms, "ms_per_step": ms, "batch": batch,
+            "phases_ms_per_step": {k: v["ms"] / steps for k, v in prof.items()},
+            "support_equal_truth": f"{sup_ok}/{len(probs)}",
+            "rel_l2_vs_truth_max": max(l2) if l2 else None}
+    return out
+
+
 def measure_serving(sfft, plan, signals, rate, seconds, seed):
     """Submit requests (one workload signal each) at Poisson arrival times for `seconds`,
     then drain; latency = submit to completion, as the server measures it."""
@@ -496,6 +544,12 @@ def run_gpu(args):
     except Exception as exc:  # report, never fall back
         serving = {"error": repr(exc)[:200]}
 
+    oneshot = None
+    try:
+        oneshot = measure_oneshot(sfft)
+    except Exception as exc:  # report, never fall back
+        oneshot = {"error": repr(exc)[:200]}
+
     large = None
     if not args.no_large:
         try:
@@ -548,6 +602,7 @@ def run_gpu(args):
         "e2e": e2e,
         "serving": serving,
         "large_signal": large,
+        "oneshot": oneshot,
         "clocks": clk,
     }
     if rank == 0:

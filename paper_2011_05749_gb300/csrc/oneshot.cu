@@ -19,6 +19,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "launch.h"
 #include "sfft_internal.cuh"
 
@@ -48,13 +51,19 @@ __device__ __forceinline__ Cd divd(Cd a, Cd b)
     return {(a.x * b.x + a.y * b.y) * d, (a.y * b.x - a.x * b.y) * d};
 }
 
-// e^{2 pi i t / N} for 0 <= t < N
-__device__ __forceinline__ Cd root_n(int64_t t, int32_t N)
+// e^{2 pi i t / N} for 0 <= t < N from the plan's two-level root table (entries of the
+// plan's arithmetic type): e^{2 pi i (t >> s) 2^s / N} e^{2 pi i (t & (2^s - 1)) / N}
+template <typename T>
+__device__ __forceinline__ Cd root_n(const PlanDesc& pd, const void* roots, int64_t t)
 {
-    double s, c;
-    sincospi(2.0 * (double)t / (double)N, &s, &c);
-    return {c, s};
+    using V = typename C2<T>::t;
+    const V* tw = reinterpret_cast<const V*>(roots);
+    const V hi = __ldg(tw + pd.ph_hi_off + (int)(t >> pd.ph_shift));
+    const V lo = __ldg(tw + pd.ph_lo_off + (int)(t & ((1 << pd.ph_shift) - 1)));
+    return Cd{(double)hi.x, (double)hi.y} * Cd{(double)lo.x, (double)lo.y};
 }
+
+__device__ __forceinline__ int ldv(const int32_t* p) { return *(const volatile int32_t*)p; }
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -104,57 +113,70 @@ __device__ bool solve_lane(Cd* A, Cd* b, int n)
     return true;
 }
 
-// Eigenvalues of a Hermitian n x n matrix (n <= 3) by cyclic Jacobi rotations: for the
-// pivot g = G[p][q] = |g| e^{i phi}, the phase e^{-i phi} on coordinate q makes the 2 x 2
-// block real symmetric, and the rotation with t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
-// zeta = (G_qq - G_pp) / (2 |g|), annihilates it.
-__device__ void hermitian_eigenvalues(Cd G[3][3], int n, double* ev)
+// Eigenvalues of a Hermitian n x n matrix (n = NN <= 3, unrolled so G stays in registers)
+// by cyclic Jacobi rotations: for the pivot g = G[p][q] = |g| e^{i phi}, the phase e^{-i phi}
+// on coordinate q makes the 2 x 2 block real symmetric, and the rotation with
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (G_qq - G_pp) / (2 |g|), annihilates it.
+template <int NN>
+__device__ __forceinline__ void jacobi_rotate(Cd (&G)[3][3], int p, int q)
 {
-    for (int sweep = 0; sweep < 10; ++sweep) {
-        double off = 0.0, diag = 0.0;
-        for (int p = 0; p < n; ++p) {
-            diag += fabs(G[p][p].x);
-            for (int q = p + 1; q < n; ++q) off += abs2(G[p][q]);
-        }
-        if (off <= 1e-36 * diag * diag) break;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double ag = sqrt(abs2(G[p][q]));
-                const double a = G[p][p].x, b = G[q][q].x;
-                if (ag <= 1e-300 || ag <= 1e-18 * (fabs(a) + fabs(b))) {
-                    G[p][q] = G[q][p] = cd(0, 0);
-                    continue;
-                }
-                const Cd e = {G[p][q].x / ag, G[p][q].y / ag};  // e^{i phi}
-                const double zeta = (b - a) / (2.0 * ag);
-                const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
-                                                    : (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-                for (int r = 0; r < n; ++r) {
-                    if (r == p || r == q) continue;
-                    const Cd grp = G[r][p], grq = G[r][q];
-                    const Cd eg = conjd(e) * grq;
-                    const Cd nrp = {c * grp.x - s * eg.x, c * grp.y - s * eg.y};
-                    const Cd nrq = {s * grp.x + c * eg.x, s * grp.y + c * eg.y};
-                    G[r][p] = nrp;
-                    G[p][r] = conjd(nrp);
-                    G[r][q] = nrq;
-                    G[q][r] = conjd(nrq);
-                }
-                G[p][p] = cd(a - t * ag, 0);
-                G[q][q] = cd(b + t * ag, 0);
-                G[p][q] = G[q][p] = cd(0, 0);
-            }
+    const double ag = sqrt(abs2(G[p][q]));
+    const double a = G[p][p].x, b = G[q][q].x;
+    if (ag <= 1e-300 || ag <= 1e-18 * (fabs(a) + fabs(b))) {
+        G[p][q] = G[q][p] = cd(0, 0);
+        return;
     }
-    for (int p = 0; p < n; ++p) ev[p] = G[p][p].x;
+    const Cd e = {G[p][q].x / ag, G[p][q].y / ag};  // e^{i phi}
+    const double zeta = (b - a) / (2.0 * ag);
+    const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
+                                        : (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+#pragma unroll
+    for (int r = 0; r < NN; ++r) {
+        if (r == p || r == q) continue;
+        const Cd grp = G[r][p], grq = G[r][q];
+        const Cd eg = conjd(e) * grq;
+        const Cd nrp = {c * grp.x - s * eg.x, c * grp.y - s * eg.y};
+        const Cd nrq = {s * grp.x + c * eg.x, s * grp.y + c * eg.y};
+        G[r][p] = nrp;
+        G[p][r] = conjd(nrp);
+        G[r][q] = nrq;
+        G[q][r] = conjd(nrq);
+    }
+    G[p][p] = cd(a - t * ag, 0);
+    G[q][q] = cd(b + t * ag, 0);
+    G[p][q] = G[q][p] = cd(0, 0);
+}
+
+template <int NN>
+__device__ __forceinline__ void hermitian_eigenvalues(Cd (&G)[3][3], double* ev)
+{
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        double off = 0.0, diag = 0.0;
+#pragma unroll
+        for (int p = 0; p < NN; ++p) {
+            diag += fabs(G[p][p].x);
+#pragma unroll
+            for (int q = p + 1; q < NN; ++q) off += abs2(G[p][q]);
+        }
+        if (off <= 1e-30 * diag * diag) break;  // off-diagonal below 1e-15 of the diagonal
+#pragma unroll
+        for (int p = 0; p < NN; ++p)
+#pragma unroll
+            for (int q = p + 1; q < NN; ++q) jacobi_rotate<NN>(G, p, q);
+    }
+#pragma unroll
+    for (int p = 0; p < NN; ++p) ev[p] = G[p][p].x;
 }
 
 }  // namespace
 
-// DT1: one thread per (signal, bin position b); writes the a_m singular values of the
-// bucket, descending, at sv[b * a_m ..].
+// DT1a: one thread per (signal, bin position b).  Every singular value of M_{a_m} is at most
+// ||M||_F; a bucket whose ||M||_F (in the bins' type) is clearly below the vote's floor
+// cannot be voted: its singular values are written as zeros.  The others are listed (in
+// the slot's nzl array, count in ctr[kCtrDtList]) for the FP64 work of DT1b and DT3.
 template <typename T>
-__global__ void dt_sv_kernel(const __grid_constant__ DecodeArgs a)
+__global__ void dt_screen_kernel(const __grid_constant__ DecodeArgs a)
 {
     using V = typename C2<T>::t;
     const PlanDesc& pd = a.pd;
@@ -163,36 +185,77 @@ __global__ void dt_sv_kernel(const __grid_constant__ DecodeArgs a)
     if (gid >= (int64_t)a.n_sig * B) return;
     const int sig = (int)(gid / B), b = (int)(gid - (int64_t)sig * B);
     const V* Y = reinterpret_cast<const V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
-    const double invB = 1.0 / (double)B;
-    Cd m[5];  // m_0 .. m_{2 a_m - 2}
+    T e[5];  // |Y_k|^2 of m_0 .. m_{2 a_m - 2}
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        m[k] = cd(0, 0);
+        e[k] = 0;
         if (k < 2 * am - 1) {
+            const V y = __ldcg(Y + (int64_t)(k + am) * B + b);
+            e[k] = y.x * y.x + y.y * y.y;
+        }
+    }
+    T fro = 0;  // ||M||_F^2 B^2: m_{r+c} appears once per (r, c)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) fro += (T)min(k + 1, 2 * am - 1 - k) * e[k];
+    const double fl = 0.8 * pd.sv_floor * (double)B;
+    if ((double)fro < fl * fl) {
+        double* out = a.ws.sv + (int64_t)sig * ((int64_t)B * am + 1) + (int64_t)b * am;
+        for (int t = 0; t < am; ++t) out[t] = 0.0;
+        return;
+    }
+    int32_t* ctr = a.ws.ctr + (int64_t)sig * a.ctr_stride;
+    a.ws.nzl[(int64_t)sig * B + atomicAdd(ctr + kCtrDtList, 1)] = b;
+}
+
+// DT1b: the listed buckets' a_m singular values, descending, at sv[b * a_m ..], in FP64.
+// Grid (x, signal), threads striding over the signal's list.
+template <typename T, int AM>
+__global__ void dt_sv_kernel(const __grid_constant__ DecodeArgs a)
+{
+    using V = typename C2<T>::t;
+    const PlanDesc& pd = a.pd;
+    const int B = pd.sumB;
+    constexpr int am = AM;
+    const int sig = blockIdx.y;
+    const int n = ldv(a.ws.ctr + (int64_t)sig * a.ctr_stride + kCtrDtList);
+    const V* Y = reinterpret_cast<const V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
+    const double invB = 1.0 / (double)B;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int b = __ldcg(a.ws.nzl + (int64_t)sig * B + i);
+        Cd m[2 * AM - 1];  // m_0 .. m_{2 a_m - 2}
+#pragma unroll
+        for (int k = 0; k < 2 * AM - 1; ++k) {
             const V y = __ldcg(Y + (int64_t)(k + am) * B + b);
             m[k] = cd((double)y.x * invB, (double)y.y * invB);
         }
+        // G = M^H M with M[r][c] = m_{r+c}: G[p][q] = sum_r conj(m_{r+p}) m_{r+q}
+        Cd G[3][3];
+#pragma unroll
+        for (int p = 0; p < AM; ++p)
+#pragma unroll
+            for (int q = 0; q < AM; ++q) {
+                Cd s = cd(0, 0);
+#pragma unroll
+                for (int r = 0; r < AM; ++r) s = s + conjd(m[r + p]) * m[r + q];
+                G[p][q] = s;
+            }
+        double sv[3];
+        hermitian_eigenvalues<AM>(G, sv);
+#pragma unroll
+        for (int t = 0; t < AM; ++t) sv[t] = sqrt(fmax(sv[t], 0.0));
+#pragma unroll
+        for (int u = 1; u < AM; ++u)  // descending
+#pragma unroll
+            for (int k = u; k > 0; --k)
+                if (sv[k - 1] < sv[k]) {
+                    const double t = sv[k];
+                    sv[k] = sv[k - 1];
+                    sv[k - 1] = t;
+                }
+        double* out = a.ws.sv + (int64_t)sig * ((int64_t)B * am + 1) + (int64_t)b * am;
+#pragma unroll
+        for (int t = 0; t < AM; ++t) out[t] = sv[t];
     }
-    // G = M^H M with M[r][c] = m_{r+c}: G[p][q] = sum_r conj(m_{r+p}) m_{r+q}
-    Cd G[3][3];
-    for (int p = 0; p < am; ++p)
-        for (int q = 0; q < am; ++q) {
-            Cd s = cd(0, 0);
-            for (int r = 0; r < am; ++r) s = s + conjd(m[r + p]) * m[r + q];
-            G[p][q] = s;
-        }
-    double ev[3] = {0, 0, 0};
-    hermitian_eigenvalues(G, am, ev);
-    double sv[3];
-    for (int t = 0; t < am; ++t) sv[t] = sqrt(fmax(ev[t], 0.0));
-    for (int i = 1; i < am; ++i)  // descending
-        for (int k = i; k > 0 && sv[k - 1] < sv[k]; --k) {
-            const double t = sv[k];
-            sv[k] = sv[k - 1];
-            sv[k - 1] = t;
-        }
-    double* out = a.ws.sv + (int64_t)sig * ((int64_t)B * am + 1) + (int64_t)b * am;
-    for (int t = 0; t < am; ++t) out[t] = sv[t];
 }
 
 // DT2: one CTA per signal.  theta = the K-th largest singular value among those above the
@@ -214,8 +277,13 @@ __global__ void __launch_bounds__(1024) dt_vote_kernel(const __grid_constant__ D
         s_prefix = 0;
     }
     __syncthreads();
+    // only listed buckets can hold values above the floor (the others were written as zeros)
+    const int nl = ldv(a.ws.ctr + (int64_t)sig * a.ctr_stride + kCtrDtList);
+    const int32_t* list = a.ws.nzl + (int64_t)sig * pd.sumB;
+    const int am = pd.am, nv = nl * am;
+    auto value = [&](int i) { return __ldcg(sv + (int64_t)__ldcg(list + i / am) * am + i % am); };
     int cnt = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) cnt += __ldcg(sv + i) > floor_v;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) cnt += value(i) > floor_v;
     atomicAdd(&s_total, cnt);
     __syncthreads();
     const int total = s_total;
@@ -225,8 +293,8 @@ __global__ void __launch_bounds__(1024) dt_vote_kernel(const __grid_constant__ D
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
         const unsigned long long prefix = s_prefix;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const double v = __ldcg(sv + i);
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+            const double v = value(i);
             if (!(v > floor_v)) continue;
             const unsigned long long u = (unsigned long long)__double_as_longlong(v);
             if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
@@ -255,9 +323,24 @@ __global__ void __launch_bounds__(1024) dt_vote_kernel(const __grid_constant__ D
     }
 }
 
-// DT3: one warp per (signal, bin position b); buckets with no vote leave at once.
+template <typename T>
+__device__ __noinline__ void dt_solve_bucket(const DecodeArgs& a, int sig, int b);
+
+// DT3: grid (x, signal); each warp takes listed buckets of its signal in turn; buckets
+// without a vote are skipped.
 template <typename T>
 __global__ void __launch_bounds__(kSolveThreads) dt_solve_kernel(const __grid_constant__ DecodeArgs a)
+{
+    const int sig = blockIdx.y;
+    const int n = ldv(a.ws.ctr + (int64_t)sig * a.ctr_stride + kCtrDtList);
+    const int wpb = blockDim.x >> 5;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb)
+        dt_solve_bucket<T>(a, sig, __ldcg(a.ws.nzl + (int64_t)sig * a.pd.sumB + i));
+}
+
+// Steps 2-3 of one voted bucket by one warp (every lane calls with the same b).
+template <typename T>
+__device__ __noinline__ void dt_solve_bucket(const DecodeArgs& a, int sig, int b)
 {
     using V = typename C2<T>::t;
     const PlanDesc& pd = a.pd;
@@ -265,9 +348,6 @@ __global__ void __launch_bounds__(kSolveThreads) dt_solve_kernel(const __grid_co
     const int B = pd.sumB, am = pd.am, L = st.L;
     const int32_t N = pd.N;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (gw >= (int64_t)a.n_sig * B) return;
-    const int sig = (int)(gw / B), b = (int)(gw - (int64_t)sig * B);
     const double* sv = a.ws.sv + (int64_t)sig * ((int64_t)B * am + 1);
     const double theta = __ldcg(sv + (int64_t)B * am);
     int na = 0;
@@ -323,12 +403,10 @@ __global__ void __launch_bounds__(kSolveThreads) dt_solve_kernel(const __grid_co
         bq[t] = 0x7fffffff;
     }
     {
-        Cd z = root_n(((int64_t)j + (int64_t)lane * B) % N, N);
-        double s, cc;
-        sincospi(2.0 * 32.0 / (double)L, &s, &cc);
-        const Cd w = cd(cc, s);
+        Cd z = root_n<T>(pd, a.roots, ((int64_t)j + (int64_t)lane * B) % N);
+        const Cd w = root_n<T>(pd, a.roots, (32 * (int64_t)B) % N);  // e^{2 pi i 32 / L}
         for (int q = lane; q < L; q += 32) {
-            if (((q - lane) & 1023) == 0 && q != lane) z = root_n(((int64_t)j + (int64_t)q * B) % N, N);
+            if (((q - lane) & 1023) == 0 && q != lane) z = root_n<T>(pd, a.roots, ((int64_t)j + (int64_t)q * B) % N);
             Cd pz = cd(1, 0);
             for (int t = na - 1; t >= 0; --t) pz = pz * z + c[t];
             const double v = abs2(pz);
@@ -399,7 +477,7 @@ __global__ void __launch_bounds__(kSolveThreads) dt_solve_kernel(const __grid_co
         y = cd((double)v.x * invB, (double)v.y * invB);
     }
     const int64_t tau = mine ? (int64_t)st.tau[3 * am + lane] : 0;
-    for (int d = 0; d < kMaxAtoms; ++d) phi[d] = (mine && d < nd) ? root_n((dic[d] * tau) % N, N) : cd(0, 0);
+    for (int d = 0; d < kMaxAtoms; ++d) phi[d] = (mine && d < nd) ? root_n<T>(pd, a.roots, (dic[d] * tau) % N) : cd(0, 0);
 
     // least squares on the atoms sup[0..ns) by the normal equations; returns the residual
     // energy, the coefficients in p[], and this lane's residual in *r
@@ -512,15 +590,33 @@ cudaError_t launch_oneshot(const DecodeArgs& a, int precision, cudaStream_t st)
     if (a.n_sig == 0) return cudaSuccess;
     const int64_t n = (int64_t)a.n_sig * a.pd.sumB;
     const unsigned g1 = (unsigned)((n + 255) / 256);
+    // listed buckets are a small share: CTAs of 64 threads, about 4864 of them in all (32 per
+    // SM), split over the signals
+    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)a.pd.sumB + 63) / 64,
+                                                                         4864 / a.n_sig + 1));
+    const dim3 g2(gx, (unsigned)a.n_sig);
+    auto sv = [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        dt_screen_kernel<T><<<g1, 256, 0, st>>>(a);
+        if (a.pd.am == 1)
+            dt_sv_kernel<T, 1><<<g2, 64, 0, st>>>(a);
+        else if (a.pd.am == 2)
+            dt_sv_kernel<T, 2><<<g2, 64, 0, st>>>(a);
+        else
+            dt_sv_kernel<T, 3><<<g2, 64, 0, st>>>(a);
+    };
     if (precision == 1)
-        dt_sv_kernel<float><<<g1, 256, 0, st>>>(a);
+        sv((float*)nullptr);
     else
-        dt_sv_kernel<double><<<g1, 256, 0, st>>>(a);
+        sv((double*)nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dt_vote_kernel<<<(unsigned)a.n_sig, 1024, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const unsigned g3 = (unsigned)((n * 32 + kSolveThreads - 1) / kSolveThreads);
+    // warps of 4864 in all (32 per SM), split over the signals
+    const dim3 g3((unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)a.pd.sumB + 7) / 8,
+                                                                   4864 / 8 / a.n_sig + 1)),
+                  (unsigned)a.n_sig);
     if (precision == 1)
         dt_solve_kernel<float><<<g3, kSolveThreads, 0, st>>>(a);
     else

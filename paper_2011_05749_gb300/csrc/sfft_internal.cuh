@@ -139,6 +139,7 @@ enum Ctr : int {
     kCtrErr = 4,        // device error (timeout)
     kCtrBarCount = 5,   // group barrier arrivals
     kCtrBarGen = 6,     // group barrier generation
+    kCtrDtList = 7,     // one-shot decoder: buckets listed for the FP64 work (in nzl)
     kCtrRoundBase = 8,  // per round r (1-based): [3 r + 0] next-list size, [+1] non-zero
                         // bins, [+2] single-ton candidates
 };

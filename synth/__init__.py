@@ -141,6 +141,10 @@ CONFIGS = {
     # mid size used by the batched mix: N = 49*50*51
     "rffast_124950": dict(N=124950, f=(49, 50, 51), K=100, R=6, delays="random",
                           mag=(1.0, 10.0), snr_db=20.0),
+    # one-shot decoder (Sec. 3.1, Sec. 4.1 with B = 32 K): N = 2^21, one stage of B = 8192
+    # buckets (L = 256), K = 256, a_m = 3, delays -3 .. 5 then 7 random (R = 16)
+    "oneshot_2097152": dict(N=2097152, f=(256,), K=256, R=16, delays="oneshot", a_m=3,
+                            mag=(1.0, 10.0), snr_db=None),
     # large single signal: N = 511*512*513, 10 delays, K = 10000
     "rffast_134217216": dict(N=134217216, f=(511, 512, 513), K=10000, R=10, delays="random",
                              mag=(1.0, 10.0), snr_db=None),
@@ -150,5 +154,9 @@ CONFIGS = {
 def config_problem(name: str, seed: int, **over) -> Problem:
     c = dict(CONFIGS[name])
     c.update(over)
-    return make_problem(c["N"], c["f"], c["K"], seed, R=c["R"], delays=c["delays"],
+    delays = c["delays"]
+    if delays == "oneshot":
+        delays = oneshot_delays(c["N"], c["a_m"], c["R"] - 3 * c["a_m"],
+                                np.random.default_rng(seed + 7919))
+    return make_problem(c["N"], c["f"], c["K"], seed, R=c["R"], delays=delays,
                         mag=c["mag"], snr_db=c["snr_db"])

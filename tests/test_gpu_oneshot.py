@@ -122,3 +122,13 @@ def test_zero_signal(sfft):
     info = info.cpu().numpy()
     assert int(info[0]) == 0 and int(info[1]) == 0
     plan.close()
+
+
+def test_full_size_config_matches_oracle(sfft, oracle_mod):
+    """The benchmark's one-shot workload, N = 2^21, B = 8192, K = 256, R = 16, exactly
+    sparse, FP32: support equal to the oracle's (and the truth's), values within 1e-5."""
+    p = synth.config_problem("oneshot_2097152", seed=60)
+    ref = oracle_decode(oracle_mod, p, p.delays, 3, 3e-3)
+    np.testing.assert_array_equal(ref.idx, p.support)
+    got = run_gpu(sfft, p, p.delays, 3, "fp32")[0]
+    check(got, ref, "fp32")
