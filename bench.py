@@ -320,18 +320,24 @@ def measure_oneshot(sfft, batch=64, steps=20, warmup=3):
         ms = e0.elapsed_time(e1) / steps
         prof = plan.profile(reset=True)
         idx, val, info = (t.cpu().numpy() for t in res)
-        sup_ok, l2 = 0, []
+        sup_ok, l0, l2 = 0, 0, []
         for i, p in enumerate(probs):
             n = int(info[i, 0])
             sup_ok += int(n == p.K and np.array_equal(idx[i, :n], p.support))
-            if n == p.K:
-                l2.append(float(np.linalg.norm(val[i, :n] - p.values) / np.linalg.norm(p.values)))
+            # L0 / L2 over the union of the supports (missing coefficients count as zero)
+            got = dict(zip(idx[i, :n].tolist(), val[i, :n].tolist()))
+            ref = dict(zip(p.support.tolist(), p.values.tolist()))
+            keys = sorted(set(got) | set(ref))
+            l0 += len(set(got) ^ set(ref))
+            d = np.array([got.get(k, 0) - ref.get(k, 0) for k in keys])
+            l2.append(float(np.linalg.norm(d) / np.linalg.norm(p.values)))
         plan.close()
         out["exact" if snr is None else f"snr_{int(snr)}db"] = {
             "signals_per_s": batch * 1e3 / ms, "ms_per_step": ms, "batch": batch,
             "phases_ms_per_step": {k: v["ms"] / steps for k, v in prof.items()},
             "support_equal_truth": f"{sup_ok}/{len(probs)}",
-            "rel_l2_vs_truth_max": max(l2) if l2 else None}
+            "l0_vs_truth_total": l0, "l0_per_signal_of_K": l0 / len(probs) / probs[0].K,
+            "rel_l2_vs_truth_max": max(l2)}
     return out
 
 
