@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large single-signal measurement (N = 511*512*513)")
+    ap.add_argument("--only", choices=["large", "oneshot"], default=None,
+                    help="run only that block (a short run for profiling) and print its JSON")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip sfft_autotune and use the default schedule")
     ap.add_argument("--timed-only", action="store_true",
@@ -621,10 +623,27 @@ def run_gpu(args):
     return 0
 
 
+def run_only(args):
+    """One block on its own, with few repetitions: the commands the ncu summaries use."""
+    import paper_2011_05749_gb300 as sfft
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        peak = 6800.0
+    if args.only == "large":
+        out = measure_large(sfft, peak, reps=max(1, args.steps))
+    else:
+        out = measure_oneshot(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
+    print(json.dumps(out, default=float), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_gpu(args)
 
 
