@@ -45,7 +45,8 @@ class _Stats(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("noise_var", ctypes.c_double), ("a_min", ctypes.c_double),
                 ("eta", ctypes.c_double), ("c0", ctypes.c_double), ("c1", ctypes.c_double),
-                ("locate", ctypes.c_int32), ("max_rounds", ctypes.c_int32)]
+                ("locate", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
+                ("kay_m", ctypes.c_int32)]
 
 
 class _RoundLog(ctypes.Structure):
@@ -130,8 +131,9 @@ class OracleOpts:
     eta: float = 1e-6
     c0: float = 4.0
     c1: float = 2.0
-    locate: int = 0          # 0 ARG (FFAST phase), 1 ML (candidate enumeration)
+    locate: int = 0          # 0 ARG (FFAST phase), 1 ML (candidate enumeration), 2 KAY
     max_rounds: int = 64
+    kay_m: int = 2           # KAY: delays per iteration (slots c m + t hold r_c + t 2^c)
 
 
 def thresholds(N: int, f, R: int, opts: OracleOpts):
@@ -165,7 +167,7 @@ def decode(N: int, f, delays, Y, K: int, opts: OracleOpts | None = None) -> dict
             for k in ("idents", "n_zero", "n_single", "n_multi", "n_accepted")}
     rl = _RoundLog(*[_ptr(logs[k]) for k in
                      ("idents", "n_zero", "n_single", "n_multi", "n_accepted")])
-    co = _Opts(opts.noise_var, opts.a_min, opts.eta, opts.c0, opts.c1, opts.locate, mr)
+    co = _Opts(opts.noise_var, opts.a_min, opts.eta, opts.c0, opts.c1, opts.locate, mr, opts.kay_m)
     st = _Stats()
     rc = _load().oracle_decode(N, D, _ptr(f), R, _ptr(delays), _ptr(Y), K, ctypes.byref(co),
                                _ptr(out_idx), _ptr(out_val), _ptr(rec_f), _ptr(rec_v),

@@ -25,7 +25,9 @@
  *     with sigma^2 the noise variance per time sample;
  *   - locate: ARG reads the phase of Y(tau=1) conj(Y(tau=0)) (Sec. 3.2, subproblem 2, exactly
  *     sparse case) and snaps it to the candidate set {j, j+B, ..., j+(L-1)B}; ML picks the
- *     candidate of that set whose delay phasors best correlate with the bin vector;
+ *     candidate of that set whose delay phasors best correlate with the bin vector; KAY
+ *     (general sparse case, Eq. 21-22) reads one bit of f / N per iteration of structured
+ *     delays r_c + t 2^c and takes the candidate nearest the interval the bits leave;
  *   - value: least squares over all R delays (the LSM of the general sparse case);
  *   - a frequency that is a singleton in several stages in one round is taken from the
  *     lowest stage; a frequency already recovered in an earlier round is not taken again;
@@ -189,8 +191,9 @@ typedef struct {
     double a_min;     /* smallest significant |xhat| */
     double eta;       /* relative numerical floor of the thresholds */
     double c0, c1;    /* zero-ton / single-ton threshold multipliers */
-    int32_t locate;   /* 0 = ARG (needs delays 0 and 1 in every stage), 1 = ML */
+    int32_t locate;   /* 0 = ARG (needs delays 0 and 1 in every stage), 1 = ML, 2 = KAY */
     int32_t max_rounds;
+    int32_t kay_m;    /* KAY: delays per iteration m (slots c m + t hold r_c + t 2^c) */
 } oracle_opts;
 
 typedef struct {
@@ -234,6 +237,40 @@ static void fit_tone(const cplx* y, int32_t R, const int64_t* tau, int64_t f, in
     }
     *v_out = v;
     *rho_out = rho;
+}
+
+/* Kay's weights of Eq. 22 for m delays per iteration: w_t, t = 0 .. m-2 */
+static double kay_weight(int32_t m, int32_t t)
+{
+    double u = (2.0 * t - m + 2.0) / (2.0 * m);
+    return 3.0 * m / (2.0 * ((double)m * m - 1.0)) * (1.0 - 4.0 * u * u);
+}
+
+/* R-FFAST single-ton locate of the general sparse case (Sec. 3.2, subproblem 2): the delay
+ * slots form C = R / m iterations, slot c m + t holding r_c + t 2^c.  Iteration c gives
+ * the phase differences Delta_t = arg(y_{c,t+1} conj(y_{c,t})), t < m - 1, each about
+ * 2 pi 2^c f / N (mod 2 pi); Eq. 21 averages them with the weights of Eq. 22 into an
+ * estimate of the angle of omega^{2^c f}, omega = e^{2 pi i / N}.  The binary search reads
+ * one bit per iteration: the angle in [0, pi) keeps the lower half of the current range of
+ * f / N, otherwise the upper half, so after C iterations f / N lies in
+ * [k / 2^C, (k + 1) / 2^C).  The candidate j + q B of the bin nearest the centre of that
+ * interval (around the circle of N frequencies) is the location.                         */
+static int64_t locate_kay(const cplx* yv, int32_t R, int32_t m, int64_t j, int64_t B, int64_t L,
+                          int64_t N)
+{
+    int32_t C = R / m;
+    int64_t k = 0;
+    for (int32_t c = 0; c < C; ++c) {
+        double th = 0.0;
+        for (int32_t t = 0; t + 1 < m; ++t)
+            th += kay_weight(m, t) * carg(yv[c * m + t + 1] * conj(yv[c * m + t]));
+        double ph = fmod(th, OR_TWO_PI);
+        if (ph < 0) ph += OR_TWO_PI;
+        k = 2 * k + (ph >= OR_TWO_PI / 2 ? 1 : 0);
+    }
+    double target = ((double)k + 0.5) * (double)N / ldexp(1.0, C);
+    double qd = floor((target - (double)j) / (double)B + 0.5);
+    return j + pos_mod((int64_t)qd, L) * B;
 }
 
 typedef struct { int64_t f; cplx v; } rec_entry;
@@ -295,6 +332,12 @@ int oracle_decode(int64_t N, int32_t n_stages, const int64_t* f, int32_t R, cons
         }
         if (opt->locate == 0 && (r0[d] < 0 || r1[d] < 0)) return OR_EINVAL;
     }
+    if (opt->locate == 2) {
+        /* C = R / m iterations must tell the L candidates of every stage apart: 2^C >= L */
+        if (opt->kay_m < 2 || R % opt->kay_m != 0 || R / opt->kay_m > 30) return OR_EINVAL;
+        for (int32_t d = 0; d < D; ++d)
+            if (((int64_t)1 << (R / opt->kay_m)) < f[d]) return OR_EINVAL;
+    }
 
     unsigned char* state = (unsigned char*)calloc((size_t)nb, 1); /* 0 open, else class */
     int64_t* cand_f = (int64_t*)malloc(sizeof(int64_t) * (size_t)nb);
@@ -337,7 +380,9 @@ int oracle_decode(int64_t N, int32_t n_stages, const int64_t* f, int32_t R, cons
             idents++;
             if (E <= T0[d]) { state[b] = OR_ZERO; nz++; continue; }
             int64_t L = f[d], fq;
-            if (opt->locate == 0) {
+            if (opt->locate == 2) {
+                fq = locate_kay(yv, R, opt->kay_m, j, B[d], L, N);
+            } else if (opt->locate == 0) {
                 /* FFAST phase encoding: angle of y(1)/y(0) times N / 2 pi, snapped to the bin's
                  * candidate set {j + q B} */
                 cplx ratio = yv[r1[d]] * conj(yv[r0[d]]);

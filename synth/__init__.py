@@ -86,6 +86,23 @@ def draw_delays(N: int, n_stages: int, R: int, rng: np.random.Generator, fixed=(
     return out
 
 
+def kay_delays(N: int, n_stages: int, C: int, m: int, rng: np.random.Generator) -> np.ndarray:
+    """Structured R-FFAST delays (Sec. 4.2): per stage, C iterations of m delays
+    r_c, r_c + 2^c, ..., r_c + (m - 1) 2^c (mod N) with r_c uniform; slot c m + t.  All
+    distinct within a stage."""
+    out = np.zeros((n_stages, C * m), dtype=np.int64)
+    for d in range(n_stages):
+        while True:
+            row = []
+            for c in range(C):
+                r = int(rng.integers(0, N))
+                row += [(r + t * (1 << c)) % N for t in range(m)]
+            if len(set(row)) == len(row):
+                break
+        out[d] = row
+    return out
+
+
 def oneshot_delays(N: int, a_m: int, P: int, rng: np.random.Generator) -> np.ndarray:
     """Delays of the one-shot decoder's single stage: the consecutive set -a_m .. 2 a_m - 1
     (mod N), then P distinct uniform draws outside it (Sec. 4.1, Stage 1)."""

@@ -175,6 +175,48 @@ def test_ml_locate_is_brute_force_over_candidates(oracle_mod):
         assert abs(res["val"][0] - v) < 1e-12
 
 
+def test_kay_locate_every_frequency(oracle_mod):
+    """KAY locate (Sec. 3.2 subproblem 2, Eq. 21-22) on structured delays r_c + t 2^c: a
+    single tone at every frequency of N = 504 (L = 7, 8, 9; C = 4 iterations) is located
+    exactly, for m = 2 and for m = 4 (where Eq. 22's weights must sum to one for the
+    averaged phase to land on the tone's)."""
+    N, f = 504, (7, 8, 9)
+    rng = np.random.default_rng(13)
+    for m in (2, 4):
+        delays = synth.kay_delays(N, 3, 4, m, rng)
+        for k in range(N):
+            v = 1.5 * np.exp(1j * rng.uniform(0, 2 * np.pi))
+            x = synth.time_signal(N, [k], [v])
+            Y = oracle_mod.bucketize(N, f, delays, x)
+            res = oracle_mod.decode(N, f, delays, Y, K=1,
+                                    opts=oracle_mod.OracleOpts(locate=2, kay_m=m))
+            assert list(res["idx"]) == [k], (m, k)
+            assert abs(res["val"][0] - v) < 1e-12
+
+
+def test_kay_exact_recovery_124950(oracle_mod):
+    """Exactly sparse, N = 49*50*51 with C = 6 iterations of m = 3 delays per stage: the
+    peeling decoder with KAY locate returns the truth."""
+    N, f = 124950, (49, 50, 51)
+    dl = synth.kay_delays(N, 3, 6, 3, np.random.default_rng(3))
+    p = synth.make_problem(N, f, 60, seed=4, delays=dl, mag=(1.0, 10.0))
+    Y = oracle_mod.bucketize(N, f, dl, p.x)
+    res = oracle_mod.decode(N, f, dl, Y, K=60, opts=oracle_mod.OracleOpts(locate=2, kay_m=3))
+    assert res["status"] == 0
+    np.testing.assert_array_equal(res["idx"], p.support)
+    np.testing.assert_allclose(res["val"], p.values, rtol=0, atol=1e-11)
+
+
+def test_kay_needs_enough_iterations(oracle_mod):
+    """2^C must reach L: C = 5 iterations cannot tell L = 51 candidates apart."""
+    N, f = 124950, (49, 50, 51)
+    dl = synth.kay_delays(N, 3, 5, 2, np.random.default_rng(3))
+    p = synth.make_problem(N, f, 10, seed=4, delays=dl)
+    Y = oracle_mod.bucketize(N, f, dl, p.x)
+    with pytest.raises(ValueError):
+        oracle_mod.decode(N, f, dl, Y, K=10, opts=oracle_mod.OracleOpts(locate=2, kay_m=2))
+
+
 def test_noisy_rffast_recovers_truth(oracle_mod):
     """General sparse case at 30 dB: every true frequency found, values within noise."""
     p = synth.make_problem(124950, (49, 50, 51), 60, seed=21, R=8, delays="random",
