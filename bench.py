@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large single-signal measurement (N = 511*512*513)")
-    ap.add_argument("--only", choices=["large", "oneshot"], default=None,
+    ap.add_argument("--only", choices=["large", "oneshot", "locate"], default=None,
                     help="run only that block (a short run for profiling) and print its JSON")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip sfft_autotune and use the default schedule")
@@ -326,13 +326,9 @@ def measure_oneshot(sfft, batch=64, steps=20, warmup=3):
         for i, p in enumerate(probs):
             n = int(info[i, 0])
             sup_ok += int(n == p.K and np.array_equal(idx[i, :n], p.support))
-            # L0 / L2 over the union of the supports (missing coefficients count as zero)
-            got = dict(zip(idx[i, :n].tolist(), val[i, :n].tolist()))
-            ref = dict(zip(p.support.tolist(), p.values.tolist()))
-            keys = sorted(set(got) | set(ref))
-            l0 += len(set(got) ^ set(ref))
-            d = np.array([got.get(k, 0) - ref.get(k, 0) for k in keys])
-            l2.append(float(np.linalg.norm(d) / np.linalg.norm(p.values)))
+            e0_, e2_ = union_errors(idx[i], val[i], n, p)
+            l0 += e0_
+            l2.append(e2_)
         plan.close()
         out["exact" if snr is None else f"snr_{int(snr)}db"] = {
             "signals_per_s": batch * 1e3 / ms, "ms_per_step": ms, "batch": batch,
@@ -340,6 +336,61 @@ def measure_oneshot(sfft, batch=64, steps=20, warmup=3):
             "support_equal_truth": f"{sup_ok}/{len(probs)}",
             "l0_vs_truth_total": l0, "l0_per_signal_of_K": l0 / len(probs) / probs[0].K,
             "rel_l2_vs_truth_max": max(l2)}
+    return out
+
+
+def union_errors(idx, val, n, p):
+    """L0 and relative L2 of one result against the truth over the union of the supports
+    (a missing coefficient counts as zero)."""
+    got = dict(zip(idx[:n].tolist(), val[:n].tolist()))
+    ref = dict(zip(p.support.tolist(), p.values.tolist()))
+    keys = sorted(set(got) | set(ref))
+    d = np.array([got.get(k, 0) - ref.get(k, 0) for k in keys])
+    return len(set(got) ^ set(ref)), float(np.linalg.norm(d) / np.linalg.norm(p.values))
+
+
+def measure_locate_modes(sfft, batch=64, steps=20, warmup=3):
+    """The R-FFAST workload's signals (N = 127*128*129, K = 1000, 20 dB) located two ways:
+    ML over the candidates with 8 delays per stage (0, 1, 6 random; the benchmark's mode)
+    and the paper's structured delays with the Kay estimator and binary search (Sec. 3.2,
+    Eq. 21-22; C = 8 iterations of m = 2, 16 delays per stage).  Same signals for both."""
+    import torch
+    N, f, K = CFG["N"], CFG["f"], CFG["K"]
+    modes = {"ml": dict(delays=synth.draw_delays(N, 3, 8, np.random.default_rng(71)), kw={}),
+             "kay": dict(delays=synth.kay_delays(N, 3, 8, 2, np.random.default_rng(72)),
+                         kw=dict(locate="kay", kay_m=2))}
+    out = {"workload": f"{WORKLOAD} signals at 20 dB; ml: 8 delays (0, 1, 6 random); "
+                       "kay: 16 structured delays (C = 8, m = 2)"}
+    for name, md in modes.items():
+        probs = [synth.make_problem(N, f, K, seed=80 + i, delays=md["delays"], mag=(1.0, 10.0),
+                                    snr_db=20.0) for i in range(8)]
+        nv = float(np.mean([p.noise_var for p in probs]))
+        kw = dict(precision="fp32", noise_var=nv, max_batch=batch, **md["kw"])
+        if name == "ml":
+            kw["locate"] = "ml"
+        plan = sfft.Plan(N, K, f, md["delays"], **kw)
+        dev = [torch.from_numpy(p.x.astype(np.complex64)).cuda() for p in probs]
+        xs = torch.stack([dev[i % len(dev)] for i in range(batch)])
+        res = plan.empty_outputs("cuda", batch)
+        for _ in range(warmup):
+            plan.execute_many(xs, res)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.execute_many(xs, res)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        idx, val, info = (t.cpu().numpy() for t in res)
+        errs = [union_errors(idx[i], val[i], int(info[i, 0]), p) for i, p in enumerate(probs)]
+        plan.close()
+        del xs, dev
+        out[name] = {"delays_per_stage": int(md["delays"].shape[1]),
+                     "signals_per_s": batch * 1e3 / ms, "ms_per_step": ms, "batch": batch,
+                     "l0_vs_truth_total": int(sum(e[0] for e in errs)),
+                     "rel_l2_vs_truth_max": max(e[1] for e in errs),
+                     "status_incomplete": int(np.sum(info[:len(probs), 1] == 2))}
     return out
 
 
@@ -557,6 +608,11 @@ def run_gpu(args):
         oneshot = measure_oneshot(sfft)
     except Exception as exc:  # report, never fall back
         oneshot = {"error": repr(exc)[:200]}
+    locate_modes = None
+    try:
+        locate_modes = measure_locate_modes(sfft)
+    except Exception as exc:  # report, never fall back
+        locate_modes = {"error": repr(exc)[:200]}
 
     large = None
     if not args.no_large:
@@ -611,6 +667,7 @@ def run_gpu(args):
         "serving": serving,
         "large_signal": large,
         "oneshot": oneshot,
+        "locate_ml_vs_kay": locate_modes,
         "clocks": clk,
     }
     if rank == 0:
@@ -632,6 +689,8 @@ def run_only(args):
         peak = 6800.0
     if args.only == "large":
         out = measure_large(sfft, peak, reps=max(1, args.steps))
+    elif args.only == "locate":
+        out = measure_locate_modes(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     else:
         out = measure_oneshot(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     print(json.dumps(out, default=float), flush=True)

@@ -73,6 +73,12 @@ typedef struct sfft_server_s* sfft_server_t;
                                 candidates; needs delays 0 and 1 in every stage (FFAST) */
 #define SFFT_LOCATE_ML 1     /* best delay-phasor correlation over the L_d candidates
                                 {j, j + B_d, ...} of the bin (random delays, R-FFAST) */
+#define SFFT_LOCATE_KAY 2    /* R-FFAST with structured delays (Sec. 3.2 subproblem 2,
+                                Eq. 21-22): slot c m + t of every stage holds r_c + t 2^c
+                                (mod N), C = n_delays / m iterations with 2^C >= L_d; each
+                                iteration's Kay-weighted phase difference gives one bit of
+                                f / N, and the bin's candidate nearest the resulting
+                                interval is the location (m = opts->kay_m) */
 
 /* decoder (Sec. 3) */
 #define SFFT_DECODER_PEEL 0     /* FFAST / R-FFAST peeling across stages (Sec. 3.2) */
@@ -105,6 +111,7 @@ typedef struct {
     int32_t decoder;          /* SFFT_DECODER_PEEL (default) or SFFT_DECODER_ONESHOT */
     int32_t oneshot_am;       /* one-shot decoder: a_m, the most frequencies one bucket may
                                  hold (1..3, default 3) */
+    int32_t kay_m;            /* SFFT_LOCATE_KAY: delays per iteration m >= 2 (default 2) */
     int32_t reserved;
 } sfft_opts;
 
@@ -122,8 +129,9 @@ void sfft_opts_default(sfft_opts* opts);
  * followed by P >= 2 a_m distinct random delays (a_m = opts->oneshot_am).
  * Host arrays; the plan copies them.  N < 2^30.  The plan owns device tables (twiddles,
  * index maps) and the workspace for opts->max_batch signals until sfft_plan_destroy.
- * Errors: SFFT_EINVAL (bad sizes, factors, delays, ARG without delays 0 and 1, a one-shot
- * plan breaking the rules above), SFFT_ENOMEM, SFFT_ECUDA.                                */
+ * Errors: SFFT_EINVAL (bad sizes, factors, delays, ARG without delays 0 and 1, KAY delays
+ * without the structure of SFFT_LOCATE_KAY, a one-shot plan breaking the rules above),
+ * SFFT_ENOMEM, SFFT_ECUDA.                                                                */
 int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t n_stages, const int64_t* f,
                      int32_t n_delays, const int64_t* delays, const sfft_opts* opts);
 void sfft_plan_destroy(sfft_plan_t plan);

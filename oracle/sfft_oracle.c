@@ -254,13 +254,21 @@ static double kay_weight(int32_t m, int32_t t)
  * one bit per iteration: the angle in [0, pi) keeps the lower half of the current range of
  * f / N, otherwise the upper half, so after C iterations f / N lies in
  * [k / 2^C, (k + 1) / 2^C).  The candidate j + q B of the bin nearest the centre of that
- * interval (around the circle of N frequencies) is the location.                         */
+ * interval (around the circle of N frequencies) is the location.
+ * Reading where the paper is silent: when L divides 2^c, every candidate of the bin gives
+ * the same 2^c f / N mod 1 = 2^c j / N mod 1, so the phase of that iteration carries no
+ * information and can sit exactly on the decision boundary (j = 0); its bit is then taken
+ * from j by integer arithmetic, floor(2^{c+1} j / N) mod 2.                               */
 static int64_t locate_kay(const cplx* yv, int32_t R, int32_t m, int64_t j, int64_t B, int64_t L,
                           int64_t N)
 {
     int32_t C = R / m;
     int64_t k = 0;
     for (int32_t c = 0; c < C; ++c) {
+        if ((((int64_t)1 << c) % L) == 0) {
+            k = 2 * k + (((j << (c + 1)) / N) & 1);
+            continue;
+        }
         double th = 0.0;
         for (int32_t t = 0; t + 1 < m; ++t)
             th += kay_weight(m, t) * carg(yv[c * m + t + 1] * conj(yv[c * m + t]));

@@ -28,7 +28,7 @@ SFFT_ETOOBIG = -8
 
 C64, C128 = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
-LOCATE_ARG, LOCATE_ML = 0, 1
+LOCATE_ARG, LOCATE_ML, LOCATE_KAY = 0, 1, 2
 DECODER_PEEL, DECODER_ONESHOT = 0, 1
 
 
@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
                 ("eta", ctypes.c_double), ("c0", ctypes.c_double), ("c1", ctypes.c_double),
                 ("wait_limit_log2", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
                 ("decode_ctas", ctypes.c_int32), ("decoder", ctypes.c_int32),
-                ("oneshot_am", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("oneshot_am", ctypes.c_int32), ("kay_m", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

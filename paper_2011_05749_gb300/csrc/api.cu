@@ -104,6 +104,7 @@ extern "C" void sfft_opts_default(sfft_opts* o)
     o->c1 = 2.0;
     o->decoder = SFFT_DECODER_PEEL;
     o->oneshot_am = 3;
+    o->kay_m = 2;
 }
 
 static void free_plan_memory(sfft_plan_s* p)
@@ -143,7 +144,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         return SFFT_EINVAL;
     if ((o.dtype != SFFT_C64 && o.dtype != SFFT_C128) ||
         (o.precision != SFFT_PREC_FP32 && o.precision != SFFT_PREC_FP64) ||
-        (o.locate != SFFT_LOCATE_ARG && o.locate != SFFT_LOCATE_ML) || o.max_rounds < 1 ||
+        (o.locate != SFFT_LOCATE_ARG && o.locate != SFFT_LOCATE_ML && o.locate != SFFT_LOCATE_KAY) ||
+        o.max_rounds < 1 ||
         o.max_rounds > 4096 || o.max_batch < 1 || o.max_tile < 0 || o.noise_var < 0 || o.a_min < 0 ||
         o.eta < 0 || o.c0 < 0 || o.c1 < 0)
         return SFFT_EINVAL;
@@ -159,6 +161,22 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         }
     }
     if (o.decoder != SFFT_DECODER_PEEL && o.decoder != SFFT_DECODER_ONESHOT) return SFFT_EINVAL;
+    if (o.locate == SFFT_LOCATE_KAY && o.decoder == SFFT_DECODER_PEEL) {
+        // structured delays: slot c m + t = r_c + t 2^c (mod N); 2^C >= L_d tells the L_d
+        // candidates apart
+        const int m = o.kay_m;
+        if (m < 2 || n_delays % m != 0 || n_delays / m > 30) return SFFT_EINVAL;
+        const int C = n_delays / m;
+        for (int d = 0; d < n_stages; ++d) {
+            if ((1ll << C) < f[d]) return SFFT_EINVAL;
+            for (int c = 0; c < C; ++c)
+                for (int t = 1; t < m; ++t) {
+                    const int64_t base = delays[(int64_t)d * n_delays + c * m];
+                    if (delays[(int64_t)d * n_delays + c * m + t] != (base + ((int64_t)t << c)) % N)
+                        return SFFT_EINVAL;
+                }
+        }
+    }
     if (o.decoder == SFFT_DECODER_ONESHOT) {
         // one stage; slots 0 .. 3 a_m - 1 hold -a_m .. 2 a_m - 1 (mod N), then at least 2 a_m
         // random delays (Sec. 4.1, Stage 1); the output holds at most one value per bucket
@@ -196,6 +214,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     pd.invN = 1.0 / (double)N;
     pd.mu = ~0ull / (uint64_t)N;
     pd.mode = o.decoder == SFFT_DECODER_ONESHOT ? 1 : 0;
+    pd.kay_m = o.locate == SFFT_LOCATE_KAY ? o.kay_m : 0;
     if (pd.mode == 1) {
         // the vote's floor: a_m times the per-delay zero-ton level of a bucket in moment
         // units, sqrt(c0 B sigma^2 + (eta B a_min)^2) / B; the pursuit's residual tolerance

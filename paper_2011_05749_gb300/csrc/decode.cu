@@ -265,10 +265,12 @@ __device__ __forceinline__ int ml_group_size(int n, int Lmax, int R, int nt)
     return best_g;
 }
 
-// D2, ARG locate (FFAST, Sec. 3.2 subproblem 2): f from the phase of Y(1) conj(Y(0)) in
-// FP64, snapped to the candidate set {j + q B}; one thread per bin.
+// D2, phase locate, one thread per bin: ARG (FFAST, Sec. 3.2 subproblem 2, exact case): f
+// from the phase of Y(1) conj(Y(0)) in FP64; KAY (general sparse case, Eq. 21-22): one bit
+// of f / N per iteration of structured delays, in FP64.  Either estimate is snapped to the
+// bin's candidate set {j + q B}; then the least-squares value and the residual test.
 template <typename T>
-__device__ void locate_arg_thread(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+__device__ void locate_phase_thread(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
                                   const typename C2<T>::t* Y, int round, int b)
 {
     using V = typename C2<T>::t;
@@ -279,23 +281,62 @@ __device__ void locate_arg_thread(const DecodeArgs& a, int32_t* ctr, const Decod
     const int B = st.B, L = st.L, N = pd.N;
     const int j = __ldg(a.pbin + b);
     const V* Yb = Y + st.y_off + (b - st.bin_base);
-    const V y0 = __ldcg(Yb + (int64_t)st.r0 * B);
-    const V y1 = __ldcg(Yb + (int64_t)st.r1 * B);
-    const double rx = (double)y1.x * y0.x + (double)y1.y * y0.y;
-    const double ry = (double)y1.y * y0.x - (double)y1.x * y0.y;
-    const double fe = atan2(ry, rx) * (double)N / 6.283185307179586476925286766559;
+    constexpr double kTwoPi = 6.283185307179586476925286766559;
+    V ar[kMaxDelays], yv[kMaxDelays];
+#pragma unroll
+    for (int r = 0; r < kMaxDelays; ++r)
+        if (r < R) yv[r] = __ldcg(Yb + (int64_t)r * B);
+    double fe;  // estimated position on the circle of N frequencies
+    if (pd.locate == 2) {
+        // KAY (general sparse case, Eq. 21-22): slots c m + t hold r_c + t 2^c; iteration c
+        // averages the phase differences arg(y_{c,t+1} conj(y_{c,t})) with Kay's weights into
+        // the angle of omega^{2^c f} and reads one bit of f / N from it (binary search); the
+        // C bits leave f / N in [k / 2^C, (k + 1) / 2^C), whose centre is fe / N
+        const int m = pd.kay_m;
+        int64_t k = 0;
+        double th = 0.0;
+        V yp = yv[0];
+#pragma unroll 1
+        for (int r = 1; r < R; ++r) {
+            const int t1 = r % m;  // t + 1 of this difference, 0 at an iteration's first slot
+            const V yr = __ldcg(Yb + (int64_t)r * B);
+            if (t1 != 0) {
+                const double rx = (double)yr.x * yp.x + (double)yr.y * yp.y;
+                const double ry = (double)yr.y * yp.x - (double)yr.x * yp.y;
+                const double u = (2.0 * (t1 - 1) - m + 2.0) / (2.0 * m);
+                th += 3.0 * m / (2.0 * ((double)m * m - 1.0)) * (1.0 - 4.0 * u * u) * atan2(ry, rx);
+            }
+            if (t1 == m - 1) {
+                // iteration c complete.  The weights are positive and sum to one, so th lies
+                // in (-pi, pi]; its angle mod 2 pi is in [pi, 2 pi) (upper half) iff th < 0 or
+                // th = pi.  When L divides 2^c the iteration carries no information (every
+                // candidate gives 2^c f / N = 2^c j / N mod 1, possibly exactly on the
+                // boundary): the bit comes from j, floor(2^{c+1} j / N) mod 2.
+                const int c = r / m;
+                if (((1ll << c) % L) == 0)
+                    k = 2 * k + ((((int64_t)j << (c + 1)) / N) & 1);
+                else
+                    k = 2 * k + ((th < 0.0 || th >= kTwoPi / 2) ? 1 : 0);
+                th = 0.0;
+            }
+            yp = yr;
+        }
+        fe = ((double)k + 0.5) * (double)N / (double)(1ll << (R / m));
+    } else {
+        // ARG (FFAST phase encoding): angle of y(1) conj(y(0)) times N / 2 pi
+        const V u0 = __ldcg(Yb + (int64_t)st.r0 * B), u1 = __ldcg(Yb + (int64_t)st.r1 * B);
+        const double rx = (double)u1.x * u0.x + (double)u1.y * u0.y;
+        const double ry = (double)u1.y * u0.x - (double)u1.x * u0.y;
+        fe = atan2(ry, rx) * (double)N / kTwoPi;
+    }
+    // the bin's candidate j + q B nearest fe
     const double qd = floor((fe - (double)j) / (double)B + 0.5);
     int64_t q = (int64_t)qd % L;
     if (q < 0) q += L;
     const int64_t f = (int64_t)j + q * B;
-    V ar[kMaxDelays], yv[kMaxDelays];
 #pragma unroll
-    for (int r = 0; r < kMaxDelays; ++r) {
-        if (r < R) {
-            ar[r] = delay_phasor<T>(a, f, st.tau[r]);
-            yv[r] = __ldcg(Yb + (int64_t)r * B);
-        }
-    }
+    for (int r = 0; r < kMaxDelays; ++r)
+        if (r < R) ar[r] = delay_phasor<T>(a, f, st.tau[r]);
     V c = {0, 0};
 #pragma unroll
     for (int r = 0; r < kMaxDelays; ++r) {
@@ -533,7 +574,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 2) classify_kernel(const __g
             locate_ml<T>(a, w.ctr, w, Y, wtab, wtab_base, 1, s_nz[i < n_nz ? i : 0], i < n_nz, G);
         }
     } else {
-        for (int i = threadIdx.x; i < n_nz; i += blockDim.x) locate_arg_thread<T>(a, w.ctr, w, Y, 1, s_nz[i]);
+        for (int i = threadIdx.x; i < n_nz; i += blockDim.x) locate_phase_thread<T>(a, w.ctr, w, Y, 1, s_nz[i]);
     }
     if (threadIdx.x == 0) {
         atomicAdd(w.ctr + kCtrResolved, s_res);
@@ -589,7 +630,7 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
             for (int i = gw; i < n_nz; i += nwarps)
                 locate_ml<T>(a, ctr, w, Y, wtab, 0, round, __ldcg(w.nzl + i), true, 32);
         } else {
-            for (int i = wt; i < n_nz; i += nw) locate_arg_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
+            for (int i = wt; i < n_nz; i += nw) locate_phase_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
         }
         if (!group_barrier(ctr, G, a.spin_limit)) break;
     }

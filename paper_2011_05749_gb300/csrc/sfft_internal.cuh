@@ -69,7 +69,7 @@ struct PlanDesc {
     int32_t D, R;
     int32_t sumB;            // bins per delay over all stages
     int64_t y_per_sig;       // R * sumB
-    int32_t locate;          // 0 ARG, 1 ML
+    int32_t locate;          // 0 ARG, 1 ML, 2 KAY
     int32_t max_rounds;
     int32_t K;
     int32_t root_total;      // sum_d L_d: root-table entries (at st[0].root_off onwards)
@@ -80,7 +80,7 @@ struct PlanDesc {
     int32_t ph_hi_off;
     uint64_t mu;             // floor((2^64 - 1) / N): Barrett reduction modulo N
     int32_t am;              // one-shot: a_m (delay slots 0 .. 3 a_m - 1 hold -a_m .. 2 a_m - 1)
-    int32_t pad1;
+    int32_t kay_m;           // KAY locate: delays per iteration (slot c m + t holds r_c + t 2^c)
     double sv_floor;         // one-shot: singular values at or below this are not counted
     double sp_tol2;          // one-shot: residual tolerance of the subspace pursuit
     StageDesc st[kMaxStages];

@@ -24,7 +24,7 @@ class Plan:
                  a_min: float = 1.0, eta: float = 0.0, c0: float = 4.0, c1: float = 2.0,
                  max_rounds: int = 64, max_batch: int = 1, max_tile: int = 0,
                  wait_limit_log2: int = 0, fault_inject: int = 0, decode_ctas: int = 0,
-                 decoder: str = "peel", a_m: int = 3):
+                 decoder: str = "peel", a_m: int = 3, kay_m: int = 2):
         lib = load()
         f = np.ascontiguousarray(f, dtype=np.int64)
         delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -32,7 +32,8 @@ class Plan:
         lib.sfft_opts_default(ctypes.byref(o))
         o.dtype = {"c64": _lib.C64, "c128": _lib.C128}[dtype]
         o.precision = {"fp32": _lib.PREC_FP32, "fp64": _lib.PREC_FP64}[precision]
-        o.locate = {"arg": _lib.LOCATE_ARG, "ml": _lib.LOCATE_ML}[locate]
+        o.locate = {"arg": _lib.LOCATE_ARG, "ml": _lib.LOCATE_ML, "kay": _lib.LOCATE_KAY}[locate]
+        o.kay_m = kay_m
         o.max_rounds = max_rounds
         o.max_batch = max_batch
         o.max_tile = max_tile
@@ -56,7 +57,7 @@ class Plan:
         self.delays = delays.copy()
         self.R = int(delays.shape[1])
         self.dtype, self.precision, self.locate = dtype, precision, locate
-        self.decoder, self.a_m = decoder, a_m
+        self.decoder, self.a_m, self.kay_m = decoder, a_m, kay_m
         self.max_batch = max_batch
         self.num_bins = int(lib.sfft_plan_num_bins(h))
 
@@ -174,7 +175,8 @@ def autotune(N: int, K: int, f, delays, xs, stream=None, **plan_kw):
     lib.sfft_opts_default(ctypes.byref(o))
     o.dtype = {"c64": _lib.C64, "c128": _lib.C128}[tmp.dtype]
     o.precision = {"fp32": _lib.PREC_FP32, "fp64": _lib.PREC_FP64}[tmp.precision]
-    o.locate = {"arg": _lib.LOCATE_ARG, "ml": _lib.LOCATE_ML}[tmp.locate]
+    o.locate = {"arg": _lib.LOCATE_ARG, "ml": _lib.LOCATE_ML, "kay": _lib.LOCATE_KAY}[tmp.locate]
+    o.kay_m = tmp.kay_m
     for k in ("noise_var", "a_min", "eta", "c0", "c1", "max_rounds"):
         if k in plan_kw:
             setattr(o, k, plan_kw[k])

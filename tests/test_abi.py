@@ -68,7 +68,7 @@ def test_opts_layout_and_defaults_without_gpu():
     _lib.load().sfft_opts_default(ct.byref(o))
     assert (o.dtype, o.precision, o.locate, o.max_rounds, o.max_batch) == (0, 1, 1, 64, 1)
     assert (o.a_min, o.c0, o.c1) == (1.0, 4.0, 2.0)
-    assert (o.decoder, o.oneshot_am, o.reserved) == (_lib.DECODER_PEEL, 3, 0)
+    assert (o.decoder, o.oneshot_am, o.kay_m, o.reserved) == (_lib.DECODER_PEEL, 3, 2, 0)
 
 
 def test_oneshot_plan_rules_checked_without_gpu():
@@ -96,3 +96,29 @@ def test_oneshot_plan_rules_checked_without_gpu():
     assert create([16], good[:13]) == inval                           # P = 4 < 2 a_m
     assert create([16], good, K=N // 16 + 1) == inval                  # K > B
     assert create([16], good, a_m=4) == inval                          # a_m > 3
+
+
+def test_kay_plan_rules_checked_without_gpu():
+    """KAY plans: slot c m + t = r_c + t 2^c (mod N) in every stage and 2^C >= L_d."""
+    import ctypes as ct
+    import numpy as np
+    import synth
+    from paper_2011_05749_gb300 import _lib
+    lib = _lib.load()
+    N, f = 124950, np.array([49, 50, 51], dtype=np.int64)
+
+    def create(delays, m=2):
+        o = _lib.Opts()
+        lib.sfft_opts_default(ct.byref(o))
+        o.locate, o.kay_m = _lib.LOCATE_KAY, m
+        d = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(3, -1))
+        h = ct.c_void_p()
+        return lib.sfft_plan_create(ct.byref(h), N, 10, 3, f.ctypes.data, d.shape[1],
+                                    d.ctypes.data, ct.byref(o))
+    inval = _lib.SFFT_EINVAL
+    good = synth.kay_delays(N, 3, 6, 2, np.random.default_rng(1))
+    bad = good.copy()
+    bad[1, 3] = (bad[1, 3] + 1) % N                                  # breaks r_c + 2^c
+    assert create(bad) == inval
+    assert create(synth.kay_delays(N, 3, 5, 2, np.random.default_rng(1))) == inval  # 2^5 < 51
+    assert create(good, m=3) == inval                                # 12 slots, m = 3: wrong structure

@@ -179,7 +179,8 @@ def test_kay_locate_every_frequency(oracle_mod):
     """KAY locate (Sec. 3.2 subproblem 2, Eq. 21-22) on structured delays r_c + t 2^c: a
     single tone at every frequency of N = 504 (L = 7, 8, 9; C = 4 iterations) is located
     exactly, for m = 2 and for m = 4 (where Eq. 22's weights must sum to one for the
-    averaged phase to land on the tone's)."""
+    averaged phase to land on the tone's).  The L = 8 stage's last iteration (2^3 = 8) is
+    the uninformative case whose bit comes from the bin index."""
     N, f = 504, (7, 8, 9)
     rng = np.random.default_rng(13)
     for m in (2, 4):
