@@ -12,4 +12,6 @@ from .oracle import (  # noqa: F401
     decode,
     OracleOpts,
     thresholds,
+    gamma_median,
+    noise_estimate,
 )

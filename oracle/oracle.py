@@ -39,14 +39,15 @@ def build_oracle(force: bool = False) -> str:
 class _Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("rounds", ctypes.c_int32),
                 ("n_recovered", ctypes.c_int32), ("n_out", ctypes.c_int32),
-                ("idents", ctypes.c_int64), ("unresolved", ctypes.c_int64)]
+                ("idents", ctypes.c_int64), ("unresolved", ctypes.c_int64),
+                ("noise_var", ctypes.c_double)]
 
 
 class _Opts(ctypes.Structure):
     _fields_ = [("noise_var", ctypes.c_double), ("a_min", ctypes.c_double),
                 ("eta", ctypes.c_double), ("c0", ctypes.c_double), ("c1", ctypes.c_double),
                 ("locate", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
-                ("kay_m", ctypes.c_int32)]
+                ("kay_m", ctypes.c_int32), ("noise_auto", ctypes.c_int32)]
 
 
 class _RoundLog(ctypes.Structure):
@@ -124,6 +125,23 @@ def bin_value(N: int, L: int, tau: int, j: int, x) -> complex:
     return complex(out[0])
 
 
+def gamma_median(R: int) -> float:
+    """Median of Gamma(R, 1), the oracle's bisection."""
+    lib = _load()
+    lib.oracle_gamma_median.restype = ctypes.c_double
+    return float(lib.oracle_gamma_median(ctypes.c_int32(R)))
+
+
+def noise_estimate(N: int, f, R: int, Y) -> float:
+    """sigma^2 from the lower median of the bin energies E / B (oracle_noise_estimate)."""
+    lib = _load()
+    lib.oracle_noise_estimate.restype = ctypes.c_double
+    f = _i64(f)
+    Y = _c128(Y)
+    return float(lib.oracle_noise_estimate(ctypes.c_int64(N), ctypes.c_int32(f.size), _ptr(f),
+                                           ctypes.c_int32(R), _ptr(Y)))
+
+
 @dataclasses.dataclass
 class OracleOpts:
     noise_var: float = 0.0
@@ -134,6 +152,7 @@ class OracleOpts:
     locate: int = 0          # 0 ARG (FFAST phase), 1 ML (candidate enumeration), 2 KAY
     max_rounds: int = 64
     kay_m: int = 2           # KAY: delays per iteration (slots c m + t hold r_c + t 2^c)
+    noise_auto: int = 0      # 1: sigma^2 from the median bin energy (noise_var unused)
 
 
 def thresholds(N: int, f, R: int, opts: OracleOpts):
@@ -167,7 +186,8 @@ def decode(N: int, f, delays, Y, K: int, opts: OracleOpts | None = None) -> dict
             for k in ("idents", "n_zero", "n_single", "n_multi", "n_accepted")}
     rl = _RoundLog(*[_ptr(logs[k]) for k in
                      ("idents", "n_zero", "n_single", "n_multi", "n_accepted")])
-    co = _Opts(opts.noise_var, opts.a_min, opts.eta, opts.c0, opts.c1, opts.locate, mr, opts.kay_m)
+    co = _Opts(opts.noise_var, opts.a_min, opts.eta, opts.c0, opts.c1, opts.locate, mr, opts.kay_m,
+               opts.noise_auto)
     st = _Stats()
     rc = _load().oracle_decode(N, D, _ptr(f), R, _ptr(delays), _ptr(Y), K, ctypes.byref(co),
                                _ptr(out_idx), _ptr(out_val), _ptr(rec_f), _ptr(rec_v),
@@ -184,5 +204,6 @@ def decode(N: int, f, delays, Y, K: int, opts: OracleOpts | None = None) -> dict
         "rounds": st.rounds,
         "idents": st.idents,
         "unresolved": st.unresolved,
+        "noise_var": st.noise_var,
         "round_log": {k: v[:n].copy() for k, v in logs.items()},
     }

@@ -194,6 +194,7 @@ typedef struct {
     int32_t locate;   /* 0 = ARG (needs delays 0 and 1 in every stage), 1 = ML, 2 = KAY */
     int32_t max_rounds;
     int32_t kay_m;    /* KAY: delays per iteration m (slots c m + t hold r_c + t 2^c) */
+    int32_t noise_auto; /* 1: estimate sigma^2 from the median bin energy (noise_var unused) */
 } oracle_opts;
 
 typedef struct {
@@ -203,6 +204,7 @@ typedef struct {
     int32_t n_out;           /* entries written to out_idx/out_val */
     int64_t idents;          /* bins classified, summed over rounds */
     int64_t unresolved;      /* bins never resolved */
+    double noise_var;        /* sigma^2 the thresholds used (estimated with noise_auto) */
 } oracle_stats;
 
 /* per round counters, filled when the caller passes arrays of max_rounds entries */
@@ -237,6 +239,60 @@ static void fit_tone(const cplx* y, int32_t R, const int64_t* tau, int64_t f, in
     }
     *v_out = v;
     *rho_out = rho;
+}
+
+/* Median of the Gamma(R, 1) distribution (the sum of R unit exponentials): the x with
+ * P(R, x) = 1 - e^{-x} sum_{k<R} x^k / k! = 1/2, by bisection.                            */
+double oracle_gamma_median(int32_t R)
+{
+    double lo = 0.0, hi = 4.0 * R + 10.0;
+    for (int it = 0; it < 200; ++it) {
+        double x = 0.5 * (lo + hi), term = 1.0, sum = 1.0;
+        for (int32_t k = 1; k < R; ++k) {
+            term *= x / k;
+            sum += term;
+        }
+        double cdf = 1.0 - exp(-x) * sum;
+        if (cdf < 0.5) lo = x; else hi = x;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static int cmp_double(const void* a, const void* b)
+{
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* Noise variance per time sample from the bins (SURVEY's "next" reading of Sec. 3.2's
+ * thresholds, which assume sigma^2 known): a bin holding only noise has R delays of
+ * CN(0, B sigma^2) values, so E / B = sum_r |Y_r|^2 / B is sigma^2 times a Gamma(R, 1)
+ * variable; with K much below sum B almost every bin is such, and sigma^2 is the lower
+ * median of E / B over all bins divided by the Gamma(R, 1) median.                       */
+double oracle_noise_estimate(int64_t N, int32_t n_stages, const int64_t* f, int32_t R,
+                             const cplx* Y)
+{
+    int64_t nb = 0;
+    for (int32_t d = 0; d < n_stages; ++d) nb += N / f[d];
+    double* e = (double*)malloc(sizeof(double) * (size_t)nb);
+    if (!e) return -1.0;
+    int64_t i = 0, off = 0;
+    for (int32_t d = 0; d < n_stages; ++d) {
+        int64_t B = N / f[d];
+        for (int64_t j = 0; j < B; ++j) {
+            double E = 0;
+            for (int32_t r = 0; r < R; ++r) {
+                cplx y = Y[off + (int64_t)r * B + j];
+                E += creal(y) * creal(y) + cimag(y) * cimag(y);
+            }
+            e[i++] = E / (double)B;
+        }
+        off += (int64_t)R * B;
+    }
+    qsort(e, (size_t)nb, sizeof(double), cmp_double);
+    double med = e[(nb - 1) / 2];
+    free(e);
+    return med / oracle_gamma_median(R);
 }
 
 /* Kay's weights of Eq. 22 for m delays per iteration: w_t, t = 0 .. m-2 */
@@ -316,13 +372,17 @@ int oracle_decode(int64_t N, int32_t n_stages, const int64_t* f, int32_t R, cons
     double* T0 = (double*)calloc((size_t)D, sizeof(double));
     double* T1 = (double*)calloc((size_t)D, sizeof(double));
     if (!B || !binbase || !yoff || !T0 || !T1) return OR_ENOMEM;
-    for (int32_t d = 0; d < D; ++d) {
+    for (int32_t d = 0; d < D; ++d)
         if (f[d] <= 0 || N % f[d] != 0) return OR_EINVAL;
+    const double noise_var = opt->noise_auto ? oracle_noise_estimate(N, D, f, R, Y) : opt->noise_var;
+    if (noise_var < 0) return OR_ENOMEM;
+    st->noise_var = noise_var;
+    for (int32_t d = 0; d < D; ++d) {
         B[d] = N / f[d];
         binbase[d + 1] = binbase[d] + B[d];
         yoff[d] = (int64_t)R * binbase[d];
         /* Sec. 3.2 subproblem 1: ||y||^2 <= T0 zero-ton, ||y - poly||^2 <= T1 single-ton */
-        double sig_y = (double)B[d] * opt->noise_var;
+        double sig_y = (double)B[d] * noise_var;
         double floor_ = opt->eta * (double)B[d] * opt->a_min;
         T0[d] = (double)R * (opt->c0 * sig_y + floor_ * floor_);
         T1[d] = (double)R * (opt->c1 * sig_y + floor_ * floor_);

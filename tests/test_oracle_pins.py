@@ -264,3 +264,38 @@ def test_zero_signal_gives_empty_output(oracle_mod):
     Y = oracle_mod.bucketize(N, f, delays, np.zeros(N, dtype=np.complex128))
     res = oracle_mod.decode(N, f, delays, Y, K=10, opts=oracle_mod.OracleOpts())
     assert res["idx"].size == 0 and res["status"] == 0 and res["rounds"] == 1
+
+
+# ------------------------------------------------------------- noise-variance estimate
+def test_gamma_median_matches_library(oracle_mod):
+    """The Gamma(R, 1) median the estimate divides by, against scipy's inverse of the
+    regularised incomplete gamma function."""
+    special = pytest.importorskip("scipy.special")
+    for R in range(1, 17):
+        assert abs(oracle_mod.gamma_median(R) - special.gammaincinv(R, 0.5)) < 1e-12
+
+
+def test_noise_estimate_on_pure_noise(oracle_mod):
+    """White noise of known sigma^2 at N = 49*50*51: every bin is a zero-ton, and the median
+    estimate is within 2 % of sigma^2 (the median of 7500 Gamma draws has a relative
+    spread near 0.6 %)."""
+    N, f, R = 124950, (49, 50, 51), 8
+    rng = np.random.default_rng(17)
+    delays = synth.draw_delays(N, 3, R, rng)
+    for var in (0.5, 3.0):
+        x = synth.awgn(N, var, rng)
+        Y = oracle_mod.bucketize(N, f, delays, x)
+        est = oracle_mod.noise_estimate(N, f, R, Y)
+        assert abs(est / var - 1.0) < 0.02, (var, est)
+
+
+def test_noise_auto_decoding_recovers_truth(oracle_mod):
+    """20 dB at N = 49*50*51 (K = 60 in 7500 bins): decoding with the estimated sigma^2
+    returns the truth's support, like decoding with the true one."""
+    p = synth.make_problem(124950, (49, 50, 51), 60, seed=23, R=8, delays="random",
+                           mag=(1.0, 10.0), snr_db=20.0)
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x)
+    res = oracle_mod.decode(p.N, p.f, p.delays, Y, K=p.K,
+                            opts=oracle_mod.OracleOpts(locate=1, noise_auto=1))
+    np.testing.assert_array_equal(res["idx"], p.support)
+    assert abs(res["noise_var"] / p.noise_var - 1.0) < 0.1, (res["noise_var"], p.noise_var)
