@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large single-signal measurement (N = 511*512*513)")
-    ap.add_argument("--only", choices=["large", "oneshot", "locate"], default=None,
+    ap.add_argument("--only", choices=["large", "oneshot", "locate", "noise"], default=None,
                     help="run only that block (a short run for profiling) and print its JSON")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip sfft_autotune and use the default schedule")
@@ -394,6 +394,41 @@ def measure_locate_modes(sfft, batch=64, steps=20, warmup=3):
     return out
 
 
+def measure_noise_auto(sfft, batch=64, steps=20, warmup=3):
+    """The R-FFAST workload (N = 127*128*129, K = 1000, 20 dB, ML locate, 8 delays) decoded
+    without a given sigma^2: each signal's sigma^2 is estimated from its bins (the lower
+    median of sum_r |Y_r|^2 / B over all bins over the median of Gamma(R, 1)) and sets T0, T1.
+    Reports signals/s, L0/L2 against the truth and the estimates over the true sigma^2."""
+    import torch
+    N, f, K = CFG["N"], CFG["f"], CFG["K"]
+    delays = plan_delays(2)
+    probs = problems(2, delays, N_DISTINCT)
+    plan = sfft.Plan(N, K, f, delays, precision="fp32", locate="ml", noise_auto=True,
+                     max_batch=batch)
+    dev = [torch.from_numpy(p.x.astype(np.complex64)).cuda() for p in probs]
+    xs = torch.stack([dev[i % len(dev)] for i in range(batch)])
+    res = plan.empty_outputs("cuda", batch)
+    for _ in range(warmup):
+        plan.execute_many(xs, res)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.execute_many(xs, res)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    idx, val, info = (t.cpu().numpy() for t in res)
+    errs = [union_errors(idx[i], val[i], int(info[i, 0]), p) for i, p in enumerate(probs)]
+    ratio = [plan.noise_var(i) / p.noise_var for i, p in enumerate(probs)]
+    plan.close()
+    return {"workload": f"{WORKLOAD} at 20 dB, sigma^2 estimated per signal (noise_auto)",
+            "signals_per_s": batch * 1e3 / ms, "ms_per_step": ms, "batch": batch,
+            "l0_vs_truth_total": int(sum(e[0] for e in errs)),
+            "rel_l2_vs_truth_max": max(e[1] for e in errs),
+            "sigma2_estimate_over_true": {"min": min(ratio), "max": max(ratio)}}
+
+
 def measure_serving(sfft, plan, signals, rate, seconds, seed):
     """Submit requests (one workload signal each) at Poisson arrival times for `seconds`,
     then drain; latency = submit to completion, as the server measures it."""
@@ -613,6 +648,11 @@ def run_gpu(args):
         locate_modes = measure_locate_modes(sfft)
     except Exception as exc:  # report, never fall back
         locate_modes = {"error": repr(exc)[:200]}
+    noise_auto = None
+    try:
+        noise_auto = measure_noise_auto(sfft)
+    except Exception as exc:  # report, never fall back
+        noise_auto = {"error": repr(exc)[:200]}
 
     large = None
     if not args.no_large:
@@ -668,6 +708,7 @@ def run_gpu(args):
         "large_signal": large,
         "oneshot": oneshot,
         "locate_ml_vs_kay": locate_modes,
+        "noise_auto": noise_auto,
         "clocks": clk,
     }
     if rank == 0:
@@ -691,6 +732,8 @@ def run_only(args):
         out = measure_large(sfft, peak, reps=max(1, args.steps))
     elif args.only == "locate":
         out = measure_locate_modes(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
+    elif args.only == "noise":
+        out = measure_noise_auto(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     else:
         out = measure_oneshot(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     print(json.dumps(out, default=float), flush=True)

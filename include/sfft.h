@@ -112,7 +112,10 @@ typedef struct {
     int32_t oneshot_am;       /* one-shot decoder: a_m, the most frequencies one bucket may
                                  hold (1..3, default 3) */
     int32_t kay_m;            /* SFFT_LOCATE_KAY: delays per iteration m >= 2 (default 2) */
-    int32_t reserved;
+    int32_t noise_auto;       /* peeling decoder: 1 = estimate sigma^2 per signal from its bins
+                                 (lower median over all bins of sum_r |Y_r|^2 / B_d, divided
+                                 by the median of Gamma(R, 1)) and set T0, T1 from it;
+                                 noise_var is then unused.  0 (default) = use noise_var */
 } sfft_opts;
 
 /* Fill *opts with the defaults above. */
@@ -138,6 +141,13 @@ void sfft_plan_destroy(sfft_plan_t plan);
 
 /* Bins per signal: sum_d B_d (so the bucketization output has n_delays times as many). */
 int64_t sfft_plan_num_bins(sfft_plan_t plan);
+
+/* noise_auto plans: the sigma^2 estimated for workspace slot `slot` (0 <= slot < max_batch;
+ * signal i of the last sfft_execute_batch group or execute call used slot i) by its last
+ * execution, in *out (host).  The thresholds of Sec. 3.2 subproblem 1 assume sigma^2 known;
+ * the estimate has no counterpart in the paper.  Waits for the device.
+ * Errors: SFFT_EINVAL (plan without noise_auto, slot out of range, null out), SFFT_ECUDA. */
+int sfft_plan_noise_var(sfft_plan_t plan, int32_t slot, double* out);
 
 /* Recover one signal.
  *   x          N complex samples of the plan's dtype

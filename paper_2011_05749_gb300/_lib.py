@@ -51,7 +51,7 @@ class Opts(ctypes.Structure):
                 ("wait_limit_log2", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
                 ("decode_ctas", ctypes.c_int32), ("decoder", ctypes.c_int32),
                 ("oneshot_am", ctypes.c_int32), ("kay_m", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("noise_auto", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -65,6 +65,7 @@ EXPORTS = {
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(Opts)]),
     "sfft_plan_destroy": (None, [ctypes.c_void_p]),
     "sfft_plan_num_bins": (ctypes.c_int64, [ctypes.c_void_p]),
+    "sfft_plan_noise_var": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "sfft_execute": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "sfft_execute_batch": (ctypes.c_int, [ctypes.c_int32] + [ctypes.c_void_p] * 6),
     "sfft_bucketize": (ctypes.c_int, [ctypes.c_void_p] * 4),

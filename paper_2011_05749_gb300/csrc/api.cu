@@ -161,6 +161,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         }
     }
     if (o.decoder != SFFT_DECODER_PEEL && o.decoder != SFFT_DECODER_ONESHOT) return SFFT_EINVAL;
+    if (o.noise_auto != 0 && (o.noise_auto != 1 || o.decoder != SFFT_DECODER_PEEL)) return SFFT_EINVAL;
     if (o.locate == SFFT_LOCATE_KAY && o.decoder == SFFT_DECODER_PEEL) {
         // structured delays: slot c m + t = r_c + t 2^c (mod N); 2^C >= L_d tells the L_d
         // candidates apart
@@ -215,6 +216,25 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     pd.mu = ~0ull / (uint64_t)N;
     pd.mode = o.decoder == SFFT_DECODER_ONESHOT ? 1 : 0;
     pd.kay_m = o.locate == SFFT_LOCATE_KAY ? o.kay_m : 0;
+    pd.noise_auto = o.noise_auto;
+    {
+        // median of Gamma(R, 1): CDF(x) = 1 - e^{-x} sum_{k<R} x^k / k! = 1/2, by Newton's
+        // method from x = R - 1/3 (the density x^{R-1} e^{-x} / (R-1)! is the derivative)
+        double x = n_delays - 1.0 / 3.0;
+        for (int it = 0; it < 50; ++it) {
+            double term = 1.0, sum = 1.0;
+            for (int k = 1; k < n_delays; ++k) {
+                term *= x / k;
+                sum += term;
+            }
+            const double cdf = 1.0 - exp(-x) * sum;
+            const double pdf = exp(-x) * term;  // x^{R-1} e^{-x} / (R-1)!
+            const double step = (cdf - 0.5) / pdf;
+            x -= step;
+            if (fabs(step) < 1e-15 * x) break;
+        }
+        pd.gmed = x;
+    }
     if (pd.mode == 1) {
         // the vote's floor: a_m times the per-delay zero-ton level of a bucket in moment
         // units, sqrt(c0 B sigma^2 + (eta B a_min)^2) / B; the pursuit's residual tolerance
@@ -268,6 +288,9 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         s.T1 = (double)n_delays * (o.c1 * sig_y + fl * fl);
         s.T0f = (float)s.T0;
         s.T1f = (float)s.T1;
+        s.T0a = (double)n_delays * o.c0 * (double)B;
+        s.T1a = (double)n_delays * o.c1 * (double)B;
+        s.Tb = (double)n_delays * fl * fl;
 
         // index maps
         const size_t base = h_nidx.size();
@@ -392,6 +415,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     const size_t o_rv = carve(p->esz * nb * mb);
     const size_t o_ctr = carve(4 * (size_t)p->ctr_stride * mb);
     const size_t o_sv = pd.mode == 1 ? carve(8 * (nb * pd.am + 1) * mb) : 0;
+    const size_t o_s2 = pd.noise_auto ? carve(8 * mb) : 0;
     p->dec_bytes = off;
     p->ctr_bytes_per_sig = 4 * (size_t)p->ctr_stride;
 
@@ -447,6 +471,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     w.rec_v = base + o_rv;
     w.ctr = (int32_t*)(base + o_ctr);
     w.sv = pd.mode == 1 ? (double*)(base + o_sv) : nullptr;
+    w.sig2 = pd.noise_auto ? (double*)(base + o_s2) : nullptr;
     p->footprint = 4 * 3 * h_nidx.size() + p->esz * tw_P.size() + ybytes * (p->need_pass2 ? 2 : 1) +
                    p->dec_bytes + 2 * sizeof(uint64_t) * (size_t)p->sort_cap * mb;
     p->decode_occ = decode_occupancy(p->prec, 512);
@@ -463,6 +488,15 @@ extern "C" void sfft_plan_destroy(sfft_plan_t p)
 }
 
 extern "C" int64_t sfft_plan_num_bins(sfft_plan_t p) { return p ? p->pd.sumB : -1; }
+
+extern "C" int sfft_plan_noise_var(sfft_plan_t p, int32_t slot, double* out)
+{
+    if (!p || !out || !p->pd.noise_auto || slot < 0 || slot >= p->max_batch || !p->ws.sig2)
+        return SFFT_EINVAL;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(out, p->ws.sig2 + slot, sizeof(double), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SFFT_OK : sfft::cuda_fail(e);
+}
 
 namespace sfft {
 
@@ -520,6 +554,7 @@ static DecodeWs ws_at(const sfft_plan_s* p, int slot0)
     w.rec_v = (unsigned char*)w.rec_v + so * p->esz;
     w.ctr += (size_t)slot0 * p->ctr_stride;
     if (w.sv) w.sv += (size_t)slot0 * ((size_t)p->pd.sumB * p->pd.am + 1);
+    if (w.sig2) w.sig2 += slot0;
     return w;
 }
 
@@ -594,7 +629,8 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
         PhaseScope ps(p, st, 1, 3);
         CK(launch_oneshot(da, p->prec, st));
     } else {
-        PhaseScope ps(p, st, 1, 2);
+        PhaseScope ps(p, st, 1, pd.noise_auto ? 4 : 2);
+        if (pd.noise_auto) CK(launch_noise_estimate(da, p->prec, st));
         CK(launch_classify(da, p->prec, st));
         CK(launch_decode(da, p->prec, threads, G > 1, st));
     }

@@ -143,7 +143,8 @@ __device__ __forceinline__ void record_candidate(int32_t* ctr, const DecodeWs& w
 template <typename T, int RT>
 __device__ void locate_ml_group(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
                                 const typename C2<T>::t* Y, const typename C2<T>::t* wtab,
-                                int32_t wtab_base, int round, int b, bool valid, int G)
+                                int32_t wtab_base, int round, int b, bool valid, int G,
+                                const Thr* thr)
 {
     using V = typename C2<T>::t;
     constexpr int RM = RT > 0 ? RT : kMaxDelays;  // delay slots the loops unroll over
@@ -243,7 +244,7 @@ __device__ void locate_ml_group(const DecodeArgs& a, int32_t* ctr, const DecodeW
             e2 += ex * ex + ey * ey;
         }
     }
-    if (below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
+    if (below(e2, thr[d].T1f, thr[d].T1)) record_candidate<T>(ctr, w, round, b, f, v);
 }
 
 // Lanes per bin for the ML search of n bins with at most Lmax candidates by nt threads:
@@ -271,7 +272,7 @@ __device__ __forceinline__ int ml_group_size(int n, int Lmax, int R, int nt)
 // bin's candidate set {j + q B}; then the least-squares value and the residual test.
 template <typename T>
 __device__ void locate_phase_thread(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
-                                  const typename C2<T>::t* Y, int round, int b)
+                                    const typename C2<T>::t* Y, int round, int b, const Thr* thr)
 {
     using V = typename C2<T>::t;
     const PlanDesc& pd = a.pd;
@@ -356,7 +357,7 @@ __device__ void locate_phase_thread(const DecodeArgs& a, int32_t* ctr, const Dec
             e2 += ex * ex + ey * ey;
         }
     }
-    if (below(e2, st.T1f, st.T1)) record_candidate<T>(ctr, w, round, b, f, v);
+    if (below(e2, thr[d].T1f, thr[d].T1)) record_candidate<T>(ctr, w, round, b, f, v);
 }
 
 __device__ __forceinline__ void atomic_sub_c(float2* p, float2 d)
@@ -447,7 +448,8 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
 
 // D1 of one bin: energy over the R delays (all loads in flight)
 template <typename T>
-__device__ __forceinline__ bool bin_is_zero(const PlanDesc& pd, const typename C2<T>::t* Y, int b)
+__device__ __forceinline__ bool bin_is_zero(const PlanDesc& pd, const typename C2<T>::t* Y, int b,
+                                            const Thr* thr)
 {
     using V = typename C2<T>::t;
     const int d = stage_of(pd, b);
@@ -461,7 +463,7 @@ __device__ __forceinline__ bool bin_is_zero(const PlanDesc& pd, const typename C
 #pragma unroll
     for (int r = 0; r < kMaxDelays; ++r)
         if (r < pd.R) E += y[r].x * y[r].x + y[r].y * y[r].y;
-    return below(E, st.T0f, st.T0);
+    return below(E, thr[d].T0f, thr[d].T0);
 }
 
 template <typename T>
@@ -489,13 +491,34 @@ __device__ __forceinline__ DecodeWs slot_ws(const DecodeArgs& a, int sig)
 template <typename T>
 __device__ __forceinline__ void locate_ml(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
                                           const typename C2<T>::t* Y, const typename C2<T>::t* wtab,
-                                          int32_t wtab_base, int round, int b, bool valid, int G)
+                                          int32_t wtab_base, int round, int b, bool valid, int G,
+                                          const Thr* thr)
 {
     switch (a.pd.R) {
-    case 6: locate_ml_group<T, 6>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G); break;
-    case 8: locate_ml_group<T, 8>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G); break;
-    case 10: locate_ml_group<T, 10>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G); break;
-    default: locate_ml_group<T, 0>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G); break;
+    case 6: locate_ml_group<T, 6>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G, thr); break;
+    case 8: locate_ml_group<T, 8>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G, thr); break;
+    case 10: locate_ml_group<T, 10>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G, thr); break;
+    default: locate_ml_group<T, 0>(a, ctr, w, Y, wtab, wtab_base, round, b, valid, G, thr); break;
+    }
+}
+
+// The stages' thresholds for signal sig into thr[0 .. D): the plan's, or from the signal's
+// estimated sigma^2 (noise_auto).  Called by one thread.
+__device__ __forceinline__ void signal_thresholds(const DecodeArgs& a, int sig, Thr* thr)
+{
+    const PlanDesc& pd = a.pd;
+    const double s2 = pd.noise_auto ? __ldcg(a.ws.sig2 + sig) : 0.0;
+    for (int d = 0; d < pd.D; ++d) {
+        const StageDesc& st = pd.st[d];
+        if (pd.noise_auto) {
+            thr[d].T0 = st.T0a * s2 + st.Tb;
+            thr[d].T1 = st.T1a * s2 + st.Tb;
+        } else {
+            thr[d].T0 = st.T0;
+            thr[d].T1 = st.T1;
+        }
+        thr[d].T0f = (float)thr[d].T0;
+        thr[d].T1f = (float)thr[d].T1;
     }
 }
 
@@ -535,9 +558,11 @@ __global__ void __launch_bounds__(kClassifyThreads, 2) classify_kernel(const __g
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
         wtab = ws;
     }
+    __shared__ Thr s_thr[kMaxStages];
     if (threadIdx.x == 0) {
         s_cnt = 0;
         s_res = 0;
+        signal_thresholds(a, sig, s_thr);
     }
     __syncthreads();
     // D1, four bins per thread in flight
@@ -547,7 +572,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 2) classify_kernel(const __g
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int bu = b + u * blockDim.x;
-            z[u] = bu < b1 ? bin_is_zero<T>(pd, Y, bu) : true;
+            z[u] = bu < b1 ? bin_is_zero<T>(pd, Y, bu, s_thr) : true;
         }
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
@@ -571,10 +596,11 @@ __global__ void __launch_bounds__(kClassifyThreads, 2) classify_kernel(const __g
         const int per = blockDim.x / G;
         for (int k = 0; k < (n_nz + per - 1) / per; ++k) {
             const int i = k * per + threadIdx.x / G;
-            locate_ml<T>(a, w.ctr, w, Y, wtab, wtab_base, 1, s_nz[i < n_nz ? i : 0], i < n_nz, G);
+            locate_ml<T>(a, w.ctr, w, Y, wtab, wtab_base, 1, s_nz[i < n_nz ? i : 0], i < n_nz, G, s_thr);
         }
     } else {
-        for (int i = threadIdx.x; i < n_nz; i += blockDim.x) locate_phase_thread<T>(a, w.ctr, w, Y, 1, s_nz[i]);
+        for (int i = threadIdx.x; i < n_nz; i += blockDim.x)
+            locate_phase_thread<T>(a, w.ctr, w, Y, 1, s_nz[i], s_thr);
     }
     if (threadIdx.x == 0) {
         atomicAdd(w.ctr + kCtrResolved, s_res);
@@ -598,6 +624,9 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
     if (a.fault == 1 && G > 1 && gi == G - 1) return;  // injected loss of a CTA (testing)
     const int wt = gi * blockDim.x + threadIdx.x;
     const int nw = G * blockDim.x;
+    __shared__ Thr s_thr[kMaxStages];
+    if (threadIdx.x == 0) signal_thresholds(a, sig, s_thr);
+    __syncthreads();
 
     int round = 1;
     while (true) {
@@ -613,7 +642,7 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
         for (int i = wt; i < n_next; i += nw) {
             const int b = __ldcg(act + i);
             __stcg(w.dirty + b, 0u);
-            if (bin_is_zero<T>(pd, Y, b)) {
+            if (bin_is_zero<T>(pd, Y, b, s_thr)) {
                 __stcg(w.state + b, (uint8_t)1);
                 atomicAdd(ctr + kCtrResolved, 1);
             } else {
@@ -628,9 +657,10 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
             const int gw = wt >> 5, nwarps = nw >> 5;
             const V* wtab = reinterpret_cast<const V*>(a.roots);
             for (int i = gw; i < n_nz; i += nwarps)
-                locate_ml<T>(a, ctr, w, Y, wtab, 0, round, __ldcg(w.nzl + i), true, 32);
+                locate_ml<T>(a, ctr, w, Y, wtab, 0, round, __ldcg(w.nzl + i), true, 32, s_thr);
         } else {
-            for (int i = wt; i < n_nz; i += nw) locate_phase_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i));
+            for (int i = wt; i < n_nz; i += nw)
+                locate_phase_thread<T>(a, ctr, w, Y, round, __ldcg(w.nzl + i), s_thr);
         }
         if (!group_barrier(ctr, G, a.spin_limit)) break;
     }
@@ -740,6 +770,89 @@ __global__ void __launch_bounds__(1024) compact_kernel(const __grid_constant__ C
     __syncthreads();
     int32_t* wctr = const_cast<int32_t*>(ctr);
     for (int i = threadIdx.x; i < a.ctr_stride; i += blockDim.x) wctr[i] = 0;
+}
+
+// Noise-variance estimate (thresholds without a given sigma^2): a bin holding only noise
+// has R delays of CN(0, B sigma^2) values, so e = sum_r |Y_r|^2 / B is sigma^2 times a
+// Gamma(R, 1) variable; sigma^2 = (lower median of e over the signal's bins) / median of
+// Gamma(R, 1).  NE1: one thread per (signal, bin) writes e (FP32) into the slot's cf array,
+// which the decode only uses later.
+template <typename T>
+__global__ void noise_energy_kernel(const __grid_constant__ DecodeArgs a)
+{
+    using V = typename C2<T>::t;
+    const PlanDesc& pd = a.pd;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)a.n_sig * pd.sumB) return;
+    const int sig = (int)(gid / pd.sumB), b = (int)(gid - (int64_t)sig * pd.sumB);
+    const V* Y = reinterpret_cast<const V*>(a.bins) + (int64_t)sig * pd.y_per_sig;
+    const int d = stage_of(pd, b);
+    const StageDesc& st = pd.st[d];
+    const V* Yb = Y + st.y_off + (b - st.bin_base);
+    T E = 0;
+    for (int r = 0; r < pd.R; ++r) {
+        const V y = __ldcg(Yb + (int64_t)r * st.B);
+        E += y.x * y.x + y.y * y.y;
+    }
+    reinterpret_cast<float*>(a.ws.cf)[(int64_t)sig * pd.sumB * 2 + b] = (float)(E / (T)st.B);
+}
+
+// NE2: one CTA per signal; the lower median (rank floor((n - 1) / 2) from the smallest) of
+// the n = sumB energies by an 8-bit radix select on their FP32 bit patterns, then sigma^2.
+__global__ void __launch_bounds__(1024) noise_median_kernel(const __grid_constant__ DecodeArgs a)
+{
+    const PlanDesc& pd = a.pd;
+    const int sig = blockIdx.x;
+    const int n = pd.sumB;
+    const uint32_t* e = reinterpret_cast<const uint32_t*>(a.ws.cf) + (int64_t)sig * n * 2;
+    __shared__ unsigned int hist[256];
+    __shared__ uint32_t s_prefix;
+    __shared__ int s_need;
+    if (threadIdx.x == 0) {
+        s_prefix = 0;
+        s_need = (n - 1) / 2 + 1;  // 1-based rank from the smallest
+    }
+    uint32_t mask = 0;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        const uint32_t prefix = s_prefix;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t u = __ldcg(e + i);
+            if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int cum = 0;
+            const int need = s_need;
+            for (int dg = 0; dg < 256; ++dg) {
+                if (cum + (int)hist[dg] >= need) {
+                    s_prefix = prefix | ((uint32_t)dg << shift);
+                    s_need = need - cum;
+                    break;
+                }
+                cum += (int)hist[dg];
+            }
+        }
+        mask |= 255u << shift;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.ws.sig2[sig] = (double)__uint_as_float(s_prefix) / pd.gmed;
+}
+
+cudaError_t launch_noise_estimate(const DecodeArgs& a, int precision, cudaStream_t st)
+{
+    if (a.n_sig == 0) return cudaSuccess;
+    const int64_t n = (int64_t)a.n_sig * a.pd.sumB;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (precision == 1)
+        noise_energy_kernel<float><<<g, 256, 0, st>>>(a);
+    else
+        noise_energy_kernel<double><<<g, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    noise_median_kernel<<<(unsigned)a.n_sig, 1024, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_classify(const DecodeArgs& a, int precision, cudaStream_t st)

@@ -59,6 +59,8 @@ cudaError_t launch_bucketize(const BucketArgs& a, int precision, int xdouble, in
                              size_t smem, cudaStream_t st);
 // round 1 of the decoder (classification of every bin) over all signals
 cudaError_t launch_classify(const DecodeArgs& a, int precision, cudaStream_t st);
+// sigma^2 per signal from the median bin energy (noise_auto plans), before classify
+cudaError_t launch_noise_estimate(const DecodeArgs& a, int precision, cudaStream_t st);
 // one-shot decoder (three kernels: singular values, vote, solve)
 cudaError_t launch_oneshot(const DecodeArgs& a, int precision, cudaStream_t st);
 // peeling rounds, G CTAs per signal (cooperative when G > 1)

@@ -62,6 +62,7 @@ struct StageDesc {
     int32_t pad2;
     double T0, T1;           // thresholds on sum_r |Y_r|^2 and on the single-tone residual
     float T0f, T1f;          // the same in FP32 (the FP32 path compares in FP32)
+    double T0a, T1a, Tb;     // T0 = T0a sigma^2 + Tb, T1 = T1a sigma^2 + Tb (estimated sigma^2)
 };
 
 struct PlanDesc {
@@ -83,6 +84,9 @@ struct PlanDesc {
     int32_t kay_m;           // KAY locate: delays per iteration (slot c m + t holds r_c + t 2^c)
     double sv_floor;         // one-shot: singular values at or below this are not counted
     double sp_tol2;          // one-shot: residual tolerance of the subspace pursuit
+    double gmed;             // median of Gamma(R, 1), for the sigma^2 estimate
+    int32_t noise_auto;      // 1: thresholds from each signal's estimated sigma^2
+    int32_t pad2;
     StageDesc st[kMaxStages];
 };
 
@@ -128,6 +132,13 @@ struct DecodeWs {
     void* rec_v;         // recovered values
     int32_t* ctr;        // counters, see Ctr
     double* sv;          // one-shot: sumB * a_m singular values, then the vote threshold
+    double* sig2;        // noise_auto: the signal's estimated sigma^2 (one per slot)
+};
+
+// the two thresholds of a stage for one signal (Sec. 3.2 subproblem 1), in both types
+struct Thr {
+    double T0, T1;
+    float T0f, T1f;
 };
 
 // counter words of a signal slot

@@ -24,7 +24,7 @@ class Plan:
                  a_min: float = 1.0, eta: float = 0.0, c0: float = 4.0, c1: float = 2.0,
                  max_rounds: int = 64, max_batch: int = 1, max_tile: int = 0,
                  wait_limit_log2: int = 0, fault_inject: int = 0, decode_ctas: int = 0,
-                 decoder: str = "peel", a_m: int = 3, kay_m: int = 2):
+                 decoder: str = "peel", a_m: int = 3, kay_m: int = 2, noise_auto: bool = False):
         lib = load()
         f = np.ascontiguousarray(f, dtype=np.int64)
         delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -34,6 +34,7 @@ class Plan:
         o.precision = {"fp32": _lib.PREC_FP32, "fp64": _lib.PREC_FP64}[precision]
         o.locate = {"arg": _lib.LOCATE_ARG, "ml": _lib.LOCATE_ML, "kay": _lib.LOCATE_KAY}[locate]
         o.kay_m = kay_m
+        o.noise_auto = 1 if noise_auto else 0
         o.max_rounds = max_rounds
         o.max_batch = max_batch
         o.max_tile = max_tile
@@ -60,6 +61,12 @@ class Plan:
         self.decoder, self.a_m, self.kay_m = decoder, a_m, kay_m
         self.max_batch = max_batch
         self.num_bins = int(lib.sfft_plan_num_bins(h))
+
+    def noise_var(self, slot: int = 0) -> float:
+        """sigma^2 estimated for workspace slot `slot` by its last execution (noise_auto)."""
+        out = ctypes.c_double()
+        check(load().sfft_plan_noise_var(self._h, slot, ctypes.byref(out)), "sfft_plan_noise_var")
+        return out.value
 
     @property
     def handle(self) -> int:

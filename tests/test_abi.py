@@ -68,7 +68,7 @@ def test_opts_layout_and_defaults_without_gpu():
     _lib.load().sfft_opts_default(ct.byref(o))
     assert (o.dtype, o.precision, o.locate, o.max_rounds, o.max_batch) == (0, 1, 1, 64, 1)
     assert (o.a_min, o.c0, o.c1) == (1.0, 4.0, 2.0)
-    assert (o.decoder, o.oneshot_am, o.kay_m, o.reserved) == (_lib.DECODER_PEEL, 3, 2, 0)
+    assert (o.decoder, o.oneshot_am, o.kay_m, o.noise_auto) == (_lib.DECODER_PEEL, 3, 2, 0)
 
 
 def test_oneshot_plan_rules_checked_without_gpu():
@@ -122,3 +122,23 @@ def test_kay_plan_rules_checked_without_gpu():
     assert create(bad) == inval
     assert create(synth.kay_delays(N, 3, 5, 2, np.random.default_rng(1))) == inval  # 2^5 < 51
     assert create(good, m=3) == inval                                # 12 slots, m = 3: wrong structure
+
+
+def test_noise_auto_rules_checked_without_gpu():
+    import ctypes as ct
+    import numpy as np
+    from paper_2011_05749_gb300 import _lib
+    lib = _lib.load()
+    N, f = 4096, np.array([16], dtype=np.int64)
+    delays = np.ascontiguousarray([[(k - 3) % N for k in range(9)] + [100, 200, 300, 400, 500, 600, 700]],
+                                  dtype=np.int64)
+
+    def create(noise_auto, decoder):
+        o = _lib.Opts()
+        lib.sfft_opts_default(ct.byref(o))
+        o.noise_auto, o.decoder = noise_auto, decoder
+        h = ct.c_void_p()
+        return lib.sfft_plan_create(ct.byref(h), N, 10, 1, f.ctypes.data, delays.shape[1],
+                                    delays.ctypes.data, ct.byref(o))
+    assert create(2, _lib.DECODER_PEEL) == _lib.SFFT_EINVAL
+    assert create(1, _lib.DECODER_ONESHOT) == _lib.SFFT_EINVAL
