@@ -299,3 +299,47 @@ def test_noise_auto_decoding_recovers_truth(oracle_mod):
                             opts=oracle_mod.OracleOpts(locate=1, noise_auto=1))
     np.testing.assert_array_equal(res["idx"], p.support)
     assert abs(res["noise_var"] / p.noise_var - 1.0) < 0.1, (res["noise_var"], p.noise_var)
+
+
+# ---------------------------------------------------------------------------- DSFFT
+def test_dsfft_paper_worked_example(oracle_mod):
+    """Sec. 3.3, Fig. 6: N = 64, tones at 1, 6, 13, 20, 59.  Starting from the root, the
+    layers hold m_d = 1, 2, 4, 5 efficient nodes; the search stops at d = 3 with one
+    frequency per node and returns the five tones."""
+    from oracle import dsfft
+    g = json.load(open(os.path.join(GOLDEN, "dsfft_n64_example.json")))
+    N = g["N"]
+    vals = np.exp(2j * np.pi * np.arange(5) / 5) * (1.0 + np.arange(5))
+    x = synth.time_signal(N, g["support"], vals)
+    res = dsfft.decode(N, 5, x, start_layer=0)
+    assert res.layer_counts == g["layer_counts"]
+    assert res.stop_layer == g["stop_layer"]
+    assert res.status == 0
+    np.testing.assert_array_equal(res.idx, g["support"])
+    np.testing.assert_allclose(res.val, vals, rtol=0, atol=1e-12)
+    Y = dsfft.layer_bins(x, N, 3)
+    nodes = np.nonzero(np.abs(Y[:8]) > 1e-9)[0].tolist()
+    assert nodes == g["efficient_nodes_of_stop_layer"]
+
+
+def test_dsfft_layer_bins_are_aliasing_sums(oracle_mod):
+    """Layer d's tau = 0 node i is B times the sum of xhat over f = i mod 2^d (Eq. 23), and
+    its tau = 1 node carries e^{2 pi i f / N} per frequency (Eq. 6)."""
+    from oracle import dsfft
+    N, K, d = 1024, 9, 5
+    p = synth.make_problem(N, (N >> d,), K, seed=41, delays=np.array([[0, 1]]), mag=(1.0, 3.0))
+    Y = dsfft.layer_bins(p.x, N, d)
+    np.testing.assert_allclose(Y, aliasing_bins(N, (N >> d,), [[0, 1]], p.support, p.values),
+                               rtol=0, atol=1e-9)
+
+
+def test_dsfft_exact_recovery(oracle_mod):
+    """N = 2^16, K = 8 exactly sparse, starting at layer ceil(log2 K): the truth."""
+    from oracle import dsfft
+    N, K = 1 << 16, 8
+    p = synth.make_problem(N, (1,), K, seed=43, delays=np.array([[0, 1]]), mag=(1.0, 10.0))
+    res = dsfft.decode(N, K, p.x, start_layer=3)
+    assert res.status == 0
+    np.testing.assert_array_equal(res.idx, p.support)
+    np.testing.assert_allclose(res.val, p.values, rtol=0, atol=1e-10)
+    assert res.layer_counts[-1] == K
