@@ -85,6 +85,13 @@ typedef struct sfft_server_s* sfft_server_t;
 #define SFFT_DECODER_ONESHOT 1  /* sFFT-DT one-shot decoder on a single stage (Sec. 3.1):
                                    Hankel singular-value count, Prony enumeration of the
                                    positions, subspace-pursuit values */
+#define SFFT_DECODER_DSFFT 2    /* DSFFT binary tree search (Sec. 3.3, Sec. 4.3): N a power of
+                                   two; layer d holds the 2^d aliasing bins of subsampling
+                                   factor N / 2^d with delays {0, 1}; the search starts at the
+                                   layer of f[0] and goes down one layer at a time until every
+                                   efficient (non-zero) node holds one frequency, which the
+                                   phase encoding of Sec. 3.2 then recovers.  Host-driven: one
+                                   device round trip per layer searched */
 
 typedef struct {
     int32_t dtype;       /* SFFT_C64 or SFFT_C128 (default C64) */
@@ -130,6 +137,12 @@ void sfft_opts_default(sfft_opts* opts);
  * With opts->decoder = SFFT_DECODER_ONESHOT (Sec. 3.1, Sec. 4.1): one stage, K <= B, and
  * the delays are the consecutive set -a_m .. 2 a_m - 1 (mod N) in slots 0 .. 3 a_m - 1
  * followed by P >= 2 a_m distinct random delays (a_m = opts->oneshot_am).
+ * With opts->decoder = SFFT_DECODER_DSFFT: N a power of two, one stage whose f[0] (a power
+ * of two) is the start layer's subsampling factor N / 2^p, delays {0, 1}; locate is ARG.
+ * The plan holds the layers from p down to the deepest whose 2^d bins one CTA can
+ * transform (2^14 in FP32, 2^13 in FP64); sfft_plan_num_bins returns that layer's 2^d.
+ * The info row of a DSFFT execution holds the layer d the search stopped at in place of
+ * the round count.
  * Host arrays; the plan copies them.  N < 2^30.  The plan owns device tables (twiddles,
  * index maps) and the workspace for opts->max_batch signals until sfft_plan_destroy.
  * Errors: SFFT_EINVAL (bad sizes, factors, delays, ARG without delays 0 and 1, KAY delays
@@ -172,7 +185,8 @@ int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const void* const* x
 
 /* Bucketization only (Eq. 6 / Eq. 19): writes the bins of one signal in natural order,
  * bins[off_d + r * B_d + j] with off_d = n_delays * sum_{d'<d} B_d', as complex of the
- * plan's arithmetic (FP32 -> C64, FP64 -> C128).  Device pointers only.                  */
+ * plan's arithmetic (FP32 -> C64, FP64 -> C128).  Device pointers only.  SFFT_EINVAL for
+ * a DSFFT plan (its layers have different sizes).                                         */
 int sfft_bucketize(sfft_plan_t plan, const void* x, void* bins, void* stream);
 
 /* Bucketization without any device allocation (no counterpart in the paper: this is a
@@ -193,7 +207,8 @@ int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t* f, int32_t
                           const void* x, void* bins, void* stream);
 
 /* Peeling decoder only, on caller-supplied bins in the layout of sfft_bucketize (read,
- * not modified).  Outputs as sfft_execute.  Device pointers only.                         */
+ * not modified).  Outputs as sfft_execute.  Device pointers only.  SFFT_EINVAL for a DSFFT
+ * plan.                                                                                   */
 int sfft_decode_bins(sfft_plan_t plan, const void* bins, int64_t* out_idx, void* out_val,
                      int32_t* out_info, void* stream);
 
@@ -220,7 +235,8 @@ int sfft_plan_profile(sfft_plan_t plan, double* ms, int64_t* launches, int64_t* 
  * the device), and retires them as their events complete.                                */
 int sfft_server_create(sfft_server_t* out, size_t hbm_budget, int32_t max_slots);
 /* Queue one request (device pointers, as sfft_execute).  The buffers must stay valid until
- * sfft_poll reports a final status.  *ticket identifies it.                               */
+ * sfft_poll reports a final status.  *ticket identifies it.  DSFFT plans (host-driven
+ * layer search) are refused with SFFT_EINVAL.                                             */
 int sfft_submit(sfft_server_t srv, sfft_plan_t plan, const void* x, int64_t* out_idx,
                 void* out_val, int32_t* out_info, uint64_t* ticket);
 /* *status = SFFT_PENDING while queued or running, else SFFT_OK once the outputs are

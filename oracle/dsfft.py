@@ -43,10 +43,14 @@ class DsfftResult:
     layer_counts: list       # m_d of every layer searched, from the start layer on
 
 
-def decode(N: int, K: int, x, start_layer: int, opts: core.OracleOpts | None = None) -> DsfftResult:
+def decode(N: int, K: int, x, start_layer: int, opts: core.OracleOpts | None = None,
+           last_layer: int | None = None) -> DsfftResult:
+    """The search from start_layer down to last_layer (default log2 N)."""
     n = N.bit_length() - 1
     if 1 << n != N:
         raise ValueError("N must be a power of two")
+    if last_layer is not None:
+        n = min(n, last_layer)
     opts = opts or core.OracleOpts()
     opts = dataclasses.replace(opts, locate=0)
     counts = []

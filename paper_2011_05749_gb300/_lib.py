@@ -29,7 +29,7 @@ SFFT_ETOOBIG = -8
 C64, C128 = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
 LOCATE_ARG, LOCATE_ML, LOCATE_KAY = 0, 1, 2
-DECODER_PEEL, DECODER_ONESHOT = 0, 1
+DECODER_PEEL, DECODER_ONESHOT, DECODER_DSFFT = 0, 1, 2
 
 
 class SfftError(RuntimeError):

@@ -160,6 +160,46 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
                 if (delays[(int64_t)d * n_delays + q] == t) return SFFT_EINVAL;
         }
     }
+    if (o.decoder == SFFT_DECODER_DSFFT) {
+        // binary tree search (Sec. 3.3): N = 2^n, start factor f[0] = N / 2^p, delays {0, 1};
+        // one single-stage ARG plan per layer d = p .. n
+        if (n_stages != 1 || (N & (N - 1)) != 0 || (f[0] & (f[0] - 1)) != 0 || n_delays != 2 ||
+            delays[0] != 0 || delays[1] != 1 || o.noise_auto != 0)
+            return SFFT_EINVAL;
+        sfft_plan_s* p = new (std::nothrow) sfft_plan_s();
+        if (!p) return SFFT_ENOMEM;
+        p->opts = o;
+        p->max_batch = o.max_batch;
+        int n = 0;
+        while ((1ll << n) < N) ++n;
+        int lp = 0;
+        while ((1ll << lp) < f[0]) ++lp;
+        p->start_layer = n - lp;
+        sfft_opts ol = o;
+        ol.decoder = SFFT_DECODER_PEEL;
+        ol.locate = SFFT_LOCATE_ARG;
+        // layers down to the deepest one the bucketization supports (a power-of-two B is one
+        // axis, so B is bounded by what one CTA's shared memory holds)
+        for (int64_t L = f[0]; L >= 1; L >>= 1) {
+            sfft_plan_t lay = nullptr;
+            const int rc = sfft_plan_create(&lay, N, K, 1, &L, 2, delays, &ol);
+            if (rc == SFFT_EINVAL && !p->layers.empty()) break;
+            if (rc) {
+                for (sfft_plan_s* q : p->layers) sfft_plan_destroy(q);
+                delete p;
+                return rc;
+            }
+            p->layers.push_back(lay);
+            p->footprint += lay->footprint;
+        }
+        p->pd = p->layers.back()->pd;  // the last layer's description (sizes, K)
+        p->prec = p->layers.back()->prec;
+        p->xdouble = p->layers.back()->xdouble;
+        p->esz = p->layers.back()->esz;
+        p->xesz = p->layers.back()->xesz;
+        *out = p;
+        return SFFT_OK;
+    }
     if (o.decoder != SFFT_DECODER_PEEL && o.decoder != SFFT_DECODER_ONESHOT) return SFFT_EINVAL;
     if (o.noise_auto != 0 && (o.noise_auto != 1 || o.decoder != SFFT_DECODER_PEEL)) return SFFT_EINVAL;
     if (o.locate == SFFT_LOCATE_KAY && o.decoder == SFFT_DECODER_PEEL) {
@@ -482,6 +522,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
 extern "C" void sfft_plan_destroy(sfft_plan_t p)
 {
     if (!p) return;
+    for (sfft_plan_s* q : p->layers) sfft_plan_destroy(q);
+    p->layers.clear();
     cudaDeviceSynchronize();
     free_plan_memory(p);
     delete p;
@@ -668,11 +710,45 @@ static bool is_host_ptr(const void* ptr)
 
 }  // namespace sfft
 
+namespace sfft {
+// DSFFT (Sec. 3.3): execute the layer plans from the start layer down until a layer's bins
+// are all resolved (every efficient node single-frequency) or the last layer; the outputs
+// are that layer's.  Reads each layer's status back to the host.
+static int dsfft_execute(sfft_plan_s* p, const void* x, int64_t* out_idx, void* out_val,
+                         int32_t* out_info, cudaStream_t st)
+{
+    const bool hf = is_host_ptr(out_info);
+    int32_t info[4] = {0, 0, 0, 0};
+    for (size_t i = 0; i < p->layers.size(); ++i) {
+        const int rc = sfft_execute(p->layers[i], x, out_idx, out_val, out_info, st);
+        if (rc) return rc;
+        if (hf) {
+            memcpy(info, out_info, sizeof(info));
+        } else {
+            CK(cudaMemcpyAsync(info, out_info, sizeof(info), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        if (info[1] == SFFT_OK || info[1] == SFFT_ETIMEDOUT || i + 1 == p->layers.size()) {
+            const int32_t d = p->start_layer + (int32_t)i;
+            if (hf) {
+                out_info[2] = d;
+            } else {
+                CK(cudaMemcpyAsync(out_info + 2, &d, sizeof(d), cudaMemcpyHostToDevice, st));
+                CK(cudaStreamSynchronize(st));
+            }
+            return SFFT_OK;
+        }
+    }
+    return SFFT_OK;
+}
+}  // namespace sfft
+
 extern "C" int sfft_execute(sfft_plan_t p, const void* x, int64_t* out_idx, void* out_val,
                             int32_t* out_info, void* stream)
 {
     if (!p || !x || !out_idx || !out_val || !out_info) return SFFT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    if (!p->layers.empty()) return dsfft_execute(p, x, out_idx, out_val, out_info, st);
     const bool hx = is_host_ptr(x), hi = is_host_ptr(out_idx), hv = is_host_ptr(out_val),
                hf = is_host_ptr(out_info);
     if (!(hx || hi || hv || hf)) return run_chunk(p, 1, x, nullptr, out_idx, out_val, nullptr, nullptr, out_info, nullptr, st);
@@ -819,6 +895,13 @@ static int execute_group_host(sfft_plan_s* p, int n, const void* const* xs, int6
 int execute_group(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
                   void* const* val, int32_t* infos, cudaStream_t st, bool host = false)
 {
+    if (!p->layers.empty()) {  // DSFFT: each signal searches its own layers
+        for (int i = 0; i < n; ++i) {
+            const int rc = sfft_execute(p, xs[i], idx[i], val[i], infos + 4 * i, st);
+            if (rc) return rc;
+        }
+        return SFFT_OK;
+    }
     return host ? execute_group_host(p, n, xs, idx, val, infos, st)
                 : execute_group_device(p, n, xs, idx, val, infos, st);
 }
@@ -981,7 +1064,7 @@ extern "C" int sfft_plan_profile(sfft_plan_t p, double* ms, int64_t* launches, i
 
 extern "C" int sfft_bucketize(sfft_plan_t p, const void* x, void* bins, void* stream)
 {
-    if (!p || !x || !bins) return SFFT_EINVAL;
+    if (!p || !x || !bins || !p->layers.empty()) return SFFT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     BucketArgs a;
     memset(&a, 0, sizeof(a));
@@ -1010,7 +1093,7 @@ extern "C" int sfft_bucketize(sfft_plan_t p, const void* x, void* bins, void* st
 extern "C" int sfft_decode_bins(sfft_plan_t p, const void* bins, int64_t* out_idx, void* out_val,
                                 int32_t* out_info, void* stream)
 {
-    if (!p || !bins || !out_idx || !out_val || !out_info) return SFFT_EINVAL;
+    if (!p || !bins || !out_idx || !out_val || !out_info || !p->layers.empty()) return SFFT_EINVAL;
     return run_chunk(p, 1, nullptr, nullptr, out_idx, out_val, nullptr, nullptr, out_info, bins,
                      (cudaStream_t)stream);
 }

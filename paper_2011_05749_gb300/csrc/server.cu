@@ -259,6 +259,7 @@ extern "C" int sfft_submit(sfft_server_t s, sfft_plan_t plan, const void* x, int
                            void* out_val, int32_t* out_info, uint64_t* ticket)
 {
     if (!s || !plan || !x || !out_idx || !out_val || !out_info || !ticket) return SFFT_EINVAL;
+    if (!plan->layers.empty()) return SFFT_EINVAL;  // DSFFT plans are host-driven, not served
     const size_t need = plan->footprint / (size_t)plan->max_batch * kGroupMax + 4096;
     if (need > s->budget) return SFFT_EADMIT;
     std::lock_guard<std::mutex> lk(s->mu);

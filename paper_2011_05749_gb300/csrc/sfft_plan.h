@@ -64,4 +64,8 @@ struct sfft_plan_s {
     double prof_ms[3] = {0, 0, 0};
     int64_t prof_launches[3] = {0, 0, 0};
     int64_t prof_calls[3] = {0, 0, 0};
+    // DSFFT plans: one single-stage plan per layer of the binary tree, from the start layer
+    // down (layer d of start_layer + i is layers[i]); the parent owns no workspace
+    std::vector<sfft_plan_s*> layers;
+    int start_layer = 0;
 };

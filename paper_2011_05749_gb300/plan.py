@@ -41,7 +41,8 @@ class Plan:
         o.wait_limit_log2 = wait_limit_log2
         o.fault_inject = fault_inject
         o.decode_ctas = decode_ctas
-        o.decoder = {"peel": _lib.DECODER_PEEL, "oneshot": _lib.DECODER_ONESHOT}[decoder]
+        o.decoder = {"peel": _lib.DECODER_PEEL, "oneshot": _lib.DECODER_ONESHOT,
+                     "dsfft": _lib.DECODER_DSFFT}[decoder]
         o.oneshot_am = a_m
         o.noise_var = noise_var
         o.a_min = a_min

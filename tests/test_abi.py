@@ -142,3 +142,26 @@ def test_noise_auto_rules_checked_without_gpu():
                                     delays.ctypes.data, ct.byref(o))
     assert create(2, _lib.DECODER_PEEL) == _lib.SFFT_EINVAL
     assert create(1, _lib.DECODER_ONESHOT) == _lib.SFFT_EINVAL
+
+
+def test_dsfft_plan_rules_checked_without_gpu():
+    """DSFFT plans: N and f[0] powers of two, one stage, delays {0, 1}."""
+    import ctypes as ct
+    import numpy as np
+    from paper_2011_05749_gb300 import _lib
+    lib = _lib.load()
+
+    def create(N, L, delays, stages=1):
+        o = _lib.Opts()
+        lib.sfft_opts_default(ct.byref(o))
+        o.decoder = _lib.DECODER_DSFFT
+        f = np.ascontiguousarray([L] * stages, dtype=np.int64)
+        d = np.ascontiguousarray(np.tile(np.asarray(delays, dtype=np.int64), (stages, 1)))
+        h = ct.c_void_p()
+        return lib.sfft_plan_create(ct.byref(h), N, 4, stages, f.ctypes.data, d.shape[1],
+                                    d.ctypes.data, ct.byref(o))
+    inval = _lib.SFFT_EINVAL
+    assert create(3000, 8, [0, 1]) == inval          # N not a power of two
+    assert create(4096, 12, [0, 1]) == inval         # f[0] not a power of two
+    assert create(4096, 8, [0, 2]) == inval          # delays not {0, 1}
+    assert create(4096, 8, [0, 1], stages=2) == inval
