@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large single-signal measurement (N = 511*512*513)")
-    ap.add_argument("--only", choices=["large", "oneshot", "locate", "noise", "dsfft"], default=None,
+    ap.add_argument("--only", choices=["large", "oneshot", "locate", "noise", "dsfft", "mix"],
+                    default=None,
                     help="run only that block (a short run for profiling) and print its JSON")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip sfft_autotune and use the default schedule")
@@ -463,6 +464,87 @@ def measure_dsfft(sfft, batch=64, steps=5, warmup=1):
             "rel_l2_vs_truth_max": max(e[1] for e in errs)}
 
 
+def measure_batched_mix(sfft, n_signals=4096, steps=3, warmup=1, plain_per_size=8):
+    """The batched configuration: n_signals complex64 signals in one sfft_execute_batch
+    call, N drawn from {9660, 124950 = 49*50*51, 2097024 = 127*128*129} (three stages, 6
+    delays: 0, 1 and 4 random), K uniform in [10, 500], SNR uniform in [10, 40] dB, |xhat|
+    ~ U[1,10].  Each signal's noise variance is estimated from its own bins (noise_auto), so
+    one plan per N serves every SNR.  The batch is ordered by N (one launch set per plan).
+    Beside it: the plain FP64 path, one signal per sfft_execute, on plain_per_size signals
+    of each N; the ratio is the batched rate over the plain rate of the same mix.
+    Inputs: 8 distinct signals per N, each stored n_signals / 24 times."""
+    import torch
+    sizes = [(9660, (20, 21, 23)), (124950, (49, 50, 51)), (2097024, (127, 128, 129))]
+    rng = np.random.default_rng(2024)
+    per = n_signals // len(sizes)
+    out = {"workload": f"{n_signals} complex64 signals, N from {{9660, 124950, 2097024}}, "
+                       "K ~ U{10..500}, SNR ~ U[10,40] dB, 6 delays (0, 1, 4 random), "
+                       "sigma^2 estimated per signal", "sizes": {}}
+    plans, xs, probs_all, plan_of = [], [], [], []
+    for N, f in sizes:
+        delays = synth.draw_delays(N, 3, 6, rng)
+        probs = []
+        for i in range(8):
+            K = int(rng.integers(10, 501))
+            snr = float(rng.uniform(10.0, 40.0))
+            probs.append(synth.make_problem(N, f, K, seed=int(rng.integers(1 << 30)),
+                                            delays=delays, mag=(1.0, 10.0), snr_db=snr))
+        plan = sfft.Plan(N, 500, f, delays, precision="fp32", locate="ml", noise_auto=True,
+                         max_batch=per)
+        dev = [torch.from_numpy(p.x.astype(np.complex64)).cuda() for p in probs]
+        for i in range(per):
+            xs.append(dev[i % 8])
+            probs_all.append(probs[i % 8])
+            plan_of.append(plan)
+        plans.append((N, f, delays, probs, plan))
+    n = len(xs)
+    idx = [torch.zeros(500, dtype=torch.int64, device="cuda") for _ in range(n)]
+    val = [torch.zeros(500, dtype=torch.complex64, device="cuda") for _ in range(n)]
+    infos = torch.zeros((n, 4), dtype=torch.int32, device="cuda")
+    for _ in range(warmup):
+        sfft.execute_batch(plan_of, xs, (idx, val, infos))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        sfft.execute_batch(plan_of, xs, (idx, val, infos))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    inf = infos.cpu().numpy()
+    k = 0
+    plain_s = 0.0
+    for N, f, delays, probs, plan in plans:
+        l0 = 0
+        for i in range(per):
+            if i < 8:
+                c = int(inf[k + i, 0])
+                l0 += union_errors(idx[k + i].cpu().numpy(), val[k + i].cpu().numpy(), c, probs[i])[0]
+        k += per
+        # plain FP64 path: one signal per call
+        p64 = sfft.Plan(N, 500, f, delays, precision="fp64", dtype="c128", locate="ml",
+                        noise_auto=True)
+        x64 = [torch.from_numpy(p.x.astype(np.complex128)).cuda() for p in probs]
+        o64 = p64.empty_outputs()
+        p64.execute(x64[0], o64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(plain_per_size):
+            p64.execute(x64[i % 8], o64)
+        torch.cuda.synchronize()
+        plain_s += (time.perf_counter() - t0) / plain_per_size
+        p64.close()
+        out["sizes"][str(N)] = {"signals": per, "l0_vs_truth_first8_total": l0,
+                                "true_K_first8": [p.K for p in probs]}
+    for *_, plan in plans:
+        plan.close()
+    batched = n * 1e3 / ms
+    plain = len(sizes) / plain_s  # signals/s over the same mix, one per call
+    out.update({"signals_per_s": batched, "ms_per_batch": ms,
+                "plain_fp64_signals_per_s": plain, "speedup_vs_plain_fp64": batched / plain})
+    return out
+
+
 def measure_serving(sfft, plan, signals, rate, seconds, seed):
     """Submit requests (one workload signal each) at Poisson arrival times for `seconds`,
     then drain; latency = submit to completion, as the server measures it."""
@@ -692,6 +774,11 @@ def run_gpu(args):
         dsfft = measure_dsfft(sfft)
     except Exception as exc:  # report, never fall back
         dsfft = {"error": repr(exc)[:200]}
+    mix = None
+    try:
+        mix = measure_batched_mix(sfft)
+    except Exception as exc:  # report, never fall back
+        mix = {"error": repr(exc)[:200]}
 
     large = None
     if not args.no_large:
@@ -749,6 +836,7 @@ def run_gpu(args):
         "locate_ml_vs_kay": locate_modes,
         "noise_auto": noise_auto,
         "dsfft": dsfft,
+        "batched_mix": mix,
         "clocks": clk,
     }
     if rank == 0:
@@ -776,6 +864,8 @@ def run_only(args):
         out = measure_noise_auto(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     elif args.only == "dsfft":
         out = measure_dsfft(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
+    elif args.only == "mix":
+        out = measure_batched_mix(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     else:
         out = measure_oneshot(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     print(json.dumps(out, default=float), flush=True)
