@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large single-signal measurement (N = 511*512*513)")
-    ap.add_argument("--only", choices=["large", "oneshot", "locate", "noise", "dsfft", "mix"],
+    ap.add_argument("--only", choices=["large", "oneshot", "locate", "noise", "dsfft", "mix",
+                                       "serve"],
                     default=None,
                     help="run only that block (a short run for profiling) and print its JSON")
     ap.add_argument("--no-autotune", action="store_true",
@@ -584,6 +585,77 @@ def measure_serving(sfft, plan, signals, rate, seconds, seed):
                         "up to 32 requests per launch group, 16 groups in flight"}
 
 
+def measure_serving_mix(sfft, rate=20000.0, seconds=1.0, seed=4):
+    """The serving configuration: Poisson arrivals (mean `rate` requests/s) of one signal
+    each, N uniform from {9660, 124950, 2097024, 16776960 = 255*256*257} (three stages, 6
+    delays), K log-uniform in [16, 4096] clamped to min_d B_d / 2, SNR uniform in [0, 40] dB
+    or exactly sparse (one in four), complex64; each signal's noise variance is estimated
+    from its bins (noise_auto), so one plan per N serves every request of that size.  The
+    server admits by an HBM budget of 120 GB.  8 distinct signals per N."""
+    import torch
+    rng = np.random.default_rng(seed)
+    sizes = [(9660, (20, 21, 23)), (124950, (49, 50, 51)), (2097024, (127, 128, 129)),
+             (16776960, (255, 256, 257))]
+    plans, sigs, outs_all = [], [], []
+    for N, f in sizes:
+        Kcap = min(4096, min(N // L for L in f) // 2)
+        delays = synth.draw_delays(N, 3, 6, rng)
+        plan = sfft.Plan(N, Kcap, f, delays, precision="fp32", locate="ml", noise_auto=True)
+        xs = []
+        for i in range(8):
+            K = int(min(Kcap, round(float(np.exp(rng.uniform(np.log(16), np.log(4096)))))))
+            snr = None if rng.random() < 0.25 else float(rng.uniform(0.0, 40.0))
+            p = synth.make_problem(N, f, K, seed=int(rng.integers(1 << 30)), delays=delays,
+                                   mag=(1.0, 10.0), snr_db=snr)
+            xs.append(torch.from_numpy(p.x.astype(np.complex64)).cuda())
+        plans.append(plan)
+        sigs.append(xs)
+    n = max(1, int(rate * seconds))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    which = rng.integers(0, len(sizes), size=n)
+    srv = sfft.Server(hbm_budget=120 << 30, max_slots=16)
+    warm = []
+    for j, plan in enumerate(plans):  # the server creates its worker workspaces on first use
+        warm += [srv.submit(plan, sigs[j][i % 8], plan.empty_outputs()) for i in range(64)]
+    srv.drain()
+    del warm
+    ring = 1024
+    outs = [[plan.empty_outputs() for _ in range(ring)] for plan in plans]
+    slot_ticket = [[0] * ring for _ in plans]
+    tickets, kinds = [], []
+    t0 = time.perf_counter()
+    for i in range(n):
+        while time.perf_counter() - t0 < arrivals[i]:
+            pass
+        j = int(which[i])
+        k = i % ring
+        if slot_ticket[j][k]:
+            while srv.poll(slot_ticket[j][k])[0] == 1:  # ring slot still in use
+                pass
+        t = srv.submit(plans[j], sigs[j][i % 8], outs[j][k])
+        slot_ticket[j][k] = t
+        tickets.append(t)
+        kinds.append(j)
+    srv.drain()
+    t1 = time.perf_counter()
+    torch.cuda.synchronize()
+    lat = np.array([srv.poll(t)[1] for t in tickets])
+    srv.close()
+    for plan in plans:
+        plan.close()
+    kinds = np.array(kinds)
+    per_n = {str(sizes[j][0]): {"requests": int(np.sum(kinds == j)),
+                               "p50_us": float(np.percentile(lat[kinds == j], 50)),
+                               "p99_us": float(np.percentile(lat[kinds == j], 99))}
+             for j in range(len(sizes)) if np.any(kinds == j)}
+    return {"offered_rate": rate, "requests": n, "completed_rate": n / (t1 - t0),
+            "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+            "per_N": per_n, "hbm_budget_gb": 120,
+            "workload": "one request per signal, N from {9660, 124950, 2097024, 16776960}, "
+                        "K log-uniform [16, 4096] (clamped), SNR U[0,40] dB or exact, "
+                        "noise variance estimated per request"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -779,6 +851,11 @@ def run_gpu(args):
         mix = measure_batched_mix(sfft)
     except Exception as exc:  # report, never fall back
         mix = {"error": repr(exc)[:200]}
+    serving_mix = None
+    try:
+        serving_mix = measure_serving_mix(sfft, args.serve_rate, args.serve_seconds)
+    except Exception as exc:  # report, never fall back
+        serving_mix = {"error": repr(exc)[:200]}
 
     large = None
     if not args.no_large:
@@ -837,6 +914,7 @@ def run_gpu(args):
         "noise_auto": noise_auto,
         "dsfft": dsfft,
         "batched_mix": mix,
+        "serving_mix": serving_mix,
         "clocks": clk,
     }
     if rank == 0:
@@ -866,6 +944,8 @@ def run_only(args):
         out = measure_dsfft(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     elif args.only == "mix":
         out = measure_batched_mix(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
+    elif args.only == "serve":
+        out = measure_serving_mix(sfft, args.serve_rate, args.serve_seconds)
     else:
         out = measure_oneshot(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     print(json.dumps(out, default=float), flush=True)
