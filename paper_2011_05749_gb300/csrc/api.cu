@@ -361,16 +361,20 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         }
         bin_base += B;
     }
-    // twiddle table: every axis (layout of axis_tw_residue), then the L roots of each stage
+    // twiddle table: every axis (layout of axis_tw_residue, or the fragment table of a
+    // tensor-core axis), then the L roots of each stage
     tw_P.assign((size_t)tw_cursor, 1);
     tw_t.assign((size_t)tw_cursor, 0);
     for (int d = 0; d < n_stages; ++d)
         for (int a = 0; a < pd.st[d].n_axes; ++a) {
             const AxisDesc& A = pd.st[d].ax[a];
-            const int cnt = axis_tw_count(A.P, A.pow2);
+            const int fp32 = p->prec == 1 ? 1 : 0;
+            const bool tc = !A.pow2 && odd_tc(A.P, fp32);
+            const int cnt = axis_tw_count(A.P, A.pow2, fp32);
             for (int i = 0; i < cnt; ++i) {
-                tw_P[(size_t)A.tw_off + i] = A.P;
-                tw_t[(size_t)A.tw_off + i] = axis_tw_residue(A.P, A.pow2, i);
+                // tensor-core axes: -P and the entry's index (fragment table)
+                tw_P[(size_t)A.tw_off + i] = tc ? -A.P : A.P;
+                tw_t[(size_t)A.tw_off + i] = tc ? i : axis_tw_residue(A.P, A.pow2, i);
             }
         }
     pd.root_total = 0;

@@ -7,8 +7,10 @@
 // power-of-two axes as in-place radix-2 decimation-in-time FFTs.  A tile of the stage
 // array lives in shared memory for a whole pass.  When B_d fits in shared memory the stage
 // is one pass straight from x to the bins; otherwise the outer axes run first (from x into
-// scratch) and the inner axes second (scratch to bins).  No tensor cores: this is not a
-// dense contraction.
+// scratch) and the inner axes second (scratch to bins).  The direct odd-axis DFTs are dense
+// contractions (a cosine and a sine matrix applied to every sub-DFT): in FP32 stages those
+// with 17 <= P <= 127 run on the tensor cores (3-term split TF32 MMAs, FP32-level accuracy),
+// the rest on the FMA pipes.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -420,6 +422,164 @@ __device__ __forceinline__ void axis_dft_odd_dispatch(typename C2<T>::t* s,
         axis_dft_odd<T, 2>(s, tw, P, LS, TS);
 }
 
+// ---- odd axes on the tensor cores (FP32 tiles) ------------------------------------------
+// After the (a_n, b_n) pre-pass the P-point DFTs of an odd axis are two real matrix products
+// over the H = (P + 1) / 2 inputs n = 0 .. (P - 1) / 2 and outputs k = 0 .. (P - 1) / 2:
+//   C[k][c] = sum_n cos(2 pi n k / P) A[n][c],   A[n] = x_0 (n = 0), a_n (n >= 1)
+//   S[k][c] = sum_n sin(2 pi n k / P) Bs[n][c],  Bs[n] = 0 (n = 0), b_n (n >= 1)
+// over the real columns c (the real and imaginary parts of every sub-DFT); then X_0 = C_0,
+// X_k = C_k - i S_k and X_{P-k} = C_k + i S_k.  Each product runs as m16n8k8 TF32 MMAs with
+// both operands split into TF32 high and low parts, keeping the three largest partial
+// products (hi hi + hi lo + lo hi), the error-corrected TF32 scheme of Ootomo and Yokota
+// (2022): the dropped terms are about 2^-20 of the product, so the result keeps FP32-level
+// accuracy.  The cosine and sine matrices come pre-split in fragment order (the axis'
+// twiddle table in global memory, see tc_twiddle_word, read through the read-only cache);
+// the data come straight from the tile in shared memory, so nothing is staged beside the
+// resident tile.
+
+__device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo)
+{
+    hi = __float_as_uint(v) & 0xffffe000u;
+    lo = __float_as_uint(v - __uint_as_float(hi)) & 0xffffe000u;
+}
+
+// d += a b for one 16 x 8 x 8 tile: a row-major (4 registers), b column-major (2), FP32 d
+__device__ __forceinline__ void mma_tf32(float* d, uint4 a, uint32_t b0, uint32_t b1)
+{
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+// WPG warps per column group of 8 sub-DFTs (an n-tile of their real parts and one of their
+// imaginary parts), each for MR of the row tiles, so each data fragment is loaded and split
+// once per warp and a thread ends up holding C and S, real and imaginary, of the same
+// sub-DFT and output row.  With one warp per group (WPG = 1) a warp overwrites only its own
+// columns and needs no block barrier until the axis is done; with two, the warps of a chunk
+// of groups all read before a barrier and overwrite after it.  Input rows 4 apart in a k-tile
+// (tc_row) put the 16 lanes of a half-warp (4 rows x 4 columns) in distinct shared-memory
+// banks when the columns are an odd number of elements apart (LS = 1, column stride P) or
+// adjacent (odd LS).
+template <int MR, int WPG>
+__device__ __noinline__ void odd_dft_tc(float2* s, const uint4* frag, int P, int LS, int TS)
+{
+    const int M = TS / P, pairs = (P - 1) >> 1;
+    const int KT = tc_ktiles(P);
+    const int NG = (M + 7) >> 3;
+    const int W = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    const int GPC = W / WPG;                 // groups per chunk
+    const int part = warp % WPG, m0 = part * MR;
+    const bool wact = warp < GPC * WPG;
+    const int g = lane >> 2, t = lane & 3;
+    const float invLS = 1.0f / (float)LS;
+    odd_prepass<float>(s, P, LS, TS);
+    for (int c0 = (WPG == 1 ? warp : 0); c0 < NG; c0 += (WPG == 1 ? W : GPC)) {
+        const int grp = WPG == 1 ? c0 : c0 + warp / WPG;
+        const bool act = wact && grp < NG;
+        float acc[MR][4][4];  // [row tile][C re, C im, S re, S im][fragment]
+#pragma unroll
+        for (int m = 0; m < MR; ++m)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[m][q][e] = 0.0f;
+        if (act) {
+            const int cc = grp * 8 + g;
+            int src = -1;
+            if (cc < M) {
+                int lo;
+                const int hi = fdivmod(cc, LS, invLS, &lo);
+                src = lo + hi * LS * P;
+            }
+            for (int kt = 0; kt < KT; ++kt) {
+                const int n0 = tc_row(kt, t), n1 = tc_row(kt, t + 4);
+                float2 a0 = {0.0f, 0.0f}, a1 = a0, b0 = a0, b1 = a0;
+                if (src >= 0) {
+                    if (n0 <= pairs) a0 = s[src + n0 * LS];
+                    if (n1 <= pairs) a1 = s[src + n1 * LS];
+                    if (n0 >= 1 && n0 <= pairs) b0 = s[src + (P - n0) * LS];
+                    if (n1 >= 1 && n1 <= pairs) b1 = s[src + (P - n1) * LS];
+                }
+                uint32_t arh[2], arl[2], aih[2], ail[2], brh[2], brl[2], bih[2], bil[2];
+                tf32_split(a0.x, arh[0], arl[0]);
+                tf32_split(a1.x, arh[1], arl[1]);
+                tf32_split(a0.y, aih[0], ail[0]);
+                tf32_split(a1.y, aih[1], ail[1]);
+                tf32_split(b0.x, brh[0], brl[0]);
+                tf32_split(b1.x, brh[1], brl[1]);
+                tf32_split(b0.y, bih[0], bil[0]);
+                tf32_split(b1.y, bih[1], bil[1]);
+                const uint4* fk = frag + ((size_t)m0 * KT + kt) * 128 + lane;
+#pragma unroll
+                for (int m = 0; m < MR; ++m) {
+                    const uint4* fm = fk + (size_t)m * KT * 128;
+                    const uint4 ch = __ldg(fm), cl = __ldg(fm + 32);
+                    const uint4 sh = __ldg(fm + 64), sl = __ldg(fm + 96);
+                    // the three partial products of the four accumulators, interleaved so
+                    // that no MMA waits on the one before it; small terms first
+                    mma_tf32(acc[m][0], cl, arh[0], arh[1]);
+                    mma_tf32(acc[m][1], cl, aih[0], aih[1]);
+                    mma_tf32(acc[m][2], sl, brh[0], brh[1]);
+                    mma_tf32(acc[m][3], sl, bih[0], bih[1]);
+                    mma_tf32(acc[m][0], ch, arl[0], arl[1]);
+                    mma_tf32(acc[m][1], ch, ail[0], ail[1]);
+                    mma_tf32(acc[m][2], sh, brl[0], brl[1]);
+                    mma_tf32(acc[m][3], sh, bil[0], bil[1]);
+                    mma_tf32(acc[m][0], ch, arh[0], arh[1]);
+                    mma_tf32(acc[m][1], ch, aih[0], aih[1]);
+                    mma_tf32(acc[m][2], sh, brh[0], brh[1]);
+                    mma_tf32(acc[m][3], sh, bih[0], bih[1]);
+                }
+            }
+        }
+        if constexpr (WPG == 1)
+            __syncwarp();
+        else
+            __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int hc = 0; hc < 2; ++hc) {
+                const int cw = grp * 8 + 2 * t + hc;
+                if (cw >= M) continue;
+                int lo;
+                const int hi = fdivmod(cw, LS, invLS, &lo);
+                const int base = lo + hi * LS * P;
+#pragma unroll
+                for (int m = 0; m < MR; ++m)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const int k = (m0 + m) * 16 + g + 8 * r, e = 2 * r + hc;
+                        if (k > pairs) continue;
+                        const float cr = acc[m][0][e], ci = acc[m][1][e];
+                        const float sr = acc[m][2][e], si = acc[m][3][e];
+                        if (k == 0) {
+                            s[base] = float2{cr, ci};
+                        } else {
+                            s[base + k * LS] = float2{cr + si, ci - sr};
+                            s[base + (P - k) * LS] = float2{cr - si, ci + sr};
+                        }
+                    }
+            }
+        }
+        if constexpr (WPG == 1) __syncwarp();
+    }
+    __syncthreads();
+}
+
+// Row tiles per warp: all of them up to three (one warp per column group); four row tiles
+// (P > 95) are split over two warps, which keeps the accumulators within the register budget.
+__device__ __forceinline__ void odd_axis_tc(float2* s, const float2* tw, int P, int LS, int TS)
+{
+    const uint4* frag = reinterpret_cast<const uint4*>(tw);
+    switch (tc_mtiles(P)) {
+        case 1: odd_dft_tc<1, 1>(s, frag, P, LS, TS); break;
+        case 2: odd_dft_tc<2, 1>(s, frag, P, LS, TS); break;
+        case 3: odd_dft_tc<3, 1>(s, frag, P, LS, TS); break;
+        default: odd_dft_tc<2, 2>(s, frag, P, LS, TS); break;
+    }
+}
+
 __device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc, int bytes)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -481,7 +641,7 @@ __global__ void __launch_bounds__(512, 1) bucketize_kernel(const __grid_constant
         const V* twg = reinterpret_cast<const V*>(a.tw);
         int off = 0;
         for (int ax = a0; ax < a1; ++ax) {
-            const int n = axis_tw_count(st.ax[ax].P, st.ax[ax].pow2);
+            const int n = axis_tw_smem(st.ax[ax].P, st.ax[ax].pow2, sizeof(T) == 4);
             for (int t = threadIdx.x; t < n; t += blockDim.x) tws[off + t] = twg[st.ax[ax].tw_off + t];
             off += (n + 1) & ~1;
         }
@@ -597,13 +757,16 @@ loaded:
             if (A.P <= 9) {
                 odd_small<T>(s, tws + off, A.P, LS, TS);
             } else {
-                if constexpr (sizeof(T) == 4)
-                    odd_axis_f32<8>(s, tws + off, A.P, LS, TS);
-                else
+                if constexpr (sizeof(T) == 4) {
+                    if (odd_tc(A.P, 1))
+                        odd_axis_tc(s, reinterpret_cast<const V*>(a.tw) + A.tw_off, A.P, LS, TS);
+                    else
+                        odd_axis_f32<8>(s, tws + off, A.P, LS, TS);
+                } else
                     axis_dft_odd_dispatch<T>(s, tws + off, A.P, LS, TS);
             }
         }
-        off += (axis_tw_count(A.P, A.pow2) + 1) & ~1;
+        off += (axis_tw_smem(A.P, A.pow2, sizeof(T) == 4) + 1) & ~1;
     }
 
     V* dst = reinterpret_cast<V*>(ps.dst_bins ? a.bins : a.scratch);
@@ -630,6 +793,13 @@ __global__ void twiddle_kernel(typename C2<T>::t* tw, const int32_t* P_of, const
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if constexpr (sizeof(T) == 4) {
+        if (P_of[i] < 0) {  // fragment table of a tensor-core odd axis: -P, entry index
+            tw[i] = typename C2<T>::t{__uint_as_float(tc_twiddle_word(-P_of[i], 2 * t_of[i])),
+                                      __uint_as_float(tc_twiddle_word(-P_of[i], 2 * t_of[i] + 1))};
+            return;
+        }
+    }
     if (P_of[i] == 0) {  // padding entry
         tw[i] = typename C2<T>::t{(T)0, (T)0};
         return;

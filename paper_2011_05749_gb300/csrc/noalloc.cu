@@ -69,12 +69,22 @@ __global__ void static_tables_kernel(const __grid_constant__ PlanDesc pd, int32_
         pbin[i] = (int32_t)(j % s.B);
     }
     if (i < n_tw) {
-        // the axis owning twiddle slot i (layout of axis_tw_residue)
+        // the axis owning twiddle slot i (layout of axis_tw_residue, or the fragment table
+        // of a tensor-core axis)
+        constexpr int fp32 = sizeof(T) == 4 ? 1 : 0;
         for (int d = 0; d < pd.D; ++d)
             for (int a = 0; a < pd.st[d].n_axes; ++a) {
                 const AxisDesc& A = pd.st[d].ax[a];
-                const int cnt = axis_tw_count(A.P, A.pow2);
+                const int cnt = axis_tw_count(A.P, A.pow2, fp32);
                 if (i >= A.tw_off && i < A.tw_off + cnt) {
+                    if constexpr (fp32) {
+                        if (!A.pow2 && odd_tc(A.P, 1)) {
+                            const int e = (int)(i - A.tw_off);
+                            tw[i] = typename C2<T>::t{__uint_as_float(tc_twiddle_word(A.P, 2 * e)),
+                                                      __uint_as_float(tc_twiddle_word(A.P, 2 * e + 1))};
+                            continue;
+                        }
+                    }
                     double sv, cv;
                     const int32_t t = axis_tw_residue(A.P, A.pow2, (int)(i - A.tw_off));
                     sincospi(2.0 * (double)t / (double)A.P, &sv, &cv);

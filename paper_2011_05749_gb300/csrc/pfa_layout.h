@@ -78,7 +78,14 @@ inline int pfa_prime_powers(int64_t B, int32_t* out, int cap)
 
 inline bool pfa_is_pow2(int32_t P) { return P > 1 && (P & (P - 1)) == 0; }
 
-inline int64_t pfa_tw_elems(int32_t P) { return pfa_even(axis_tw_count(P, pfa_is_pow2(P) ? 1 : 0)); }
+inline int64_t pfa_tw_elems(int32_t P, int fp32)
+{
+    return pfa_even(axis_tw_count(P, pfa_is_pow2(P) ? 1 : 0, fp32));
+}
+inline int64_t pfa_tw_smem(int32_t P, int fp32)
+{
+    return pfa_even(axis_tw_smem(P, pfa_is_pow2(P) ? 1 : 0, fp32));
+}
 
 struct PassPlan {
     size_t smem = 0;     // dynamic shared memory of the launch
@@ -102,8 +109,9 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
     auto fits = [&](int64_t elems, int64_t tw) {
         return (pfa_even(elems) + tw) * (int64_t)esz <= cap && (max_tile <= 0 || elems <= max_tile);
     };
+    const int fp32 = esz == 8 ? 1 : 0;
     int64_t tw_all = 0;
-    for (int i = 0; i < n; ++i) tw_all += pfa_tw_elems(Ps[i]);
+    for (int i = 0; i < n; ++i) tw_all += pfa_tw_smem(Ps[i], fp32);
     int32_t order[kMaxAxes];
     int split = n;
     for (int i = 0; i < n; ++i) order[i] = Ps[i];
@@ -115,9 +123,9 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
             for (int i = 0; i < n; ++i) {
                 if (mask >> i & 1) {
                     pi *= Ps[i];
-                    twi += pfa_tw_elems(Ps[i]);
+                    twi += pfa_tw_smem(Ps[i], fp32);
                 } else {
-                    two += pfa_tw_elems(Ps[i]);
+                    two += pfa_tw_smem(Ps[i], fp32);
                 }
             }
             const int64_t po = B / pi;
@@ -153,8 +161,8 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
         A.rur = (int32_t)(Bp % B);
         A.crt = (int32_t)((Bp * pfa_inv_mod(Bp % A.P, A.P)) % B);
         A.tw_off = *tw_cursor;
-        *tw_cursor += (int32_t)pfa_tw_elems(A.P);
-        (i < split ? tw_in : tw_out) += pfa_tw_elems(A.P);
+        *tw_cursor += (int32_t)pfa_tw_elems(A.P, fp32);
+        (i < split ? tw_in : tw_out) += pfa_tw_smem(A.P, fp32);
     }
     auto note = [&](PassPlan* l, int64_t tile, int64_t tw) {
         const size_t b = (size_t)(pfa_even(tile) + tw) * esz;

@@ -104,11 +104,71 @@ __host__ __device__ __forceinline__ int odd_row_len(int P)
     const int pairs = (P - 1) >> 1, gp = odd_group_pairs(P);
     return (pairs + gp - 1) / gp * gp;
 }
-__host__ __device__ __forceinline__ int axis_tw_count(int P, int pow2)
+// Odd axes of FP32 stages with 17 <= P <= 127 run their DFTs on the tensor cores instead
+// (two real matrix products with the cosine and sine matrices, m16n8k8 TF32 MMAs with
+// operands split into TF32 high and low parts).  Their table holds the MMAs' A fragments,
+// already split: for row tile mt (16 outputs k), k-tile kt (8 inputs n) and quarter q
+// (cos hi, cos lo, sin hi, sin lo), lane l's four fragment words sit at word
+// ((mt KT + kt) 4 + q) 128 + 4 l, as in tc_twiddle_word.
+__host__ __device__ __forceinline__ bool odd_tc(int P, int fp32)
+{
+    return fp32 && (P & 1) && P >= 17 && P <= 127;
+}
+__host__ __device__ __forceinline__ int tc_mtiles(int P) { return ((P + 1) / 2 + 15) >> 4; }
+__host__ __device__ __forceinline__ int tc_ktiles(int P) { return (((P + 1) / 2 + 31) >> 5) << 2; }
+// input row n of fragment slot i (0..7) of k-tile kt: blocks of 32 rows, every fourth row
+__host__ __device__ __forceinline__ int tc_row(int kt, int i)
+{
+    return (kt & 3) + ((kt >> 2) << 5) + (i << 2);
+}
+__host__ __device__ __forceinline__ int axis_tw_count(int P, int pow2, int fp32)
 {
     if (P <= 1) return 0;
+    if (!pow2 && odd_tc(P, fp32)) return tc_mtiles(P) * tc_ktiles(P) * 256;  // 8-byte entries
     return pow2 ? (P >> 1) : ((P - 1) >> 1) * odd_row_len(P);
 }
+// Entries of the axis' table that the bucketization copies into shared memory: the fragment
+// tables of tensor-core axes stay in global memory (read through the read-only cache), so
+// that shared memory keeps room for the L1 lines of the gather's copies in flight.
+__host__ __device__ __forceinline__ int axis_tw_smem(int P, int pow2, int fp32)
+{
+    return (!pow2 && P > 1 && odd_tc(P, fp32)) ? 0 : axis_tw_count(P, pow2, fp32);
+}
+// v = hi + lo + e with hi = v cut to TF32 (sign, exponent, 10 mantissa bits) and lo the
+// exact remainder cut to TF32 as well, so |e| < 2^-20 |v|
+__host__ __device__ __forceinline__ void tf32_split_bits(uint32_t v, uint32_t* hi, uint32_t* lo)
+{
+    union {
+        uint32_t u;
+        float f;
+    } a, b, r;
+    a.u = v;
+    b.u = v & 0xffffe000u;
+    r.f = a.f - b.f;
+    *hi = b.u;
+    *lo = r.u & 0xffffe000u;
+}
+#ifdef __CUDACC__
+// Word w of the fragment table of a tensor-core odd axis: the cosine or sine of
+// 2 pi (n k mod P) / P (FP64, rounded to FP32), for output k and input n of the fragment
+// slot, zero outside k, n <= (P - 1) / 2; its TF32 high or low part.
+__device__ __forceinline__ uint32_t tc_twiddle_word(int P, int w)
+{
+    const int KT = tc_ktiles(P), pairs = (P - 1) >> 1;
+    const int blk = w >> 7, lane = (w >> 2) & 31, c = w & 3;
+    const int q = blk & 3, tile = blk >> 2;
+    const int mt = tile / KT, kt = tile - mt * KT;
+    const int k = mt * 16 + (lane >> 2) + (c & 1) * 8;
+    const int n = tc_row(kt, (lane & 3) + (c >> 1) * 4);
+    if (k > pairs || n > pairs) return 0u;
+    double sv, cv;
+    sincospi(2.0 * (double)((n * k) % P) / (double)P, &sv, &cv);
+    const float v = (float)(q < 2 ? cv : sv);
+    uint32_t hi, lo;
+    tf32_split_bits(__float_as_uint(v), &hi, &lo);
+    return (q & 1) ? lo : hi;
+}
+#endif
 __host__ __device__ __forceinline__ int32_t axis_tw_residue(int P, int pow2, int i)
 {
     if (pow2) return i;

@@ -78,6 +78,8 @@ BUCKET_CASES = [
     (124950, (49, 50, 51), 4, "random", "fp64", "c128"),
     (96, (1,), 2, "random", "fp32", "c64"),          # one stage, B = N: the full DFT
     (2097024, (127, 128, 129), 2, "random", "fp64", "c128"),  # FP64: two-pass DFTs
+    (2097024, (127, 128, 129), 2, "random", "fp32", "c64"),   # FP32: 127- and 43-point axes
+    (551286, (81, 82, 83), 3, "random", "fp32", "c64"),       # odd axes 83, 81, 41
 ]
 
 
