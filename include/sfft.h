@@ -123,6 +123,14 @@ typedef struct {
                                  (lower median over all bins of sum_r |Y_r|^2 / B_d, divided
                                  by the median of Gamma(R, 1)) and set T0, T1 from it;
                                  noise_var is then unused.  0 (default) = use noise_var */
+    int32_t host_gather;      /* sfft_execute with a page-locked host signal (cudaHostAlloc,
+                                 or cudaHostRegister with cudaHostRegisterMapped): 1 = the
+                                 bucketization reads the samples it needs in place over the
+                                 host link, so only the cache lines holding them cross it
+                                 (about R sum_d 1/L_d x 64 / sizeof(sample) of the signal,
+                                 capped at all of it) and signals larger than device memory
+                                 can be decoded; pageable host signals are still copied.
+                                 0 (default) = copy every host signal to device memory first */
 } sfft_opts;
 
 /* Fill *opts with the defaults above. */

@@ -368,9 +368,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     for (int d = 0; d < n_stages; ++d)
         for (int a = 0; a < pd.st[d].n_axes; ++a) {
             const AxisDesc& A = pd.st[d].ax[a];
-            const int fp32 = p->prec == 1 ? 1 : 0;
-            const bool tc = !A.pow2 && odd_tc(A.P, fp32);
-            const int cnt = axis_tw_count(A.P, A.pow2, fp32);
+            const bool tc = A.tc != 0;
+            const int cnt = axis_tw_count(A.P, A.pow2, A.tc);
             for (int i = 0; i < cnt; ++i) {
                 // tensor-core axes: -P and the entry's index (fragment table)
                 tw_P[(size_t)A.tw_off + i] = tc ? -A.P : A.P;
@@ -611,7 +610,8 @@ static DecodeWs ws_at(const sfft_plan_s* p, int slot0)
 // them after reading).
 int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
               int64_t* idx0, void* val0, int64_t* const* d_idx, void* const* d_val,
-              int32_t* infos, const void* bins_in, cudaStream_t st, int slot0 = 0)
+              int32_t* infos, const void* bins_in, cudaStream_t st, int slot0 = 0,
+              bool x_sys = false)
 {
     PlanDesc& pd = p->pd;
     void* bins = (unsigned char*)p->d_bins + (size_t)slot0 * pd.y_per_sig * p->esz;
@@ -633,6 +633,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
         a.x0 = x0;
         a.scratch = scratch;
         a.bins = bins;
+        a.x_sys = x_sys ? 1 : 0;
         for (int pass = 0; pass < (p->need_pass2 ? 2 : 1); ++pass) {
             const PassDesc* src = pass == 0 ? p->pass1 : p->pass2;
             a.tile_prefix[0] = 0;
@@ -759,19 +760,32 @@ extern "C" int sfft_execute(sfft_plan_t p, const void* x, int64_t* out_idx, void
     // host buffers: stage through device memory owned by the plan
     const size_t xb = (size_t)p->pd.N * p->xesz;
     const size_t ob = align_up((size_t)p->pd.K * 8, 256) + align_up((size_t)p->pd.K * p->xesz, 256) + 256;
-    if (!p->d_x_stage) CK(cudaMalloc(&p->d_x_stage, xb));
     if (!p->d_out_stage) CK(cudaMalloc(&p->d_out_stage, ob));
     unsigned char* ostage = (unsigned char*)p->d_out_stage;
     int64_t* di = (int64_t*)ostage;
     void* dv = ostage + align_up((size_t)p->pd.K * 8, 256);
     int32_t* dinfo = (int32_t*)(ostage + ob - 256);
     const void* dx = x;
-    if (hx) {
+    bool x_sys = false;
+    if (hx && p->opts.host_gather) {
+        // page-locked host signal: the bucketization reads it in place through its
+        // device-side address; pageable memory falls through to the copy
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, x) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer) {
+            dx = at.devicePointer;
+            x_sys = true;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (hx && !x_sys) {
+        if (!p->d_x_stage) CK(cudaMalloc(&p->d_x_stage, xb));
         CK(cudaMemcpyAsync(p->d_x_stage, x, xb, cudaMemcpyHostToDevice, st));
         dx = p->d_x_stage;
     }
     int rc = run_chunk(p, 1, dx, nullptr, hi ? di : out_idx, hv ? dv : out_val, nullptr, nullptr,
-                       hf ? dinfo : out_info, nullptr, st);
+                       hf ? dinfo : out_info, nullptr, st, 0, x_sys);
     if (rc) return rc;
     if (hi) CK(cudaMemcpyAsync(out_idx, di, (size_t)p->pd.K * 8, cudaMemcpyDeviceToHost, st));
     if (hv) CK(cudaMemcpyAsync(out_val, dv, (size_t)p->pd.K * p->xesz, cudaMemcpyDeviceToHost, st));

@@ -602,9 +602,20 @@ __device__ __forceinline__ V load_sample(const void* x, int32_t i)
     return V{(decltype(V{}.x))v.x, (decltype(V{}.x))v.y};
 }
 
+// a sample of a page-locked host signal read in place (plain load, cached in L2 only)
+template <typename XS, typename V>
+__device__ __forceinline__ V load_sample_host(const void* x, int32_t i)
+{
+    using XV = typename C2<XS>::t;
+    const XV v = __ldcg(reinterpret_cast<const XV*>(x) + i);
+    return V{(decltype(V{}.x))v.x, (decltype(V{}.x))v.y};
+}
+
 // One block = one tile of one (signal, stage, delay).  Block order within a signal:
 // (stage, tile, delay), so the delays of a tile run back to back and share x's sectors.
-template <typename T, typename XS>
+// TC: the launch holds tensor-core odd axes (FP32 only).  Without them the tensor-core path
+// is compiled out, which keeps the register allocation of the other paths free of it.
+template <typename T, typename XS, bool TC>
 __global__ void __launch_bounds__(512, 1) bucketize_kernel(const __grid_constant__ BucketArgs a)
 {
     using V = typename C2<T>::t;
@@ -641,7 +652,7 @@ __global__ void __launch_bounds__(512, 1) bucketize_kernel(const __grid_constant
         const V* twg = reinterpret_cast<const V*>(a.tw);
         int off = 0;
         for (int ax = a0; ax < a1; ++ax) {
-            const int n = axis_tw_smem(st.ax[ax].P, st.ax[ax].pow2, sizeof(T) == 4);
+            const int n = axis_tw_smem(st.ax[ax].P, st.ax[ax].pow2, st.ax[ax].tc);
             for (int t = threadIdx.x; t < n; t += blockDim.x) tws[off + t] = twg[st.ax[ax].tw_off + t];
             off += (n + 1) & ~1;
         }
@@ -653,8 +664,11 @@ __global__ void __launch_bounds__(512, 1) bucketize_kernel(const __grid_constant
     const int32_t* nidx = a.nidx + st.bin_base;
     const V* scr = reinterpret_cast<const V*>(a.scratch);
 
+    // a host signal read in place takes the register loads of the general path below (no
+    // asynchronous copies from host memory)
+    const bool host_src = a.x_sys && ps.src_gather;
     if constexpr (sizeof(XS) == sizeof(T)) {
-        if (ps.src_gather && Tb == 1 && Ta == 1) {
+        if (ps.src_gather && Tb == 1 && Ta == 1 && !host_src) {
             // whole-stage tile straight from x: sample indices from the table, then
             // asynchronous 8/16-byte copies into shared memory, all in flight at once
             constexpr int U = 8;
@@ -714,26 +728,37 @@ __global__ void __launch_bounds__(512, 1) bucketize_kernel(const __grid_constant
                     }
                 }
             }
+            bool done = false;
             if constexpr (sizeof(XS) == sizeof(T)) {
-                // samples of the arithmetic type: asynchronous copies straight into shared
-                // memory (positions outside the stage are zero)
-                const V* xv = reinterpret_cast<const V*>(x);
+                if (!host_src) {
+                    // samples of the arithmetic type: asynchronous copies straight into shared
+                    // memory (positions outside the stage are zero)
+                    const V* xv = reinterpret_cast<const V*>(x);
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int e = e0 + u * blockDim.x;
-                    if (e >= TS) continue;
-                    if (pos[u] < 0)
-                        s[e] = V{0, 0};
-                    else
-                        cp_async(s + e, ps.src_gather ? xv + src[u] : scr + slot + src[u], (int)sizeof(V));
+                    for (int u = 0; u < U; ++u) {
+                        const int e = e0 + u * blockDim.x;
+                        if (e >= TS) continue;
+                        if (pos[u] < 0)
+                            s[e] = V{0, 0};
+                        else
+                            cp_async(s + e, ps.src_gather ? xv + src[u] : scr + slot + src[u], (int)sizeof(V));
+                    }
+                    done = true;
                 }
-            } else {
+            }
+            if (!done) {
                 V v[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     v[u] = V{0, 0};
-                    if (pos[u] >= 0)
-                        v[u] = ps.src_gather ? load_sample<XS, V>(x, src[u]) : __ldcg(scr + slot + src[u]);
+                    if (pos[u] >= 0) {
+                        if (!ps.src_gather)
+                            v[u] = __ldcg(scr + slot + src[u]);
+                        else if (host_src)
+                            v[u] = load_sample_host<XS, V>(x, src[u]);
+                        else
+                            v[u] = load_sample<XS, V>(x, src[u]);
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -758,7 +783,7 @@ loaded:
                 odd_small<T>(s, tws + off, A.P, LS, TS);
             } else {
                 if constexpr (sizeof(T) == 4) {
-                    if (odd_tc(A.P, 1))
+                    if (TC && A.tc)
                         odd_axis_tc(s, reinterpret_cast<const V*>(a.tw) + A.tw_off, A.P, LS, TS);
                     else
                         odd_axis_f32<8>(s, tws + off, A.P, LS, TS);
@@ -766,7 +791,7 @@ loaded:
                     axis_dft_odd_dispatch<T>(s, tws + off, A.P, LS, TS);
             }
         }
-        off += (axis_tw_smem(A.P, A.pow2, sizeof(T) == 4) + 1) & ~1;
+        off += (axis_tw_smem(A.P, A.pow2, A.tc) + 1) & ~1;
     }
 
     V* dst = reinterpret_cast<V*>(ps.dst_bins ? a.bins : a.scratch);
@@ -831,21 +856,39 @@ __global__ void bins_natural_kernel(const __grid_constant__ PlanDesc pd, const i
         dst[i] = src[nat];
 }
 
+// does any stage's pass in this launch hold a tensor-core odd axis (fragment table)
+static bool launch_has_tc(const BucketArgs& a)
+{
+    for (int d = 0; d < a.pd.D; ++d)
+        for (int ax = a.pass[d].a0; ax < a.pass[d].a1; ++ax) {
+            if (a.pd.st[d].ax[ax].tc) return true;
+        }
+    return false;
+}
+
 cudaError_t launch_bucketize(const BucketArgs& a, int precision, int xdouble, int threads,
                              size_t smem, cudaStream_t st)
 {
     const unsigned grid = (unsigned)a.n_sig * (unsigned)a.tiles_per_sig;
     if (grid == 0) return cudaSuccess;
     if (precision == 1) {
-        if (xdouble)
-            bucketize_kernel<float, double><<<grid, threads, smem, st>>>(a);
-        else
-            bucketize_kernel<float, float><<<grid, threads, smem, st>>>(a);
+        const bool tc = launch_has_tc(a);
+        if (xdouble) {
+            if (tc)
+                bucketize_kernel<float, double, true><<<grid, threads, smem, st>>>(a);
+            else
+                bucketize_kernel<float, double, false><<<grid, threads, smem, st>>>(a);
+        } else {
+            if (tc)
+                bucketize_kernel<float, float, true><<<grid, threads, smem, st>>>(a);
+            else
+                bucketize_kernel<float, float, false><<<grid, threads, smem, st>>>(a);
+        }
     } else {
         if (xdouble)
-            bucketize_kernel<double, double><<<grid, threads, smem, st>>>(a);
+            bucketize_kernel<double, double, false><<<grid, threads, smem, st>>>(a);
         else
-            bucketize_kernel<double, float><<<grid, threads, smem, st>>>(a);
+            bucketize_kernel<double, float, false><<<grid, threads, smem, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -877,18 +920,18 @@ cudaError_t launch_bins_to_natural(const PlanDesc& pd, const int32_t* pbin, cons
 
 cudaError_t set_bucketize_smem_limit(int max_smem)
 {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(bucketize_kernel<float, float>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)))
-        return e;
-    if ((e = cudaFuncSetAttribute(bucketize_kernel<float, double>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)))
-        return e;
-    if ((e = cudaFuncSetAttribute(bucketize_kernel<double, float>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)))
-        return e;
-    return cudaFuncSetAttribute(bucketize_kernel<double, double>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    const void* fns[] = {(const void*)bucketize_kernel<float, float, false>,
+                         (const void*)bucketize_kernel<float, float, true>,
+                         (const void*)bucketize_kernel<float, double, false>,
+                         (const void*)bucketize_kernel<float, double, true>,
+                         (const void*)bucketize_kernel<double, float, false>,
+                         (const void*)bucketize_kernel<double, double, false>};
+    for (const void* fn : fns) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace sfft

@@ -21,6 +21,7 @@ struct BucketArgs {
     const void* x0;          // the signal when xs == nullptr
     void* scratch;           // complex, n_sig * y_per_sig
     void* bins;              // complex, n_sig * y_per_sig
+    int32_t x_sys;           // 1: the signal is page-locked host memory read in place
 };
 
 struct DecodeArgs {

@@ -71,14 +71,13 @@ __global__ void static_tables_kernel(const __grid_constant__ PlanDesc pd, int32_
     if (i < n_tw) {
         // the axis owning twiddle slot i (layout of axis_tw_residue, or the fragment table
         // of a tensor-core axis)
-        constexpr int fp32 = sizeof(T) == 4 ? 1 : 0;
         for (int d = 0; d < pd.D; ++d)
             for (int a = 0; a < pd.st[d].n_axes; ++a) {
                 const AxisDesc& A = pd.st[d].ax[a];
-                const int cnt = axis_tw_count(A.P, A.pow2, fp32);
+                const int cnt = axis_tw_count(A.P, A.pow2, A.tc);
                 if (i >= A.tw_off && i < A.tw_off + cnt) {
-                    if constexpr (fp32) {
-                        if (!A.pow2 && odd_tc(A.P, 1)) {
+                    if constexpr (sizeof(T) == 4) {
+                        if (A.tc) {
                             const int e = (int)(i - A.tw_off);
                             tw[i] = typename C2<T>::t{__uint_as_float(tc_twiddle_word(A.P, 2 * e)),
                                                       __uint_as_float(tc_twiddle_word(A.P, 2 * e + 1))};

@@ -78,13 +78,13 @@ inline int pfa_prime_powers(int64_t B, int32_t* out, int cap)
 
 inline bool pfa_is_pow2(int32_t P) { return P > 1 && (P & (P - 1)) == 0; }
 
-inline int64_t pfa_tw_elems(int32_t P, int fp32)
+inline int64_t pfa_tw_elems(int32_t P, int tc)
 {
-    return pfa_even(axis_tw_count(P, pfa_is_pow2(P) ? 1 : 0, fp32));
+    return pfa_even(axis_tw_count(P, pfa_is_pow2(P) ? 1 : 0, tc));
 }
-inline int64_t pfa_tw_smem(int32_t P, int fp32)
+inline int64_t pfa_tw_smem(int32_t P, int tc)
 {
-    return pfa_even(axis_tw_smem(P, pfa_is_pow2(P) ? 1 : 0, fp32));
+    return pfa_even(axis_tw_smem(P, pfa_is_pow2(P) ? 1 : 0, tc));
 }
 
 struct PassPlan {
@@ -109,13 +109,17 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
     auto fits = [&](int64_t elems, int64_t tw) {
         return (pfa_even(elems) + tw) * (int64_t)esz <= cap && (max_tile <= 0 || elems <= max_tile);
     };
+    // a stage in one pass gets tensor-core odd axes (tables outside shared memory); the
+    // passes of a two-pass stage keep every axis on the FMA pipes
     const int fp32 = esz == 8 ? 1 : 0;
-    int64_t tw_all = 0;
-    for (int i = 0; i < n; ++i) tw_all += pfa_tw_smem(Ps[i], fp32);
+    auto tc_of = [&](int32_t P) { return !pfa_is_pow2(P) && odd_tc(P, fp32) ? 1 : 0; };
+    int64_t tw_one = 0;
+    for (int i = 0; i < n; ++i) tw_one += pfa_tw_smem(Ps[i], tc_of(Ps[i]));
     int32_t order[kMaxAxes];
     int split = n;
     for (int i = 0; i < n; ++i) order[i] = Ps[i];
-    if (!fits(B, tw_all)) {
+    const bool one_pass = fits(B, tw_one);
+    if (!one_pass) {
         int64_t best = -1;
         unsigned best_mask = 0;
         for (unsigned mask = 1; mask + 1 < (1u << n); ++mask) {
@@ -123,9 +127,9 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
             for (int i = 0; i < n; ++i) {
                 if (mask >> i & 1) {
                     pi *= Ps[i];
-                    twi += pfa_tw_smem(Ps[i], fp32);
+                    twi += pfa_tw_smem(Ps[i], 0);
                 } else {
-                    two += pfa_tw_smem(Ps[i], fp32);
+                    two += pfa_tw_smem(Ps[i], 0);
                 }
             }
             const int64_t po = B / pi;
@@ -160,9 +164,10 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
         const int64_t Bp = B / A.P;
         A.rur = (int32_t)(Bp % B);
         A.crt = (int32_t)((Bp * pfa_inv_mod(Bp % A.P, A.P)) % B);
+        A.tc = one_pass ? tc_of(A.P) : 0;
         A.tw_off = *tw_cursor;
-        *tw_cursor += (int32_t)pfa_tw_elems(A.P, fp32);
-        (i < split ? tw_in : tw_out) += pfa_tw_smem(A.P, fp32);
+        *tw_cursor += (int32_t)pfa_tw_elems(A.P, A.tc);
+        (i < split ? tw_in : tw_out) += pfa_tw_smem(A.P, A.tc);
     }
     auto note = [&](PassPlan* l, int64_t tile, int64_t tw) {
         const size_t b = (size_t)(pfa_even(tile) + tw) * esz;

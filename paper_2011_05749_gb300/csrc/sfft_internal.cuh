@@ -30,7 +30,7 @@ struct AxisDesc {
     int32_t rur;     // (B / P) mod B
     int32_t crt;     // CRT coefficient
     int32_t tw_off;  // offset of this axis' twiddles in the plan twiddle table
-    int32_t pad;
+    int32_t tc;      // 1: odd axis done on the tensor cores (fragment table, see odd_tc)
 };
 
 // One DFT pass over a contiguous range of axes [a0, a1) of a stage.  A tile is Tb
@@ -104,12 +104,13 @@ __host__ __device__ __forceinline__ int odd_row_len(int P)
     const int pairs = (P - 1) >> 1, gp = odd_group_pairs(P);
     return (pairs + gp - 1) / gp * gp;
 }
-// Odd axes of FP32 stages with 17 <= P <= 127 run their DFTs on the tensor cores instead
-// (two real matrix products with the cosine and sine matrices, m16n8k8 TF32 MMAs with
-// operands split into TF32 high and low parts).  Their table holds the MMAs' A fragments,
+// Odd axes with 17 <= P <= 127 of FP32 stages done in one pass (the whole stage in one
+// tile) run their DFTs on the tensor cores instead (two real matrix products with the
+// cosine and sine matrices, m16n8k8 TF32 MMAs with operands split into TF32 high and low
+// parts); the layout marks them AxisDesc::tc.  Their table holds the MMAs' A fragments,
 // already split: for row tile mt (16 outputs k), k-tile kt (8 inputs n) and quarter q
 // (cos hi, cos lo, sin hi, sin lo), lane l's four fragment words sit at word
-// ((mt KT + kt) 4 + q) 128 + 4 l, as in tc_twiddle_word.
+// ((mt KT + kt) 4 + q) 128 + 4 l, as in tc_twiddle_word.  odd_tc: whether P qualifies.
 __host__ __device__ __forceinline__ bool odd_tc(int P, int fp32)
 {
     return fp32 && (P & 1) && P >= 17 && P <= 127;
@@ -121,18 +122,19 @@ __host__ __device__ __forceinline__ int tc_row(int kt, int i)
 {
     return (kt & 3) + ((kt >> 2) << 5) + (i << 2);
 }
-__host__ __device__ __forceinline__ int axis_tw_count(int P, int pow2, int fp32)
+// entries of an axis' table; tc = AxisDesc::tc
+__host__ __device__ __forceinline__ int axis_tw_count(int P, int pow2, int tc)
 {
     if (P <= 1) return 0;
-    if (!pow2 && odd_tc(P, fp32)) return tc_mtiles(P) * tc_ktiles(P) * 256;  // 8-byte entries
+    if (tc) return tc_mtiles(P) * tc_ktiles(P) * 256;  // 8-byte entries
     return pow2 ? (P >> 1) : ((P - 1) >> 1) * odd_row_len(P);
 }
 // Entries of the axis' table that the bucketization copies into shared memory: the fragment
 // tables of tensor-core axes stay in global memory (read through the read-only cache), so
 // that shared memory keeps room for the L1 lines of the gather's copies in flight.
-__host__ __device__ __forceinline__ int axis_tw_smem(int P, int pow2, int fp32)
+__host__ __device__ __forceinline__ int axis_tw_smem(int P, int pow2, int tc)
 {
-    return (!pow2 && P > 1 && odd_tc(P, fp32)) ? 0 : axis_tw_count(P, pow2, fp32);
+    return tc ? 0 : axis_tw_count(P, pow2, 0);
 }
 // v = hi + lo + e with hi = v cut to TF32 (sign, exponent, 10 mantissa bits) and lo the
 // exact remainder cut to TF32 as well, so |e| < 2^-20 |v|

@@ -24,7 +24,8 @@ class Plan:
                  a_min: float = 1.0, eta: float = 0.0, c0: float = 4.0, c1: float = 2.0,
                  max_rounds: int = 64, max_batch: int = 1, max_tile: int = 0,
                  wait_limit_log2: int = 0, fault_inject: int = 0, decode_ctas: int = 0,
-                 decoder: str = "peel", a_m: int = 3, kay_m: int = 2, noise_auto: bool = False):
+                 decoder: str = "peel", a_m: int = 3, kay_m: int = 2, noise_auto: bool = False,
+                 host_gather: bool = False):
         lib = load()
         f = np.ascontiguousarray(f, dtype=np.int64)
         delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -35,6 +36,7 @@ class Plan:
         o.locate = {"arg": _lib.LOCATE_ARG, "ml": _lib.LOCATE_ML, "kay": _lib.LOCATE_KAY}[locate]
         o.kay_m = kay_m
         o.noise_auto = 1 if noise_auto else 0
+        o.host_gather = 1 if host_gather else 0
         o.max_rounds = max_rounds
         o.max_batch = max_batch
         o.max_tile = max_tile
