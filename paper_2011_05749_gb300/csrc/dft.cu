@@ -580,6 +580,22 @@ __device__ __forceinline__ void odd_axis_tc(float2* s, const float2* tw, int P, 
     }
 }
 
+// The tensor-core axes of a one-pass tile (run after its other axes: the axes of the
+// prime-factor map commute), then the tile's store to the bins.  Out of line, so that the
+// kernel holds nothing live across the MMA code.
+__device__ __noinline__ void tc_axes_store(float2* s, const BucketArgs& a, int d, int64_t slot,
+                                           int TS)
+{
+    const StageDesc& st = a.pd.st[d];
+    const float2* twg = reinterpret_cast<const float2*>(a.tw);
+    for (int ax = 0; ax < st.n_axes; ++ax) {
+        const AxisDesc& A = st.ax[ax];
+        if (A.tc) odd_axis_tc(s, twg + A.tw_off, A.P, A.S, TS);  // one pass: stride A.S
+    }
+    float2* dst = reinterpret_cast<float2*>(a.bins);
+    for (int e = threadIdx.x; e < TS; e += blockDim.x) __stcg(dst + slot + e, s[e]);
+}
+
 __device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc, int bytes)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -783,15 +799,21 @@ loaded:
                 odd_small<T>(s, tws + off, A.P, LS, TS);
             } else {
                 if constexpr (sizeof(T) == 4) {
-                    if (TC && A.tc)
-                        odd_axis_tc(s, reinterpret_cast<const V*>(a.tw) + A.tw_off, A.P, LS, TS);
-                    else
-                        odd_axis_f32<8>(s, tws + off, A.P, LS, TS);
+                    if (!(TC && A.tc)) odd_axis_f32<8>(s, tws + off, A.P, LS, TS);
                 } else
                     axis_dft_odd_dispatch<T>(s, tws + off, A.P, LS, TS);
             }
         }
         off += (axis_tw_smem(A.P, A.pow2, A.tc) + 1) & ~1;
+    }
+    if constexpr (TC && sizeof(T) == 4) {
+        // stages with tensor-core axes are one-pass (whole stage, straight to the bins)
+        bool has_tc = false;
+        for (int ax = a0; ax < a1; ++ax) has_tc |= st.ax[ax].tc != 0;
+        if (has_tc) {
+            tc_axes_store(reinterpret_cast<float2*>(s), a, d, slot, TS);
+            return;
+        }
     }
 
     V* dst = reinterpret_cast<V*>(ps.dst_bins ? a.bins : a.scratch);
