@@ -6,7 +6,8 @@
 // run in peel_kernel, one group of G CTAs per signal:
 //   P   every candidate frequency f not already taken (earlier round, or a lower stage in
 //       this round): recorded, and B_e v a_r(f) subtracted from bin f mod B_e of every
-//       stage e and delay r (atomics); bins that change and are still open are queued;
+//       stage e and delay r where that bin is still open (atomics; resolved bins are never
+//       read again); the bins that change are queued;
 //   D1  every queued bin: energy sum_r |Y_r|^2 against T0 -> zero-ton, else non-zero;
 //   D2  every non-zero bin: location (ARG phase or ML candidate search), least-squares
 //       value v and residual rho; rho <= T1 -> single-ton candidate (the bin is resolved).
@@ -362,8 +363,7 @@ __device__ void locate_phase_thread(const DecodeArgs& a, int32_t* ctr, const Dec
 
 __device__ __forceinline__ void atomic_sub_c(float2* p, float2 d)
 {
-    atomicAdd(&p->x, -d.x);
-    atomicAdd(&p->y, -d.y);
+    atomicAdd(p, float2{-d.x, -d.y});  // one 8-byte vector atomic (global memory, sm_90+)
 }
 __device__ __forceinline__ void atomic_sub_c(double2* p, double2 d)
 {
@@ -417,9 +417,11 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     __stcg((long long*)w.rec_f + k, (long long)f);
     reinterpret_cast<V*>(w.rec_v)[k] = v;
     const int R = pd.R;
+    // only open bins are updated: a resolved bin (zero-ton, or single-ton -- f's own bin
+    // among them) is never read again, so its value no longer matters
 #pragma unroll
     for (int e = 0; e < kMaxStages; ++e) {
-        if (e >= D) continue;
+        if (e >= D || !open[e]) continue;
         const StageDesc& se = pd.st[e];
         const T Bv = (T)se.B;
         V* Yb = Y + se.y_off + (be[e] - se.bin_base);
