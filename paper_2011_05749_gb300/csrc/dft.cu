@@ -423,8 +423,9 @@ __device__ __forceinline__ void axis_dft_odd_dispatch(typename C2<T>::t* s,
 }
 
 // ---- odd axes on the tensor cores (FP32 tiles) ------------------------------------------
-// After the (a_n, b_n) pre-pass the P-point DFTs of an odd axis are two real matrix products
-// over the H = (P + 1) / 2 inputs n = 0 .. (P - 1) / 2 and outputs k = 0 .. (P - 1) / 2:
+// With a_n = x_n + x_{P-n} and b_n = x_n - x_{P-n} the P-point DFTs of an odd axis are two
+// real matrix products over the H = (P + 1) / 2 inputs n = 0 .. (P - 1) / 2 and outputs
+// k = 0 .. (P - 1) / 2:
 //   C[k][c] = sum_n cos(2 pi n k / P) A[n][c],   A[n] = x_0 (n = 0), a_n (n >= 1)
 //   S[k][c] = sum_n sin(2 pi n k / P) Bs[n][c],  Bs[n] = 0 (n = 0), b_n (n >= 1)
 // over the real columns c (the real and imaginary parts of every sub-DFT); then X_0 = C_0,
@@ -473,7 +474,6 @@ __device__ __noinline__ void odd_dft_tc(float2* s, const uint4* frag, int P, int
     const bool wact = warp < GPC * WPG;
     const int g = lane >> 2, t = lane & 3;
     const float invLS = 1.0f / (float)LS;
-    odd_prepass<float>(s, P, LS, TS);
     for (int c0 = (WPG == 1 ? warp : 0); c0 < NG; c0 += (WPG == 1 ? W : GPC)) {
         const int grp = WPG == 1 ? c0 : c0 + warp / WPG;
         const bool act = wact && grp < NG;
@@ -493,13 +493,26 @@ __device__ __noinline__ void odd_dft_tc(float2* s, const uint4* frag, int P, int
                 src = lo + hi * LS * P;
             }
             for (int kt = 0; kt < KT; ++kt) {
+                // (a_n, b_n) = (x_n + x_{P-n}, x_n - x_{P-n}) formed as the fragments are
+                // loaded (a_0 = x_0, b_0 = 0); slot t + 4 holds a row n >= 16
                 const int n0 = tc_row(kt, t), n1 = tc_row(kt, t + 4);
                 float2 a0 = {0.0f, 0.0f}, a1 = a0, b0 = a0, b1 = a0;
                 if (src >= 0) {
-                    if (n0 <= pairs) a0 = s[src + n0 * LS];
-                    if (n1 <= pairs) a1 = s[src + n1 * LS];
-                    if (n0 >= 1 && n0 <= pairs) b0 = s[src + (P - n0) * LS];
-                    if (n1 >= 1 && n1 <= pairs) b1 = s[src + (P - n1) * LS];
+                    if (n0 <= pairs) {
+                        const float2 u = s[src + n0 * LS];
+                        if (n0 == 0) {
+                            a0 = u;
+                        } else {
+                            const float2 v = s[src + (P - n0) * LS];
+                            a0 = float2{u.x + v.x, u.y + v.y};
+                            b0 = float2{u.x - v.x, u.y - v.y};
+                        }
+                    }
+                    if (n1 <= pairs) {
+                        const float2 u = s[src + n1 * LS], v = s[src + (P - n1) * LS];
+                        a1 = float2{u.x + v.x, u.y + v.y};
+                        b1 = float2{u.x - v.x, u.y - v.y};
+                    }
                 }
                 uint32_t arh[2], arl[2], aih[2], ail[2], brh[2], brl[2], bih[2], bil[2];
                 tf32_split(a0.x, arh[0], arl[0]);
