@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large single-signal measurement (N = 511*512*513)")
     ap.add_argument("--only", choices=["large", "oneshot", "locate", "noise", "dsfft", "mix",
-                                       "serve"],
+                                       "serve", "dft"],
                     default=None,
                     help="run only that block (a short run for profiling) and print its JSON")
     ap.add_argument("--no-autotune", action="store_true",
@@ -452,6 +452,46 @@ def measure_noise_auto(sfft, batch=64, steps=20, warmup=3):
             "l0_vs_truth_total": int(sum(e[0] for e in errs)),
             "rel_l2_vs_truth_max": max(e[1] for e in errs),
             "sigma2_estimate_over_true": {"min": min(ratio), "max": max(ratio)}}
+
+
+def measure_dft_paths(sfft, batch=256, steps=20, warmup=3):
+    """The R-FFAST workload's DFTs on the two paths the library has: the default (the 43- and
+    127-point direct DFTs on the tensor cores as 3-term split TF32 products) and a
+    dft_fma_only plan (every axis on the FMA pipes).  Same signals, same schedule; reports
+    signals/s, the bucketization's ms per step and L0/L2 against the truth for each."""
+    import torch
+    N, f, K = CFG["N"], CFG["f"], CFG["K"]
+    delays = plan_delays(3)
+    probs = problems(3, delays, N_DISTINCT)
+    nv = float(np.mean([p.noise_var for p in probs]))
+    dev = [torch.from_numpy(p.x.astype(np.complex64)).cuda() for p in probs]
+    xs = torch.stack([dev[i % len(dev)] for i in range(batch)])
+    out = {"workload": f"{WORKLOAD}, batches of {batch}"}
+    for name, fma in (("tensor_core_odd_axes", False), ("fma_only", True)):
+        plan = sfft.Plan(N, K, f, delays, precision="fp32", locate="ml", noise_var=nv,
+                         max_batch=batch, dft_fma_only=fma)
+        res = plan.empty_outputs("cuda", batch)
+        for _ in range(warmup):
+            plan.execute_many(xs, res)
+        torch.cuda.synchronize()
+        plan.profile(reset=True)
+        plan.set_profiling(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.execute_many(xs, res)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = plan.profile(reset=True)
+        idx, val, info = (t.cpu().numpy() for t in res)
+        errs = [union_errors(idx[i], val[i], int(info[i, 0]), p) for i, p in enumerate(probs)]
+        plan.close()
+        out[name] = {"signals_per_s": batch * 1e3 / ms, "ms_per_step": ms,
+                     "bucketize_ms_per_step": prof["bucketize"]["ms"] / steps,
+                     "l0_vs_truth_total": int(sum(e[0] for e in errs)),
+                     "rel_l2_vs_truth_max": max(e[1] for e in errs)}
+    return out
 
 
 def measure_dsfft(sfft, batch=64, steps=5, warmup=1):
@@ -864,6 +904,11 @@ def run_gpu(args):
         noise_auto = measure_noise_auto(sfft)
     except Exception as exc:  # report, never fall back
         noise_auto = {"error": repr(exc)[:200]}
+    dft_paths = None
+    try:
+        dft_paths = measure_dft_paths(sfft)
+    except Exception as exc:  # report, never fall back
+        dft_paths = {"error": repr(exc)[:200]}
     dsfft = None
     try:
         dsfft = measure_dsfft(sfft)
@@ -935,6 +980,7 @@ def run_gpu(args):
         "oneshot": oneshot,
         "locate_ml_vs_kay": locate_modes,
         "noise_auto": noise_auto,
+        "dft_paths": dft_paths,
         "dsfft": dsfft,
         "batched_mix": mix,
         "serving_mix": serving_mix,
@@ -969,6 +1015,8 @@ def run_only(args):
         out = measure_batched_mix(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     elif args.only == "serve":
         out = measure_serving_mix(sfft, args.serve_rate, args.serve_seconds)
+    elif args.only == "dft":
+        out = measure_dft_paths(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     else:
         out = measure_oneshot(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     print(json.dumps(out, default=float), flush=True)

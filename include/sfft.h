@@ -131,6 +131,11 @@ typedef struct {
                                  capped at all of it) and signals larger than device memory
                                  can be decoded; pageable host signals are still copied.
                                  0 (default) = copy every host signal to device memory first */
+    int32_t dft_fma_only;     /* 1 = every DFT axis on the FMA pipes.  0 (default) = in FP32
+                                 stages done in one pass, the odd axes with 17 <= P <= 127 (direct
+                                 P-point DFTs: a cosine and a sine matrix applied to every
+                                 sub-DFT) run on the tensor cores as 3-term split TF32 products,
+                                 with FP32-level accuracy */
 } sfft_opts;
 
 /* Fill *opts with the defaults above. */

@@ -51,7 +51,8 @@ class Opts(ctypes.Structure):
                 ("wait_limit_log2", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
                 ("decode_ctas", ctypes.c_int32), ("decoder", ctypes.c_int32),
                 ("oneshot_am", ctypes.c_int32), ("kay_m", ctypes.c_int32),
-                ("noise_auto", ctypes.c_int32), ("host_gather", ctypes.c_int32)]
+                ("noise_auto", ctypes.c_int32), ("host_gather", ctypes.c_int32),
+                ("dft_fma_only", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

@@ -298,7 +298,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         s.B = (int32_t)B;
         s.L = (int32_t)L;
         if (!pfa_layout_stage(&s, p->esz, di.max_smem, tile_target, &p->pass1[d], &p->pass2[d],
-                              &l1, &l2, &tw_cursor, &p->need_pass2, o.max_tile)) {
+                              &l1, &l2, &tw_cursor, &p->need_pass2, o.max_tile,
+                              o.dft_fma_only == 0)) {
             free_plan_memory(p);
             delete p;
             return SFFT_EINVAL;

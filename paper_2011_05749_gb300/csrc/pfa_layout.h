@@ -94,10 +94,12 @@ struct PassPlan {
 
 // Lay out stage s (B and L already set).  esz: bytes per complex element; max_smem: the
 // device's opt-in shared memory per block.  *tw_cursor advances past this stage's
-// twiddles.  Returns false when an axis is not supported or no split fits.
+// twiddles.  allow_tc = false keeps every odd axis on the FMA pipes.  Returns false when an
+// axis is not supported or no split fits.
 inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t tile_target,
                              PassDesc* p1, PassDesc* p2, PassPlan* l1, PassPlan* l2,
-                             int32_t* tw_cursor, bool* two_pass, int64_t max_tile = 0)
+                             int32_t* tw_cursor, bool* two_pass, int64_t max_tile = 0,
+                             bool allow_tc = true)
 {
     const int64_t B = s->B;
     int32_t Ps[kMaxAxes];
@@ -112,7 +114,7 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
     // a stage in one pass gets tensor-core odd axes (tables outside shared memory); the
     // passes of a two-pass stage keep every axis on the FMA pipes
     const int fp32 = esz == 8 ? 1 : 0;
-    auto tc_of = [&](int32_t P) { return !pfa_is_pow2(P) && odd_tc(P, fp32) ? 1 : 0; };
+    auto tc_of = [&](int32_t P) { return allow_tc && !pfa_is_pow2(P) && odd_tc(P, fp32) ? 1 : 0; };
     int64_t tw_one = 0;
     for (int i = 0; i < n; ++i) tw_one += pfa_tw_smem(Ps[i], tc_of(Ps[i]));
     int32_t order[kMaxAxes];

@@ -99,6 +99,23 @@ def test_bucketize_matches_oracle(sfft, oracle_mod, case):
         assert rel_l2(g, r) <= TOL[prec], rel_l2(g, r)
 
 
+@pytest.mark.parametrize("N,f,R", [(2097024, (127, 128, 129), 2), (551286, (81, 82, 83), 3)])
+def test_bucketize_fma_only_matches_oracle(sfft, oracle_mod, N, f, R):
+    """dft_fma_only plans keep every odd axis on the FMA pipes (no tensor-core axes): the
+    bins still match the oracle within the FP32 tolerance, and decoding gives the default
+    plan's support."""
+    rng = np.random.default_rng(N + 7 * R)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    delays = synth.draw_delays(N, len(f), R, rng)
+    xd = x.astype(np.complex64)
+    Y = oracle_mod.bucketize(N, f, delays, xd.astype(np.complex128))
+    plan = sfft.Plan(N, 4, f, delays, precision="fp32", dft_fma_only=True)
+    bins = plan.bucketize(to_dev(xd, np.complex64)).cpu().numpy()
+    plan.close()
+    for g, r in zip(split_bins(bins, N, f, R), split_bins(Y, N, f, R)):
+        assert rel_l2(g, r) <= TOL["fp32"], rel_l2(g, r)
+
+
 @pytest.mark.parametrize("N,f", [(16776960, (255, 256, 257)), (134217216, (511, 512, 513))])
 def test_bucketize_large_sampled(sfft, oracle_mod, N, f):
     """Two-pass stages (B up to 262656, factors 257 / 2^9 * 3^3 * 19): sampled bins against
