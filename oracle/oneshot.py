@@ -15,9 +15,17 @@ Per bucket, in the paper's order:
   Step 1  singular values of the a_m x a_m Hankel matrix M_{a_m} = [m_{r+c}] (Eq. 10-11);
           all B a_m of them vote: the K largest (above a noise floor) give each bucket its
           count a of significant frequencies.
-  Step 2  (enumeration, method 2) C = M_a^{-1} M_s (Eq. 13-14), P(z) = z^a + sum c_t z^t
-          (Eq. 12) evaluated at every candidate z = e^{2 pi i (i + q B) / N}, q < L; the a
-          smallest |P(z)| give the positions.
+  Step 2  the a positions, by one of the paper's three methods:
+          method 1 (polynomial): C = M_a^{-1} M_s (Eq. 13-14); the a roots of
+            P(z) = z^a + sum c_t z^t (Eq. 12) are the z_j;
+          method 2 (enumeration, the default): P(z) evaluated at every candidate
+            z = e^{2 pi i (i + q B) / N}, q < L; the a smallest |P(z)| give the positions;
+          method 3 (matrix pencil): the generalized eigenvalues of Y_2 - lambda Y_1
+            (Eq. 15-17), computed as the eigenvalues of Y_1^+ Y_2 (the rank-a case of
+            Theorem 3).  By the Vandermonde factors of Theorem 3's proof they are
+            conj(z_j) = 1 / z_j, so z_j = 1 / lambda_j.
+          Methods 1 and 3 give points z; each becomes a position by its angle, snapped to
+          the nearest candidate i + q B (snap_positions).
   Step 3  values by subspace pursuit on Eq. 18 with the P random-delay measurements: the
           dictionary holds, for each position f, the atoms f, f + B and f - B; each pass
           adds the a atoms most correlated with the residual, fits the union by least
@@ -27,7 +35,9 @@ Readings where the paper is silent (also listed in the design notes): the vote k
 K largest singular values that exceed sigma_floor = a_m sqrt(c0 B sigma^2 + (eta B a_min)^2)
 / B (the per-delay zero-ton level of a bucket, in moment units, times the largest singular
 value a single tone of that level gives); ties at the K-th value all pass; the residual
-tolerance of Step 3 is P (c1 sigma^2 / B + (eta a_min)^2); at most 8 passes.
+tolerance of Step 3 is P (c1 sigma^2 / B + (eta a_min)^2); at most 8 passes.  Methods 1 and
+3 snap the roots most confident first (smallest distance to a candidate); a root whose
+candidate is taken moves to the nearest free one, on its own side first.
 
 Parity pins (tests/test_oracle_pins.py): the Hankel identity of Eq. 11 on exact bins, the
 closed-form singular values of a one-tone bucket, the quadratic roots of P(z) for a two-tone
@@ -50,6 +60,7 @@ class OneShotOpts:
     c0: float = 4.0
     c1: float = 2.0
     max_iter: int = 8
+    method: int = 2      # Step 2: 1 polynomial roots, 2 enumeration, 3 matrix pencil
 
 
 def check_delays(N: int, a_m: int, delays) -> None:
@@ -126,6 +137,50 @@ def enumerate_positions(N: int, B: int, i: int, c: np.ndarray) -> np.ndarray:
     return np.sort(f[order[:c.size]])
 
 
+def polynomial_roots(c: np.ndarray) -> np.ndarray:
+    """Step 2, method 1: the a roots of P(z) = z^a + c_{a-1} z^{a-1} + ... + c_0 (Eq. 12)."""
+    return np.roots(np.concatenate(([1.0 + 0j], c[::-1])))
+
+
+def pencil(m_row: np.ndarray, a_m: int, a: int):
+    """Y_1 and Y_2 of Eq. 16-17, (a + 1) x a: Y_1[r][c] = m_{r-c}, Y_2[r][c] = m_{r-c-1};
+    m_row is indexed k + a_m."""
+    Y1 = np.array([[m_row[r - c + a_m] for c in range(a)] for r in range(a + 1)])
+    Y2 = np.array([[m_row[r - c - 1 + a_m] for c in range(a)] for r in range(a + 1)])
+    return Y1, Y2
+
+
+def pencil_points(m_row: np.ndarray, a_m: int, a: int) -> np.ndarray:
+    """Step 2, method 3: the eigenvalues lambda_j of Y_1^+ Y_2 (Theorem 3, rank a) are
+    1 / z_j; returns the z_j."""
+    Y1, Y2 = pencil(m_row, a_m, a)
+    lam = np.linalg.eigvals(np.linalg.pinv(Y1) @ Y2)
+    lam = np.where(lam == 0, 1.0 + 0j, lam)  # a zero eigenvalue carries no angle: take z = 1
+    return 1.0 / lam
+
+
+def snap_positions(N: int, B: int, i: int, z: np.ndarray) -> np.ndarray:
+    """Positions of the points z (methods 1 and 3): u = ((arg z) N / (2 pi) - i) / B mod L
+    is the fractional candidate index; the points take candidates in order of increasing
+    |u - round(u)|, each the nearest q not yet taken (round(u), then alternately one step
+    further on u's side and on the other side).  Returns the positions ascending."""
+    L = N // B
+    u = ((np.angle(z) * N / (2 * np.pi) - i) / B) % L
+    q0 = np.floor(u + 0.5)
+    err = np.abs(u - q0)
+    taken = []
+    for t in np.argsort(err, kind="stable"):
+        side = 1 if u[t] >= q0[t] else -1
+        q = int(q0[t]) % L
+        k = 0
+        while q in taken:
+            k += 1
+            step = (k + 1) // 2 * (side if k % 2 == 1 else -side)
+            q = (int(q0[t]) + step) % L
+        taken.append(q)
+    return np.sort(i + B * np.array(taken, dtype=np.int64))
+
+
 def atoms(N: int, freqs, taus) -> np.ndarray:
     """Columns e^{2 pi i (f tau mod N) / N} over the measurement delays (Eq. 18)."""
     taus = np.asarray(taus, dtype=np.int64)
@@ -174,7 +229,7 @@ class OneShotResult:
     idx: np.ndarray
     val: np.ndarray
     counts: np.ndarray   # a_i per bucket (Step 1)
-    status: int          # 0, or 2 when a voted bucket's Eq. 14 was singular
+    status: int          # 0, or 2 when a voted bucket's Eq. 14 was singular (methods 1, 2)
     n_recovered: int
 
 
@@ -195,12 +250,18 @@ def decode(N: int, B: int, K: int, delays, Y: np.ndarray, opts: OneShotOpts) -> 
     fs, vs, status = [], [], 0
     for i in np.nonzero(counts)[0]:
         a = int(counts[i])
-        try:
-            c = prony_coefficients(m[i], a_m, a)
-        except np.linalg.LinAlgError:
-            status = 2
-            continue
-        pos = enumerate_positions(N, B, int(i), c)
+        if opts.method == 3:
+            pos = snap_positions(N, B, int(i), pencil_points(m[i], a_m, a))
+        else:
+            try:
+                c = prony_coefficients(m[i], a_m, a)
+            except np.linalg.LinAlgError:
+                status = 2
+                continue
+            if opts.method == 1:
+                pos = snap_positions(N, B, int(i), polynomial_roots(c))
+            else:
+                pos = enumerate_positions(N, B, int(i), c)
         y = Yr[3 * a_m:, i] / B
         f, p = subspace_pursuit(N, B, pos, y, taus, tol2, opts.max_iter)
         fs.extend(f.tolist())

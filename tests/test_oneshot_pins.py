@@ -116,3 +116,91 @@ def test_delay_structure_is_checked():
     rng = np.random.default_rng(0)
     with pytest.raises(ValueError):  # fewer than 2 a_m random delays
         dt.check_delays(N, 3, synth.oneshot_delays(N, 3, 5, rng))
+
+
+# ---------------------------------------------------------------- Step 2, methods 1 and 3
+def three_tone_bucket(seed):
+    i = 77
+    fs = [i + 2 * B, i + 7 * B, i + 12 * B]
+    vals = [2.0 + 1.0j, -1.5 + 0.5j, 0.7 - 1.1j]
+    p, dl = problem(3, seed, support=fs, values=vals)
+    return p, dl, i, fs
+
+
+@pytest.mark.parametrize("a", [1, 2, 3])
+def test_method1_roots_are_the_tones(oracle_mod, a):
+    """Method 1: in the exactly sparse case the a roots of P(z) = 0 (Eq. 12) are the bucket's
+    z_j = e^{2 pi i f_j / N}, written here from the generator's support."""
+    p, dl, i, fs = three_tone_bucket(5)
+    if a < 3:
+        p, dl = problem(a, 5, support=fs[:a], values=[2.0 + 1.0j, -1.5 + 0.5j][:a])
+    Y = oracle_mod.bucketize(N, [L], dl, p.x)
+    m = dt.moments(Y, B, 3)
+    roots = dt.polynomial_roots(dt.prony_coefficients(m[i], 3, a))
+    want = np.exp(2j * np.pi * np.array(fs[:a]) / N)
+    np.testing.assert_allclose(sorted(roots, key=np.angle), sorted(want, key=np.angle),
+                               rtol=0, atol=1e-9)
+    np.testing.assert_array_equal(dt.snap_positions(N, B, i, roots), fs[:a])
+
+
+@pytest.mark.parametrize("a", [2, 3])
+def test_pencil_eigenvalues_theorem3(oracle_mod, a):
+    """Method 3: the generalized eigenvalues of Y_2 - lambda Y_1 (Eq. 15-17) are conj(z_j),
+    by the Vandermonde factors of Theorem 3.  Checked with scipy's QZ on the square top
+    rows of the pencil, against the generator's z_j, and through the oracle's Y_1^+ Y_2."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    p, dl, i, fs = three_tone_bucket(6)
+    if a < 3:
+        p, dl = problem(a, 6, support=fs[:a], values=[2.0 + 1.0j, -1.5 + 0.5j][:a])
+    Y = oracle_mod.bucketize(N, [L], dl, p.x)
+    m = dt.moments(Y, B, 3)
+    Y1, Y2 = dt.pencil(m[i], 3, a)
+    assert Y1.shape == (a + 1, a) and Y2.shape == (a + 1, a)
+    lam = scipy_linalg.eig(Y2[:a], Y1[:a], right=False)
+    z = np.exp(2j * np.pi * np.array(fs[:a]) / N)
+    np.testing.assert_allclose(sorted(lam, key=np.angle), sorted(z.conj(), key=np.angle),
+                               rtol=0, atol=1e-9)
+    pts = dt.pencil_points(m[i], 3, a)
+    np.testing.assert_allclose(sorted(pts, key=np.angle), sorted(z, key=np.angle),
+                               rtol=0, atol=1e-9)
+
+
+def test_snap_positions_rule():
+    """Points take candidates most confident first; a taken candidate sends the point to
+    the nearest free one on its own side, and the index wraps modulo L."""
+    i, Lc = 77, N // B
+
+    def pt(u):
+        return np.exp(2j * np.pi * (i + u * B) / N)
+
+    got = dt.snap_positions(N, B, i, np.array([pt(5.3), pt(5.0), pt(4.6)]))
+    np.testing.assert_array_equal(got, [i + 4 * B, i + 5 * B, i + 6 * B])
+    got = dt.snap_positions(N, B, i, np.array([pt(Lc - 0.3)]))
+    np.testing.assert_array_equal(got, [i])
+
+
+@pytest.mark.parametrize("method", [1, 3])
+@pytest.mark.parametrize("a_m,P", [(2, 6), (3, 7)])
+def test_exact_recovery_methods_1_and_3(oracle_mod, method, a_m, P):
+    """Methods 1 and 3 recover the generator's truth on exactly sparse inputs, like
+    method 2."""
+    K = 60
+    for seed in range(10, 40):
+        p, dl = problem(K, seed, a_m=a_m, P=P)
+        if max(collections.Counter((p.support % B).tolist()).values()) <= a_m:
+            break
+    Y = oracle_mod.bucketize(N, [L], dl, p.x)
+    res = dt.decode(N, B, K, dl, Y, dt.OneShotOpts(a_m=a_m, method=method))
+    assert res.status == 0
+    np.testing.assert_array_equal(res.idx, p.support)
+    np.testing.assert_allclose(res.val, p.values, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("method", [1, 3])
+def test_noisy_recovery_methods_1_and_3(oracle_mod, method):
+    """30 dB: the support is the truth's for methods 1 and 3 too."""
+    K = 40
+    p, dl = problem(K, 51, snr_db=30.0)
+    Y = oracle_mod.bucketize(N, [L], dl, p.x)
+    res = dt.decode(N, B, K, dl, Y, dt.OneShotOpts(noise_var=p.noise_var, method=method))
+    np.testing.assert_array_equal(res.idx, p.support)
