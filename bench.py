@@ -321,15 +321,17 @@ def measure_oneshot(sfft, batch=64, steps=20, warmup=3):
     through sfft_execute_batch; reports signals/s, the phases and the recovery."""
     import torch
     out = {"workload": "oneshot_2097152: N=2^21 complex64, B=8192 (L=256), K=256, "
-                       "|xhat|~U[1,10], a_m=3, R=16 (9 consecutive + 7 random delays)"}
-    for snr in (None, 30.0):
+                       "|xhat|~U[1,10], a_m=3, R=16 (9 consecutive + 7 random delays); "
+                       "Step 2 by enumeration (method 2) unless the key names method 1 "
+                       "(polynomial roots) or 3 (matrix pencil)"}
+    for snr, method in ((None, 2), (30.0, 2), (None, 1), (30.0, 1), (None, 3), (30.0, 3)):
         probs = [synth.config_problem("oneshot_2097152", seed=60 + i, snr_db=snr) for i in range(8)]
         dl = probs[0].delays  # one plan: the same delays for every signal
         probs = [synth.make_problem(p.N, p.f, p.K, seed=60 + i, delays=dl, mag=(1.0, 10.0),
                                     snr_db=snr) for i, p in enumerate(probs)]
         nv = float(np.mean([p.noise_var for p in probs]))
         plan = sfft.Plan(probs[0].N, probs[0].K, probs[0].f, dl, decoder="oneshot", a_m=3,
-                         noise_var=nv, max_batch=batch)
+                         noise_var=nv, max_batch=batch, dt_method=method)
         dev = [torch.from_numpy(p.x.astype(np.complex64)).cuda() for p in probs]
         xs = torch.stack([dev[i % len(dev)] for i in range(batch)])
         res = plan.empty_outputs("cuda", batch)
@@ -355,7 +357,8 @@ def measure_oneshot(sfft, batch=64, steps=20, warmup=3):
             l0 += e0_
             l2.append(e2_)
         plan.close()
-        out["exact" if snr is None else f"snr_{int(snr)}db"] = {
+        key = "exact" if snr is None else f"snr_{int(snr)}db"
+        out[key if method == 2 else f"method{method}_{key}"] = {
             "signals_per_s": batch * 1e3 / ms, "ms_per_step": ms, "batch": batch,
             "phases_ms_per_step": {k: v["ms"] / steps for k, v in prof.items()},
             "support_equal_truth": f"{sup_ok}/{len(probs)}",

@@ -173,7 +173,7 @@ def snap_positions(N: int, B: int, i: int, z: np.ndarray) -> np.ndarray:
         side = 1 if u[t] >= q0[t] else -1
         q = int(q0[t]) % L
         k = 0
-        while q in taken:
+        while q in taken and k < 2 * L - 1:  # (the bound only matters when L < a)
             k += 1
             step = (k + 1) // 2 * (side if k % 2 == 1 else -side)
             q = (int(q0[t]) + step) % L

@@ -52,7 +52,7 @@ class Opts(ctypes.Structure):
                 ("decode_ctas", ctypes.c_int32), ("decoder", ctypes.c_int32),
                 ("oneshot_am", ctypes.c_int32), ("kay_m", ctypes.c_int32),
                 ("noise_auto", ctypes.c_int32), ("host_gather", ctypes.c_int32),
-                ("dft_fma_only", ctypes.c_int32)]
+                ("oneshot_method", ctypes.c_int32), ("dft_fma_only", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

@@ -223,6 +223,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         // random delays (Sec. 4.1, Stage 1); the output holds at most one value per bucket
         const int am = o.oneshot_am;
         if (n_stages != 1 || am < 1 || am > 3 || n_delays < 5 * am || K > N / f[0]) return SFFT_EINVAL;
+        if (o.oneshot_method < 0 || o.oneshot_method > 3) return SFFT_EINVAL;
         for (int r = 0; r < 3 * am; ++r)
             if (delays[r] != ((int64_t)r - am + N) % N) return SFFT_EINVAL;
     }
@@ -661,6 +662,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     // a tile's phasor tables go to shared memory up to 160 KB (up to 96 KB two classify
     // CTAs still fit an SM)
     da.wtab_smem = (size_t)p->wtab_elems * p->esz <= 160 * 1024 ? 1 : 0;
+    da.dt_method = p->opts.oneshot_method == 0 ? 2 : p->opts.oneshot_method;
     const int threads = 512;
     const int total = p->num_sms * p->decode_occ;
     // later rounds touch O(K) bins: about one CTA per 256 expected single-tons

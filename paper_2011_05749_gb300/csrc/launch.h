@@ -34,6 +34,7 @@ struct DecodeArgs {
     long long spin_limit; // polls before a device-side wait gives up
     int32_t wtab_elems;   // largest window of ML phasor tables a classify tile stages
     int32_t wtab_smem;    // 1: classify stages them in shared memory
+    int32_t dt_method;    // one-shot Step 2: 1 polynomial roots, 2 enumeration, 3 matrix pencil
     const int32_t* pbin;  // position -> bin j, per stage at bin_base
     const int32_t* bpos;  // bin j -> position
     const void* roots;    // the plan's twiddle table: ML phasor tables at st[d].wtab_off

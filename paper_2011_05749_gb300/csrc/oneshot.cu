@@ -9,10 +9,13 @@
 //        (Eq. 10-11), as square roots of the eigenvalues of M^H M (cyclic complex Jacobi).
 //   DT2  the vote: per signal, the K-th largest singular value above the floor, by an
 //        8-bit radix select on the FP64 bit patterns (one CTA per signal).
-//   DT3  Steps 2-3, one warp per bucket with a > 0 votes: C = M_a^{-1} M_s (Eq. 14), |P(z)|
-//        (Eq. 12) at every candidate (the lanes split them) and the a smallest; then
-//        subspace pursuit over the atoms {f, f + B, f - B} with the P random-delay
-//        measurements (Eq. 18), lane r holding measurement r.
+//   DT3  Steps 2-3, one warp per bucket with a > 0 votes.  Step 2 by one of the paper's
+//        three methods: C = M_a^{-1} M_s (Eq. 14), then |P(z)| (Eq. 12) at every candidate
+//        (the lanes split them) and the a smallest (method 2, the default), or the roots of
+//        P(z) (method 1); or the eigenvalues of Y_1^+ Y_2 (Eq. 15-17, method 3), which are
+//        1 / z_j.  Roots are snapped to the bucket's candidates by angle.  Then subspace
+//        pursuit over the atoms {f, f + B, f - B} with the P random-delay measurements
+//        (Eq. 18), lane r holding measurement r.
 // The per-bucket arithmetic is FP64 whatever the bins' type (position and value
 // estimation).  Results go to the slot's recovered list; compaction follows as for the
 // peeling decoder.
@@ -167,6 +170,105 @@ __device__ __forceinline__ void hermitian_eigenvalues(Cd (&G)[3][3], double* ev)
     }
 #pragma unroll
     for (int p = 0; p < NN; ++p) ev[p] = G[p][p].x;
+}
+
+// principal square root of w = a + b i: with r = |w|, t = sqrt((r + |a|) / 2); then
+// (t, b / (2 t)) for a >= 0, and (|b| / (2 t), +-t) with the sign of b for a < 0
+__device__ __forceinline__ Cd csqrt_d(Cd w)
+{
+    const double r = sqrt(abs2(w));
+    if (r == 0.0) return cd(0, 0);
+    const double t = sqrt(0.5 * (r + fabs(w.x)));
+    if (w.x >= 0) return cd(t, w.y / (2.0 * t));
+    return cd(fabs(w.y) / (2.0 * t), w.y >= 0 ? t : -t);
+}
+
+// The n <= 3 roots of z^n + c[n-1] z^{n-1} + ... + c[0].  n = 1, 2 in closed form (Sec. 3.1,
+// method 1; the quadratic as q = -(c1 + s sqrt(c1^2 - 4 c0)) / 2 with the sign s that
+// avoids cancellation, roots q and c0 / q); n = 3 by the Durand-Kerner (Weierstrass)
+// simultaneous iteration z_k <- z_k - p(z_k) / prod_{l != k} (z_k - z_l) from
+// (0.4 + 0.9 i)^k, at most 200 sweeps.
+__device__ void poly_roots(const Cd* c, int n, Cd* z)
+{
+    if (n == 1) {
+        z[0] = cd(-c[0].x, -c[0].y);
+        return;
+    }
+    if (n == 2) {
+        const Cd d = csqrt_d(c[1] * c[1] - cd(4.0 * c[0].x, 4.0 * c[0].y));
+        const Cd t1 = c[1] + d, t2 = c[1] - d;
+        const Cd t = abs2(t1) >= abs2(t2) ? t1 : t2;
+        const Cd q = cd(-0.5 * t.x, -0.5 * t.y);
+        z[0] = q;
+        z[1] = abs2(q) > 0 ? divd(c[0], q) : cd(0, 0);
+        return;
+    }
+    const Cd w = cd(0.4, 0.9);
+    z[0] = cd(1, 0);
+    z[1] = w;
+    z[2] = w * w;
+    for (int it = 0; it < 200; ++it) {
+        double moved = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            Cd pz = cd(1, 0);
+            for (int t = 2; t >= 0; --t) pz = pz * z[k] + c[t];
+            Cd den = cd(1, 0);
+            for (int l = 0; l < 3; ++l)
+                if (l != k) den = den * (z[k] - z[l]);
+            if (abs2(den) == 0.0) continue;
+            const Cd dz = divd(pz, den);
+            z[k] = z[k] - dz;
+            moved = fmax(moved, abs2(dz) / fmax(1.0, abs2(z[k])));
+        }
+        if (moved < 1e-30) break;
+    }
+}
+
+// Positions of n points z (methods 1 and 3): u = ((arg z) N / (2 pi) - j) / B mod L is the
+// fractional candidate index; the points take candidates in order of increasing
+// |u - round(u)| (lower index on ties), each the nearest q not yet taken: round(u), then
+// alternately one step further on u's side and on the other side.  q ascending out.
+__device__ void snap_positions(const Cd* z, int n, int j, int B, int L, int32_t N, int* q_out)
+{
+    double u[3], q0[3], err[3];
+    int ord[3];
+    for (int t = 0; t < n; ++t) {
+        const double f = atan2(z[t].y, z[t].x) * (double)N / (2.0 * 3.14159265358979323846);
+        double v = fmod((f - (double)j) / (double)B, (double)L);
+        if (v < 0) v += (double)L;
+        u[t] = v;
+        q0[t] = floor(v + 0.5);
+        err[t] = fabs(v - q0[t]);
+        ord[t] = t;
+    }
+    for (int i = 1; i < n; ++i)
+        for (int k = i; k > 0 && err[ord[k - 1]] > err[ord[k]]; --k) {
+            const int x = ord[k];
+            ord[k] = ord[k - 1];
+            ord[k - 1] = x;
+        }
+    int taken[3], nt = 0;
+    for (int s = 0; s < n; ++s) {
+        const int t = ord[s];
+        const int side = u[t] >= q0[t] ? 1 : -1;
+        const int base = (int)q0[t];
+        int q = ((base % L) + L) % L;
+        for (int k = 1; k < 2 * L; ++k) {
+            bool used = false;
+            for (int e = 0; e < nt; ++e) used |= taken[e] == q;
+            if (!used) break;
+            const int step = (k + 1) / 2 * ((k & 1) ? side : -side);
+            q = (((base + step) % L) + L) % L;
+        }
+        taken[nt++] = q;
+    }
+    for (int i = 1; i < nt; ++i)
+        for (int k = i; k > 0 && taken[k - 1] > taken[k]; --k) {
+            const int x = taken[k];
+            taken[k] = taken[k - 1];
+            taken[k - 1] = x;
+        }
+    for (int t = 0; t < nt; ++t) q_out[t] = taken[t];
 }
 
 }  // namespace
@@ -338,6 +440,60 @@ __global__ void __launch_bounds__(kSolveThreads) dt_solve_kernel(const __grid_co
         dt_solve_bucket<T>(a, sig, __ldcg(a.ws.nzl + (int64_t)sig * a.pd.sumB + i));
 }
 
+// Step 2, method 3 (Sec. 3.1, Eq. 15-17, Theorem 3) for one bucket, by one lane: Y_1[r][c]
+// = m_{r-c}, Y_2[r][c] = m_{r-c-1} ((a + 1) x a); G = Y_1^+ Y_2 from the normal equations
+// (Y_1^H Y_1) G = Y_1^H Y_2, one column at a time; G's eigenvalues are the roots of its
+// characteristic polynomial, and each is 1 / z_j (the Vandermonde factors of Theorem 3's
+// proof give conj(z_j)); a zero eigenvalue gives z = 1.  A, rhs: scratch (a^2 and a).
+template <typename T>
+__device__ void pencil_points(const typename C2<T>::t* Y, int b, int B, int am, int na,
+                              double invB, Cd* A, Cd* rhs, Cd* z)
+{
+    Cd m[7];  // m_k at k + na, k = -na .. na
+    for (int k = -na; k <= na; ++k) {
+        const typename C2<T>::t y = __ldcg(Y + (int64_t)(k + am) * B + b);
+        m[k + na] = cd((double)y.x * invB, (double)y.y * invB);
+    }
+    auto y1 = [&](int r, int c) { return m[r - c + na]; };
+    auto y2 = [&](int r, int c) { return m[r - c - 1 + na]; };
+    Cd G[3][3];
+    for (int d = 0; d < na; ++d) {
+        // column d: (Y_1^H Y_1) g_d = Y_1^H y2_d (solve_lane overwrites A, so it is rebuilt)
+        for (int u = 0; u < na; ++u) {
+            Cd h = cd(0, 0);
+            for (int r = 0; r <= na; ++r) h = h + conjd(y1(r, u)) * y2(r, d);
+            rhs[u] = h;
+            for (int v = 0; v < na; ++v) {
+                Cd e = cd(0, 0);
+                for (int r = 0; r <= na; ++r) e = e + conjd(y1(r, u)) * y1(r, v);
+                A[u * na + v] = e;
+            }
+        }
+        const bool ok = solve_lane(A, rhs, na);
+        for (int u = 0; u < na; ++u) G[u][d] = ok ? rhs[u] : cd(0, 0);
+    }
+    Cd c[3];
+    if (na == 1) {
+        c[0] = cd(-G[0][0].x, -G[0][0].y);
+    } else if (na == 2) {
+        const Cd tr = G[0][0] + G[1][1];
+        c[1] = cd(-tr.x, -tr.y);
+        c[0] = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+    } else {
+        const Cd tr = G[0][0] + G[1][1] + G[2][2];
+        c[2] = cd(-tr.x, -tr.y);
+        c[1] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) + (G[0][0] * G[2][2] - G[0][2] * G[2][0]) +
+               (G[1][1] * G[2][2] - G[1][2] * G[2][1]);
+        const Cd det = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
+                       G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+                       G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+        c[0] = cd(-det.x, -det.y);
+    }
+    Cd lam[3];
+    poly_roots(c, na, lam);
+    for (int t = 0; t < na; ++t) z[t] = abs2(lam[t]) > 0 ? divd(cd(1, 0), lam[t]) : cd(1, 0);
+}
+
 // Steps 2-3 of one voted bucket by one warp (every lane calls with the same b).
 template <typename T>
 __device__ __noinline__ void dt_solve_bucket(const DecodeArgs& a, int sig, int b)
@@ -373,87 +529,106 @@ __device__ __noinline__ void dt_solve_bucket(const DecodeArgs& a, int sig, int b
         const V y = __ldcg(Y + (int64_t)(lane + am) * B + b);
         mk = cd((double)y.x * invB, (double)y.y * invB);
     }
-    // Eq. 14: M_a C = M_s, M_a[r][c] = m_{r+c}, M_s[r] = -m_{a+r}
-    for (int idx = 0; idx < na * na; ++idx) {
-        const int r = idx / na, c = idx - r * na;
-        const double x = __shfl_sync(0xffffffffu, mk.x, r + c), y = __shfl_sync(0xffffffffu, mk.y, r + c);
-        if (lane == 0) A[idx] = cd(x, y);
+    const int method = a.dt_method;  // Step 2: 1 polynomial roots, 2 enumeration, 3 pencil
+    Cd c[3] = {cd(0, 0), cd(0, 0), cd(0, 0)};
+    if (method != 3) {
+        // Eq. 14: M_a C = M_s, M_a[r][c] = m_{r+c}, M_s[r] = -m_{a+r}
+        for (int idx = 0; idx < na * na; ++idx) {
+            const int r = idx / na, cc = idx - r * na;
+            const double x = __shfl_sync(0xffffffffu, mk.x, r + cc), y = __shfl_sync(0xffffffffu, mk.y, r + cc);
+            if (lane == 0) A[idx] = cd(x, y);
+        }
+        for (int r = 0; r < na; ++r) {
+            const double x = __shfl_sync(0xffffffffu, mk.x, na + r), y = __shfl_sync(0xffffffffu, mk.y, na + r);
+            if (lane == 0) rhs[r] = cd(-x, -y);
+        }
+        __syncwarp();
+        if (lane == 0) s_ok[wib] = solve_lane(A, rhs, na) ? 1 : 0;
+        __syncwarp();
+        if (!s_ok[wib]) {
+            if (lane == 0) atomicSub(ctr + kCtrResolved, 1);
+            return;
+        }
+        for (int t = 0; t < 3; ++t) c[t] = t < na ? rhs[t] : cd(0, 0);
+        __syncwarp();
     }
-    for (int r = 0; r < na; ++r) {
-        const double x = __shfl_sync(0xffffffffu, mk.x, na + r), y = __shfl_sync(0xffffffffu, mk.y, na + r);
-        if (lane == 0) rhs[r] = cd(-x, -y);
-    }
-    __syncwarp();
-    if (lane == 0) s_ok[wib] = solve_lane(A, rhs, na) ? 1 : 0;
-    __syncwarp();
-    if (!s_ok[wib]) {
-        if (lane == 0) atomicSub(ctr + kCtrResolved, 1);
-        return;
-    }
-    Cd c[3];
-    for (int t = 0; t < 3; ++t) c[t] = t < na ? rhs[t] : cd(0, 0);
-    __syncwarp();
 
-    // Step 2 (enumeration): candidates q = lane, lane + 32, ...; z = e^{2 pi i (j + q B) / N}
-    // by a rotation e^{2 pi i 32 / L} per step from z_lane
-    double bv[3];
-    int bq[3];
-    for (int t = 0; t < 3; ++t) {
-        bv[t] = 1e300;
-        bq[t] = 0x7fffffff;
-    }
-    {
-        Cd z = root_n<T>(pd, a.roots, ((int64_t)j + (int64_t)lane * B) % N);
-        const Cd w = root_n<T>(pd, a.roots, (32 * (int64_t)B) % N);  // e^{2 pi i 32 / L}
-        for (int q = lane; q < L; q += 32) {
-            if (((q - lane) & 1023) == 0 && q != lane) z = root_n<T>(pd, a.roots, ((int64_t)j + (int64_t)q * B) % N);
-            Cd pz = cd(1, 0);
-            for (int t = na - 1; t >= 0; --t) pz = pz * z + c[t];
-            const double v = abs2(pz);
-            // keep the na smallest (v, q), lower q first on ties; q only grows
-            int k = na;
-            while (k > 0 && v < bv[k - 1]) --k;
-            if (k < na) {
-                for (int t = na - 1; t > k; --t) {
-                    bv[t] = bv[t - 1];
-                    bq[t] = bq[t - 1];
-                }
-                bv[k] = v;
-                bq[k] = q;
-            }
-            z = z * w;
-        }
-    }
-    // merge across lanes: na rounds of a warp argmin over (v, q)
     int pos_q[3];
-    for (int t = 0; t < na; ++t) {
-        double v = bv[0];
-        int q = bq[0];
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-            const int oq = __shfl_xor_sync(0xffffffffu, q, o);
-            if (ov < v || (ov == v && oq < q)) {
-                v = ov;
-                q = oq;
+    if (method == 1 || method == 3) {
+        // methods 1 and 3: lane 0 finds the points z_j and snaps them to candidates
+        __shared__ int s_pos[kSolveThreads / 32][3];
+        if (lane == 0) {
+            Cd z[3];
+            if (method == 1)
+                poly_roots(c, na, z);
+            else
+                pencil_points<T>(Y, b, B, am, na, invB, A, rhs, z);
+            snap_positions(z, na, j, B, L, N, s_pos[wib]);
+        }
+        __syncwarp();
+        for (int t = 0; t < na; ++t) pos_q[t] = s_pos[wib][t];
+        __syncwarp();
+    } else {
+        // Step 2 (enumeration): candidates q = lane, lane + 32, ...; z = e^{2 pi i (j + q B) / N}
+        // by a rotation e^{2 pi i 32 / L} per step from z_lane
+        double bv[3];
+        int bq[3];
+        for (int t = 0; t < 3; ++t) {
+            bv[t] = 1e300;
+            bq[t] = 0x7fffffff;
+        }
+        {
+            Cd z = root_n<T>(pd, a.roots, ((int64_t)j + (int64_t)lane * B) % N);
+            const Cd w = root_n<T>(pd, a.roots, (32 * (int64_t)B) % N);  // e^{2 pi i 32 / L}
+            for (int q = lane; q < L; q += 32) {
+                if (((q - lane) & 1023) == 0 && q != lane) z = root_n<T>(pd, a.roots, ((int64_t)j + (int64_t)q * B) % N);
+                Cd pz = cd(1, 0);
+                for (int t = na - 1; t >= 0; --t) pz = pz * z + c[t];
+                const double v = abs2(pz);
+                // keep the na smallest (v, q), lower q first on ties; q only grows
+                int k = na;
+                while (k > 0 && v < bv[k - 1]) --k;
+                if (k < na) {
+                    for (int t = na - 1; t > k; --t) {
+                        bv[t] = bv[t - 1];
+                        bq[t] = bq[t - 1];
+                    }
+                    bv[k] = v;
+                    bq[k] = q;
+                }
+                z = z * w;
             }
         }
-        pos_q[t] = q;
-        if (bq[0] == q) {  // the owner pops its head
-            for (int u = 0; u + 1 < 3; ++u) {
-                bv[u] = bv[u + 1];
-                bq[u] = bq[u + 1];
+        // merge across lanes: na rounds of a warp argmin over (v, q)
+        for (int t = 0; t < na; ++t) {
+            double v = bv[0];
+            int q = bq[0];
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+                const int oq = __shfl_xor_sync(0xffffffffu, q, o);
+                if (ov < v || (ov == v && oq < q)) {
+                    v = ov;
+                    q = oq;
+                }
             }
-            bv[2] = 1e300;
-            bq[2] = 0x7fffffff;
+            pos_q[t] = q;
+            if (bq[0] == q) {  // the owner pops its head
+                for (int u = 0; u + 1 < 3; ++u) {
+                    bv[u] = bv[u + 1];
+                    bq[u] = bq[u + 1];
+                }
+                bv[2] = 1e300;
+                bq[2] = 0x7fffffff;
+            }
         }
+        // positions ascending
+        for (int i = 1; i < na; ++i)
+            for (int k = i; k > 0 && pos_q[k - 1] > pos_q[k]; --k) {
+                const int t = pos_q[k];
+                pos_q[k] = pos_q[k - 1];
+                pos_q[k - 1] = t;
+            }
     }
-    // positions ascending
-    for (int i = 1; i < na; ++i)
-        for (int k = i; k > 0 && pos_q[k - 1] > pos_q[k]; --k) {
-            const int t = pos_q[k];
-            pos_q[k] = pos_q[k - 1];
-            pos_q[k - 1] = t;
-        }
 
     // Step 3: subspace pursuit.  Dictionary: for each position f, the atoms f, f + B, f - B
     // (mod N) in that order, duplicates dropped.

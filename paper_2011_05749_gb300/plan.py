@@ -25,7 +25,7 @@ class Plan:
                  max_rounds: int = 64, max_batch: int = 1, max_tile: int = 0,
                  wait_limit_log2: int = 0, fault_inject: int = 0, decode_ctas: int = 0,
                  decoder: str = "peel", a_m: int = 3, kay_m: int = 2, noise_auto: bool = False,
-                 host_gather: bool = False, dft_fma_only: bool = False):
+                 host_gather: bool = False, dft_fma_only: bool = False, dt_method: int = 2):
         lib = load()
         f = np.ascontiguousarray(f, dtype=np.int64)
         delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -38,6 +38,7 @@ class Plan:
         o.noise_auto = 1 if noise_auto else 0
         o.host_gather = 1 if host_gather else 0
         o.dft_fma_only = 1 if dft_fma_only else 0
+        o.oneshot_method = dt_method
         o.max_rounds = max_rounds
         o.max_batch = max_batch
         o.max_tile = max_tile

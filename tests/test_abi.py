@@ -69,7 +69,7 @@ def test_opts_layout_and_defaults_without_gpu():
     assert (o.dtype, o.precision, o.locate, o.max_rounds, o.max_batch) == (0, 1, 1, 64, 1)
     assert (o.a_min, o.c0, o.c1) == (1.0, 4.0, 2.0)
     assert (o.decoder, o.oneshot_am, o.kay_m, o.noise_auto) == (_lib.DECODER_PEEL, 3, 2, 0)
-    assert (o.host_gather, o.dft_fma_only) == (0, 0)
+    assert (o.host_gather, o.oneshot_method, o.dft_fma_only) == (0, 0, 0)
 
 
 def test_oneshot_plan_rules_checked_without_gpu():

@@ -36,18 +36,19 @@ def problem(N, L, K, seed, a_m=3, P=7, snr_db=None, max_per_bucket=None):
     raise RuntimeError("no seed with the requested bucket occupancy")
 
 
-def oracle_decode(oracle_mod, p, dl, a_m, eta):
+def oracle_decode(oracle_mod, p, dl, a_m, eta, method=2):
     from oracle import oneshot as dt
     B = p.N // p.f[0]
     Y = oracle_mod.bucketize(p.N, p.f, dl, p.x)
-    return dt.decode(p.N, B, p.K, dl, Y, dt.OneShotOpts(a_m=a_m, noise_var=p.noise_var, eta=eta))
+    return dt.decode(p.N, B, p.K, dl, Y, dt.OneShotOpts(a_m=a_m, noise_var=p.noise_var, eta=eta,
+                                                        method=method))
 
 
-def run_gpu(sfft, p, dl, a_m, prec, n_copies=1):
+def run_gpu(sfft, p, dl, a_m, prec, n_copies=1, method=2):
     dtype = "c64" if prec == "fp32" else "c128"
     npdt = np.complex64 if prec == "fp32" else np.complex128
     plan = sfft.Plan(p.N, p.K, p.f, dl, precision=prec, dtype=dtype, decoder="oneshot", a_m=a_m,
-                     noise_var=p.noise_var, max_batch=n_copies)
+                     noise_var=p.noise_var, max_batch=n_copies, dt_method=method)
     x = torch.from_numpy(p.x.astype(npdt)).cuda()
     if n_copies == 1:
         idx, val, info = plan.execute(x)
@@ -132,3 +133,48 @@ def test_full_size_config_matches_oracle(sfft, oracle_mod):
     np.testing.assert_array_equal(ref.idx, p.support)
     got = run_gpu(sfft, p, p.delays, 3, "fp32")[0]
     check(got, ref, "fp32")
+
+
+# ------------------------------------------------------- Step 2 methods 1 (roots) and 3 (pencil)
+@pytest.mark.parametrize("method", [1, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("a_m,P", [(3, 7), (2, 6)])
+def test_methods_exact_match_oracle_and_truth(sfft, oracle_mod, method, prec, a_m, P):
+    """Methods 1 and 3 on exactly sparse inputs (N = 2^18, B = 4096, K = 200, at most a_m
+    tones per bucket): the oracle recovers the truth, and the GPU the oracle's support and
+    values."""
+    p, dl = problem(1 << 18, 64, 200, 71, a_m=a_m, P=P, max_per_bucket=a_m)
+    eta = 3e-3 if prec == "fp32" else 1e-6
+    ref = oracle_decode(oracle_mod, p, dl, a_m, eta, method)
+    np.testing.assert_array_equal(ref.idx, p.support)
+    got = run_gpu(sfft, p, dl, a_m, prec, method=method)[0]
+    check(got, ref, prec)
+
+
+@pytest.mark.parametrize("method", [1, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_methods_noisy_match_oracle(sfft, oracle_mod, method, prec):
+    """30 dB: support equal to the oracle's, values within tolerance of the oracle's."""
+    p, dl = problem(1 << 18, 64, 150, 81, snr_db=30.0, max_per_bucket=3)
+    eta = 3e-3 if prec == "fp32" else 1e-6
+    ref = oracle_decode(oracle_mod, p, dl, 3, eta, method)
+    got = run_gpu(sfft, p, dl, 3, prec, method=method)[0]
+    check(got, ref, prec)
+
+
+@pytest.mark.parametrize("method", [1, 3])
+def test_methods_full_size_config(sfft, oracle_mod, method):
+    """The benchmark's one-shot workload (N = 2^21, B = 8192, K = 256, R = 16, exact, FP32)
+    with methods 1 and 3: the oracle's support (and the truth's), values within 1e-5."""
+    p = synth.config_problem("oneshot_2097152", seed=61)
+    ref = oracle_decode(oracle_mod, p, p.delays, 3, 3e-3, method)
+    np.testing.assert_array_equal(ref.idx, p.support)
+    got = run_gpu(sfft, p, p.delays, 3, "fp32", method=method)[0]
+    check(got, ref, "fp32")
+
+
+def test_method_out_of_range_rejected(sfft):
+    N, L = 1 << 16, 64
+    dl = synth.oneshot_delays(N, 3, 7, np.random.default_rng(3))
+    with pytest.raises(Exception):
+        sfft.Plan(N, 10, (L,), dl, decoder="oneshot", a_m=3, dt_method=4)
