@@ -311,6 +311,7 @@ def measure_large(sfft, hbm_peak, reps=10):
                        "dram_bytes": dram,
                        "dram_frac_of_hbm": (dram / (bk_ms * 1e-3) / (hbm_peak * 1e9)
                                             if dram else None),
+                       "sector_efficiency": (alg / dram if dram else None),
                        "peak_gbs": hbm_peak}}
 
 
@@ -973,7 +974,18 @@ def run_gpu(args):
                      "traffic": (traffic_sig * sig_per_launch if traffic_sig else None),
                      "alg_bytes_per_launch": sig_per_launch * alg_bytes_sig,
                      "signals_per_launch": sig_per_launch,
-                     "avg_launch_ms": bk_ms},
+                     "avg_launch_ms": bk_ms,
+                     # against the ~7.9 TB/s nominal HBM3e rate as well as the measured copy
+                     "frac_of_nominal_7900": achieved / 7900.0,
+                     # DRAM bytes the kernel moves (ncu traffic) over its time, and the share
+                     # of them that are algorithmic (sector efficiency)
+                     "dram_frac": ((traffic_sig * sig_per_launch) / (bk_ms / 1e3) / 1e9 / hbm_peak
+                                   if traffic_sig else None),
+                     "sector_efficiency": (alg_bytes_sig / traffic_sig if traffic_sig else None),
+                     # the B-point DFTs in the FFTW convention, 5 B log2 B flops each
+                     "dft_fftw_gflops": (sig_per_launch * R * sum(5.0 * (N // L) * np.log2(N // L)
+                                                                  for L in f)
+                                         / (bk_ms / 1e3) / 1e9)},
         "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
