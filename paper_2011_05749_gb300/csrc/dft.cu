@@ -145,14 +145,15 @@ __device__ void axis_dft_odd(typename C2<T>::t* s, const typename C2<T>::t* twm,
 // block), so the tile makes ceil(log2P / 3) trips through shared memory.
 // tw[t] = (cos, sin)(2 pi t / P), t < P / 2; the butterfly of the stage with half-size H
 // multiplies by W_P^{(p mod H) P / (2 H)}.
+// nst < log2P runs only the first nst stages (the caller does the rest).
 template <typename T>
 __device__ void axis_fft_pow2(typename C2<T>::t* s, const typename C2<T>::t* tw, int P,
-                              int log2P, int LS, int TS)
+                              int log2P, int LS, int TS, int nst)
 {
     using V = typename C2<T>::t;
     const int M = TS / P;
-    for (int lh = 0; lh < log2P;) {
-        const int c = min(3, log2P - lh);
+    for (int lh = 0; lh < nst;) {
+        const int c = min(3, nst - lh);
         const int G8 = 1 << c;
         const int h = 1 << lh;
         const int ngrp = P >> c;
@@ -594,10 +595,13 @@ __device__ __forceinline__ void odd_axis_tc(float2* s, const float2* tw, int P, 
 }
 
 // The tensor-core axes of a one-pass tile (run after its other axes: the axes of the
-// prime-factor map commute), then the tile's store to the bins.  Out of line, so that the
-// kernel holds nothing live across the MMA code.
+// prime-factor map commute), then the tile's store to the bins.  When the stage has a
+// power-of-two axis (P2 > 1), its last radix-2 stage (half-size P2 / 2, twiddles tw2 in
+// shared memory) runs here: each thread reads a butterfly's two inputs and stores its two
+// outputs, which saves a trip through shared memory.  Out of line, so that the kernel holds
+// nothing live across the MMA code.
 __device__ __noinline__ void tc_axes_store(float2* s, const BucketArgs& a, int d, int64_t slot,
-                                           int TS)
+                                           int TS, const float2* tw2, int P2, int log2P2, int LS2)
 {
     const StageDesc& st = a.pd.st[d];
     const float2* twg = reinterpret_cast<const float2*>(a.tw);
@@ -605,8 +609,30 @@ __device__ __noinline__ void tc_axes_store(float2* s, const BucketArgs& a, int d
         const AxisDesc& A = st.ax[ax];
         if (A.tc) odd_axis_tc(s, twg + A.tw_off, A.P, A.S, TS);  // one pass: stride A.S
     }
-    float2* dst = reinterpret_cast<float2*>(a.bins);
-    for (int e = threadIdx.x; e < TS; e += blockDim.x) __stcg(dst + slot + e, s[e]);
+    float2* dst = reinterpret_cast<float2*>(a.bins) + slot;
+    if (P2 <= 1) {
+        for (int e = threadIdx.x; e < TS; e += blockDim.x) __stcg(dst + e, s[e]);
+        return;
+    }
+    const int H = P2 >> 1, M = TS / P2;
+    const float invM = 1.0f / (float)M, invLS = 1.0f / (float)LS2;
+    for (int w = threadIdx.x; w < M * H; w += blockDim.x) {
+        int k, m;
+        if (LS2 == 1) {
+            k = w & (H - 1);
+            m = w >> (log2P2 - 1);
+        } else {
+            k = fdivmod(w, M, invM, &m);
+        }
+        int lo = 0;
+        const int hi = LS2 == 1 ? m : fdivmod(m, LS2, invLS, &lo);
+        const int base = LS2 == 1 ? m * P2 : lo + hi * LS2 * P2;
+        const int p0 = base + k * LS2, p1 = p0 + H * LS2;
+        const float2 u = s[p0], x = s[p1], wv = tw2[k];
+        const float2 xt = {fmaf(x.x, wv.x, x.y * wv.y), fmaf(x.y, wv.x, -(x.x * wv.y))};
+        __stcg(dst + p0, float2{u.x + xt.x, u.y + xt.y});
+        __stcg(dst + p1, float2{u.x - xt.x, u.y - xt.y});
+    }
 }
 
 __device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc, int bytes)
@@ -801,12 +827,24 @@ __global__ void __launch_bounds__(512, 1) bucketize_kernel(const __grid_constant
 loaded:
     __syncthreads();
 
+    bool stage_tc = false;  // stages with tensor-core axes are one-pass (whole stage, to the bins)
+    for (int ax = a0; ax < a1; ++ax) stage_tc |= st.ax[ax].tc != 0;
+    int p2 = 1, log2p2 = 0, ls2 = 1;
+    const V* tw2 = nullptr;
     int off = 0;
     for (int ax = a0; ax < a1; ++ax) {
         const AxisDesc& A = st.ax[ax];
         const int LS = Tb * (A.S / Sb);
         if (A.pow2) {
-            axis_fft_pow2<T>(s, tws + off, A.P, A.log2P, LS, TS);
+            // with tensor-core axes, the last radix-2 stage runs in the store (tc_axes_store)
+            const bool fuse = TC && stage_tc;
+            if (fuse) {
+                p2 = A.P;
+                log2p2 = A.log2P;
+                ls2 = LS;
+                tw2 = tws + off;
+            }
+            axis_fft_pow2<T>(s, tws + off, A.P, A.log2P, LS, TS, fuse ? A.log2P - 1 : A.log2P);
         } else if (A.P > 1) {
             if (A.P <= 9) {
                 odd_small<T>(s, tws + off, A.P, LS, TS);
@@ -820,11 +858,9 @@ loaded:
         off += (axis_tw_smem(A.P, A.pow2, A.tc) + 1) & ~1;
     }
     if constexpr (TC && sizeof(T) == 4) {
-        // stages with tensor-core axes are one-pass (whole stage, straight to the bins)
-        bool has_tc = false;
-        for (int ax = a0; ax < a1; ++ax) has_tc |= st.ax[ax].tc != 0;
-        if (has_tc) {
-            tc_axes_store(reinterpret_cast<float2*>(s), a, d, slot, TS);
+        if (stage_tc) {
+            tc_axes_store(reinterpret_cast<float2*>(s), a, d, slot, TS,
+                          reinterpret_cast<const float2*>(tw2), p2, log2p2, ls2);
             return;
         }
     }
