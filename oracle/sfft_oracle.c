@@ -264,8 +264,8 @@ static int cmp_double(const void* a, const void* b)
     return (x > y) - (x < y);
 }
 
-/* Noise variance per time sample from the bins (SURVEY's "next" reading of Sec. 3.2's
- * thresholds, which assume sigma^2 known): a bin holding only noise has R delays of
+/* Noise variance per time sample from the bins (no counterpart in the paper: the
+ * thresholds of Sec. 3.2 assume sigma^2 known): a bin holding only noise has R delays of
  * CN(0, B sigma^2) values, so E / B = sum_r |Y_r|^2 / B is sigma^2 times a Gamma(R, 1)
  * variable; with K much below sum B almost every bin is such, and sigma^2 is the lower
  * median of E / B over all bins divided by the Gamma(R, 1) median.                       */
