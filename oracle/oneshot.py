@@ -20,10 +20,14 @@ Per bucket, in the paper's order:
             P(z) = z^a + sum c_t z^t (Eq. 12) are the z_j;
           method 2 (enumeration, the default): P(z) evaluated at every candidate
             z = e^{2 pi i (i + q B) / N}, q < L; the a smallest |P(z)| give the positions;
-          method 3 (matrix pencil): the generalized eigenvalues of Y_2 - lambda Y_1
-            (Eq. 15-17), computed as the eigenvalues of Y_1^+ Y_2 (the rank-a case of
-            Theorem 3).  By the Vandermonde factors of Theorem 3's proof they are
-            conj(z_j) = 1 / z_j, so z_j = 1 / lambda_j.
+          method 3 (matrix pencil, as sFFT-DT3.0 runs it in Sec. 4.1): the SVD
+            Y = U S V^H of the (a + 1) x (a + 1) Toeplitz matrix of Eq. 15; with V_s the
+            right singular vectors of the a largest singular values, V_1 = V_s without its
+            last row and V_2 = V_s without its first row, the eigenvalues of V_1^+ V_2 are
+            the z_j (the matrix pencil of Hua and Sarkar on the signal subspace: Y =
+            U_{a+1} diag(p) U_{a+1}^H, so V_s spans the Vandermonde columns).  The direct
+            pencil of Theorem 3, Y_2 - lambda Y_1 (Eq. 16-17), has eigenvalues
+            conj(z_j) = 1 / z_j (pencil_points, pinned but not used by decode).
           Methods 1 and 3 give points z; each becomes a position by its angle, snapped to
           the nearest candidate i + q B (snap_positions).
   Step 3  values by subspace pursuit on Eq. 18 with the P random-delay measurements: the
@@ -60,7 +64,7 @@ class OneShotOpts:
     c0: float = 4.0
     c1: float = 2.0
     max_iter: int = 8
-    method: int = 2      # Step 2: 1 polynomial roots, 2 enumeration, 3 matrix pencil
+    method: int = 2      # Step 2: 1 polynomial roots, 2 enumeration, 3 matrix pencil (SVD)
 
 
 def check_delays(N: int, a_m: int, delays) -> None:
@@ -159,6 +163,20 @@ def pencil_points(m_row: np.ndarray, a_m: int, a: int) -> np.ndarray:
     return 1.0 / lam
 
 
+def toeplitz_y(m_row: np.ndarray, a_m: int, a: int) -> np.ndarray:
+    """Y of Eq. 15, (a + 1) x (a + 1): Y[r][c] = m_{r-c}; m_row is indexed k + a_m."""
+    return np.array([[m_row[r - c + a_m] for c in range(a + 1)] for r in range(a + 1)])
+
+
+def pencil_svd_points(m_row: np.ndarray, a_m: int, a: int) -> np.ndarray:
+    """Step 2, method 3 as Sec. 4.1 runs it: V_s = the right singular vectors of the a
+    largest singular values of Y (Eq. 15); the eigenvalues of V_1^+ V_2 (V_1: V_s without
+    its last row, V_2: without its first) are the z_j."""
+    _, _, vh = np.linalg.svd(toeplitz_y(m_row, a_m, a))
+    vs = vh.conj().T[:, :a]
+    return np.linalg.eigvals(np.linalg.pinv(vs[:-1]) @ vs[1:])
+
+
 def snap_positions(N: int, B: int, i: int, z: np.ndarray) -> np.ndarray:
     """Positions of the points z (methods 1 and 3): u = ((arg z) N / (2 pi) - i) / B mod L
     is the fractional candidate index; the points take candidates in order of increasing
@@ -251,7 +269,7 @@ def decode(N: int, B: int, K: int, delays, Y: np.ndarray, opts: OneShotOpts) -> 
     for i in np.nonzero(counts)[0]:
         a = int(counts[i])
         if opts.method == 3:
-            pos = snap_positions(N, B, int(i), pencil_points(m[i], a_m, a))
+            pos = snap_positions(N, B, int(i), pencil_svd_points(m[i], a_m, a))
         else:
             try:
                 c = prony_coefficients(m[i], a_m, a)

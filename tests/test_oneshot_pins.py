@@ -165,6 +165,26 @@ def test_pencil_eigenvalues_theorem3(oracle_mod, a):
                                rtol=0, atol=1e-9)
 
 
+@pytest.mark.parametrize("a", [1, 2, 3])
+def test_pencil_svd_points_are_the_tones(oracle_mod, a):
+    """Method 3 as sFFT-DT3.0 runs it (Sec. 4.1): the eigenvalues of V_1^+ V_2 from the right
+    singular vectors of Eq. 15's Y are the generator's z_j (not their conjugates), and Y
+    itself is U diag(p) U^H with U[r][j] = z_j^r, written here from the truth."""
+    p, dl, i, fs = three_tone_bucket(7)
+    vals = [2.0 + 1.0j, -1.5 + 0.5j, 0.7 - 1.1j][:a]
+    if a < 3:
+        p, dl = problem(a, 7, support=fs[:a], values=vals)
+    Y = oracle_mod.bucketize(N, [L], dl, p.x)
+    m = dt.moments(Y, B, 3)
+    z = np.exp(2j * np.pi * np.array(fs[:a]) / N)
+    U = np.stack([z ** r for r in range(a + 1)])
+    np.testing.assert_allclose(dt.toeplitz_y(m[i], 3, a), U @ np.diag(vals) @ U.conj().T,
+                               rtol=0, atol=1e-9)
+    pts = dt.pencil_svd_points(m[i], 3, a)
+    np.testing.assert_allclose(sorted(pts, key=np.angle), sorted(z, key=np.angle),
+                               rtol=0, atol=1e-9)
+
+
 def test_snap_positions_rule():
     """Points take candidates most confident first; a taken candidate sends the point to
     the nearest free one on its own side, and the index wraps modulo L."""
