@@ -133,8 +133,9 @@ typedef struct {
                                  0 (default) = copy every host signal to device memory first */
     int32_t oneshot_method;   /* one-shot decoder, Step 2 (Sec. 3.1): 1 = roots of P(z)
                                  (polynomial method), 2 = enumeration of the L candidates
-                                 (default; 0 means 2), 3 = matrix pencil (Eq. 15-17).  Methods
-                                 1 and 3 snap each root z to the candidate nearest arg(z) */
+                                 (default; 0 means 2), 3 = matrix pencil on the SVD of Eq. 15's
+                                 Toeplitz Y (as sFFT-DT3.0 in Sec. 4.1).  Methods 1 and 3 snap
+                                 each root z to the candidate nearest arg(z) */
     int32_t dft_fma_only;     /* 1 = every DFT axis on the FMA pipes.  0 (default) = in FP32
                                  stages done in one pass, the odd axes with 17 <= P <= 127 (direct
                                  P-point DFTs: a cosine and a sine matrix applied to every

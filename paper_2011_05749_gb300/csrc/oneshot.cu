@@ -12,8 +12,9 @@
 //   DT3  Steps 2-3, one warp per bucket with a > 0 votes.  Step 2 by one of the paper's
 //        three methods: C = M_a^{-1} M_s (Eq. 14), then |P(z)| (Eq. 12) at every candidate
 //        (the lanes split them) and the a smallest (method 2, the default), or the roots of
-//        P(z) (method 1); or the eigenvalues of Y_1^+ Y_2 (Eq. 15-17, method 3), which are
-//        1 / z_j.  Roots are snapped to the bucket's candidates by angle.  Then subspace
+//        P(z) (method 1); or the matrix pencil on the right singular vectors of Eq. 15's
+//        Toeplitz Y (method 3, as Sec. 4.1 runs it), whose eigenvalues are the z_j.  Roots
+//        are snapped to the bucket's candidates by angle.  Then subspace
 //        pursuit over the atoms {f, f + B, f - B} with the P random-delay measurements
 //        (Eq. 18), lane r holding measurement r.
 // The per-bucket arithmetic is FP64 whatever the bins' type (position and value
@@ -440,58 +441,119 @@ __global__ void __launch_bounds__(kSolveThreads) dt_solve_kernel(const __grid_co
         dt_solve_bucket<T>(a, sig, __ldcg(a.ws.nzl + (int64_t)sig * a.pd.sumB + i));
 }
 
-// Step 2, method 3 (Sec. 3.1, Eq. 15-17, Theorem 3) for one bucket, by one lane: Y_1[r][c]
-// = m_{r-c}, Y_2[r][c] = m_{r-c-1} ((a + 1) x a); G = Y_1^+ Y_2 from the normal equations
-// (Y_1^H Y_1) G = Y_1^H Y_2, one column at a time; G's eigenvalues are the roots of its
-// characteristic polynomial, and each is 1 / z_j (the Vandermonde factors of Theorem 3's
-// proof give conj(z_j)); a zero eigenvalue gives z = 1.  A, rhs: scratch (a^2 and a).
+// Eigen-decomposition of the Hermitian n x n matrix G (n <= 4, row stride 4) by cyclic
+// complex Jacobi rotations, as in jacobi_rotate (the phase e^{-i phi} on coordinate q, then
+// the real rotation), with the rotations accumulated into V (V <- V J): G ends diagonal with
+// the eigenvalues, and column k of V is the eigenvector of G[k][k].  G and V live in the
+// warp's shared scratch, which keeps the solve kernel's stack frame small.
+__device__ void hermitian_eigen_vectors(Cd* G, Cd* V, int n)
+{
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) V[r * 4 + c] = cd(r == c ? 1.0 : 0.0, 0.0);
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int p = 0; p < n; ++p) {
+            diag += fabs(G[p * 4 + p].x);
+            for (int q = p + 1; q < n; ++q) off += abs2(G[p * 4 + q]);
+        }
+        if (off <= 1e-30 * diag * diag) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double ag = sqrt(abs2(G[p * 4 + q]));
+                const double ga = G[p * 4 + p].x, gb = G[q * 4 + q].x;
+                if (ag <= 1e-300 || ag <= 1e-18 * (fabs(ga) + fabs(gb))) {
+                    G[p * 4 + q] = G[q * 4 + p] = cd(0, 0);
+                    continue;
+                }
+                const Cd e = {G[p * 4 + q].x / ag, G[p * 4 + q].y / ag};
+                const double zeta = (gb - ga) / (2.0 * ag);
+                const double t = fabs(zeta) > 1e150
+                                     ? 0.5 / zeta
+                                     : (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int r = 0; r < n; ++r) {
+                    if (r == p || r == q) continue;
+                    const Cd grp = G[r * 4 + p], eg = conjd(e) * G[r * 4 + q];
+                    const Cd nrp = {c * grp.x - s * eg.x, c * grp.y - s * eg.y};
+                    const Cd nrq = {s * grp.x + c * eg.x, s * grp.y + c * eg.y};
+                    G[r * 4 + p] = nrp;
+                    G[p * 4 + r] = conjd(nrp);
+                    G[r * 4 + q] = nrq;
+                    G[q * 4 + r] = conjd(nrq);
+                }
+                G[p * 4 + p] = cd(ga - t * ag, 0);
+                G[q * 4 + q] = cd(gb + t * ag, 0);
+                G[p * 4 + q] = G[q * 4 + p] = cd(0, 0);
+                for (int r = 0; r < n; ++r) {
+                    const Cd vp = V[r * 4 + p], vq = conjd(e) * V[r * 4 + q];
+                    V[r * 4 + p] = cd(c * vp.x - s * vq.x, c * vp.y - s * vq.y);
+                    V[r * 4 + q] = cd(s * vp.x + c * vq.x, s * vp.y + c * vq.y);
+                }
+            }
+    }
+}
+
+// Step 2, method 3 as sFFT-DT3.0 runs it (Sec. 4.1) for one bucket, by one lane: Y[r][c] =
+// m_{r-c} ((a + 1) x (a + 1), Eq. 15); its right singular vectors are the eigenvectors of
+// Y^H Y; V_s = those of the a largest eigenvalues; with V_1 = V_s without its last row and
+// V_2 = V_s without its first, the eigenvalues of G = V_1^{-1} V_2 (the roots of its
+// characteristic polynomial) are the z_j (Y = U diag(p) U^H with U[r][j] = z_j^r, so V_s
+// spans U's columns).  A, rhs: scratch (a^2 and a).
 template <typename T>
 __device__ void pencil_points(const typename C2<T>::t* Y, int b, int B, int am, int na,
-                              double invB, Cd* A, Cd* rhs, Cd* z)
+                              double invB, Cd* A, Cd* rhs, Cd* W, Cd* z)
 {
-    Cd m[7];  // m_k at k + na, k = -na .. na
+    // W (shared, 48 entries): m_k at W[k + na] (k = -na .. na), H = Y^H Y at W[8 ..] and its
+    // eigenvectors at W[24 ..] (row stride 4), G = V_1^{-1} V_2 at W[40 ..] (row stride 3)
+    Cd* m = W;
+    Cd* H = W + 8;
+    Cd* V = W + 24;
+    Cd* G = W + 40;
     for (int k = -na; k <= na; ++k) {
         const typename C2<T>::t y = __ldcg(Y + (int64_t)(k + am) * B + b);
         m[k + na] = cd((double)y.x * invB, (double)y.y * invB);
     }
-    auto y1 = [&](int r, int c) { return m[r - c + na]; };
-    auto y2 = [&](int r, int c) { return m[r - c - 1 + na]; };
-    Cd G[3][3];
-    for (int d = 0; d < na; ++d) {
-        // column d: (Y_1^H Y_1) g_d = Y_1^H y2_d (solve_lane overwrites A, so it is rebuilt)
-        for (int u = 0; u < na; ++u) {
+    const int n = na + 1;
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
             Cd h = cd(0, 0);
-            for (int r = 0; r <= na; ++r) h = h + conjd(y1(r, u)) * y2(r, d);
-            rhs[u] = h;
-            for (int v = 0; v < na; ++v) {
-                Cd e = cd(0, 0);
-                for (int r = 0; r <= na; ++r) e = e + conjd(y1(r, u)) * y1(r, v);
-                A[u * na + v] = e;
-            }
+            for (int k = 0; k < n; ++k) h = h + conjd(m[k - r + na]) * m[k - c + na];
+            H[r * 4 + c] = h;
+        }
+    hermitian_eigen_vectors(H, V, n);
+    int idx[4] = {0, 1, 2, 3};
+    for (int i = 1; i < n; ++i)
+        for (int k = i; k > 0 && H[idx[k - 1] * 5].x < H[idx[k] * 5].x; --k) {
+            const int x = idx[k];
+            idx[k] = idx[k - 1];
+            idx[k - 1] = x;
+        }
+    for (int d = 0; d < na; ++d) {
+        for (int u = 0; u < na; ++u) {
+            for (int v = 0; v < na; ++v) A[u * na + v] = V[u * 4 + idx[v]];  // V_1
+            rhs[u] = V[(u + 1) * 4 + idx[d]];                                // V_2, column d
         }
         const bool ok = solve_lane(A, rhs, na);
-        for (int u = 0; u < na; ++u) G[u][d] = ok ? rhs[u] : cd(0, 0);
+        for (int u = 0; u < na; ++u) G[u * 3 + d] = ok ? rhs[u] : cd(0, 0);
     }
     Cd c[3];
     if (na == 1) {
-        c[0] = cd(-G[0][0].x, -G[0][0].y);
+        c[0] = cd(-G[0].x, -G[0].y);
     } else if (na == 2) {
-        const Cd tr = G[0][0] + G[1][1];
+        const Cd tr = G[0] + G[4];
         c[1] = cd(-tr.x, -tr.y);
-        c[0] = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+        c[0] = G[0] * G[4] - G[1] * G[3];
     } else {
-        const Cd tr = G[0][0] + G[1][1] + G[2][2];
+        const Cd tr = G[0] + G[4] + G[8];
         c[2] = cd(-tr.x, -tr.y);
-        c[1] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) + (G[0][0] * G[2][2] - G[0][2] * G[2][0]) +
-               (G[1][1] * G[2][2] - G[1][2] * G[2][1]);
-        const Cd det = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
-                       G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
-                       G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+        c[1] = (G[0] * G[4] - G[1] * G[3]) + (G[0] * G[8] - G[2] * G[6]) +
+               (G[4] * G[8] - G[5] * G[7]);
+        const Cd det = G[0] * (G[4] * G[8] - G[5] * G[7]) -
+                       G[1] * (G[3] * G[8] - G[5] * G[6]) +
+                       G[2] * (G[3] * G[7] - G[4] * G[6]);
         c[0] = cd(-det.x, -det.y);
     }
-    Cd lam[3];
-    poly_roots(c, na, lam);
-    for (int t = 0; t < na; ++t) z[t] = abs2(lam[t]) > 0 ? divd(cd(1, 0), lam[t]) : cd(1, 0);
+    poly_roots(c, na, z);
 }
 
 // Steps 2-3 of one voted bucket by one warp (every lane calls with the same b).
@@ -557,12 +619,13 @@ __device__ __noinline__ void dt_solve_bucket(const DecodeArgs& a, int sig, int b
     if (method == 1 || method == 3) {
         // methods 1 and 3: lane 0 finds the points z_j and snaps them to candidates
         __shared__ int s_pos[kSolveThreads / 32][3];
+        __shared__ Cd s_w[kSolveThreads / 32][48];
         if (lane == 0) {
             Cd z[3];
             if (method == 1)
                 poly_roots(c, na, z);
             else
-                pencil_points<T>(Y, b, B, am, na, invB, A, rhs, z);
+                pencil_points<T>(Y, b, B, am, na, invB, A, rhs, s_w[wib], z);
             snap_positions(z, na, j, B, L, N, s_pos[wib]);
         }
         __syncwarp();
