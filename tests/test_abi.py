@@ -74,7 +74,8 @@ def test_opts_layout_and_defaults_without_gpu():
 
 def test_oneshot_plan_rules_checked_without_gpu():
     """One-shot plans (Sec. 3.1): one stage, K <= B, slots 0 .. 3 a_m - 1 = -a_m .. 2 a_m - 1
-    (mod N), at least 2 a_m random delays; violations fail before any device work."""
+    (mod N), at least 2 a_m random delays, Step 2 method 0 (default) .. 3; violations fail
+    before any device work."""
     import ctypes as ct
     import numpy as np
     from paper_2011_05749_gb300 import _lib
@@ -82,10 +83,10 @@ def test_oneshot_plan_rules_checked_without_gpu():
     N, am = 4096, 3
     good = [(k - am) % N for k in range(3 * am)] + [100, 200, 300, 400, 500, 600, 700]
 
-    def create(f, delays, K=10, a_m=am):
+    def create(f, delays, K=10, a_m=am, method=0):
         o = _lib.Opts()
         lib.sfft_opts_default(ct.byref(o))
-        o.decoder, o.oneshot_am = _lib.DECODER_ONESHOT, a_m
+        o.decoder, o.oneshot_am, o.oneshot_method = _lib.DECODER_ONESHOT, a_m, method
         f = np.ascontiguousarray(f, dtype=np.int64)
         d = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
         h = ct.c_void_p()
@@ -97,6 +98,8 @@ def test_oneshot_plan_rules_checked_without_gpu():
     assert create([16], good[:13]) == inval                           # P = 4 < 2 a_m
     assert create([16], good, K=N // 16 + 1) == inval                  # K > B
     assert create([16], good, a_m=4) == inval                          # a_m > 3
+    assert create([16], good, method=4) == inval                       # Step 2 method 1..3
+    assert create([16], good, method=-1) == inval
 
 
 def test_kay_plan_rules_checked_without_gpu():
