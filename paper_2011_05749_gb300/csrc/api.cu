@@ -435,10 +435,14 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     p->sort_cap = 1;
     while ((size_t)p->sort_cap < nb) p->sort_cap <<= 1;
     {
-        // shared-memory keys of the compaction sort: a power of two within the device limit
+        // shared-memory keys of the compaction sort: a power of two within the device limit,
+        // and no more than both key arrays of 2 K recovered coefficients need, so that two
+        // 1024-thread CTAs share an SM (larger counts sort in the slot's global buffer)
         int cap = 1;
         while ((size_t)cap * 2 * sizeof(uint64_t) <= (size_t)di.max_smem - 1024) cap <<= 1;
-        p->smem_cap = std::min(2 * p->sort_cap, cap);
+        int want = 1;
+        while (want < 2 * K) want <<= 1;
+        p->smem_cap = std::min(std::min(2 * p->sort_cap, cap), std::max(1024, 2 * want));
     }
     // decode workspace, one block carved into arrays
     size_t off = 0;
