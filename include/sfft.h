@@ -217,8 +217,9 @@ int sfft_bucketize(sfft_plan_t plan, const void* x, void* bins, void* stream);
  * of two-pass stages live in one static 16 MiB device array inside the library, held by
  * every GPU that loads it until the process exits; a problem needing more than fits
  * (roughly sum_d B_d * (8 + 2 R * sizeof(complex)) bytes) returns SFFT_ETOOBIG before any
- * device work.  The first call on each device resolves the array's device address (it
- * should come before any stream capture).  All calls share the array and leave their data
+ * device work.  Every call resolves the array's device address on the current device; the
+ * first call on a device also loads the library's device code there, so it should come
+ * before any stream capture.  All calls share the array and leave their data
  * in it: calls that overlap on the GPU race, so the caller must order them.              */
 int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t* f, int32_t n_delays,
                           const int64_t* delays, int32_t precision, int32_t dtype,

@@ -14,15 +14,14 @@
 // to start at zero); calls share the one array, so calls that overlap on the GPU (other
 // streams, other host threads) race and must be ordered by the caller.
 //
-// Device address: in host code the array's name is only a host-side stand-in, so the
-// first call on each device (with that device current) resolves the device address with
-// cudaGetSymbolAddress and caches it; that first call should come before any stream
-// capture.
+// Device address: in host code the array's name is only a host-side stand-in, so every
+// call resolves the device address with cudaGetSymbolAddress, with the caller's device
+// current (cheap next to the launches, and it stays right if the device's context is torn
+// down and made again).  The first call on each device also loads the library's device
+// code there, so it should come before any stream capture.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
-
-#include <mutex>
 
 #include "launch.h"
 #include "pfa_layout.h"
@@ -42,9 +41,6 @@ constexpr size_t kStaticBytes = 16u << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_dev_ptr[kMaxDevices] = {};
-int g_max_smem[kMaxDevices] = {};
 
 // Tables of one call, computed on the device from the description: input sample index and
 // bin of every storage position, and the twiddles of every axis.
@@ -93,28 +89,39 @@ __global__ void static_tables_kernel(const __grid_constant__ PlanDesc pd, int32_
     }
 }
 
+// the array's device address on the current device, and the device's shared-memory limit
+// (applied to the bucketization kernels)
 int device_scratch(void** ptr, int* max_smem)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e);
     if (dev < 0 || dev >= kMaxDevices) return SFFT_EINVAL;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_dev_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return cuda_fail(e);
-        int sm = 0;
-        e = cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e != cudaSuccess) return cuda_fail(e);
-        e = set_bucketize_smem_limit(sm);
-        if (e != cudaSuccess) return cuda_fail(e);
-        g_max_smem[dev] = sm;
-        g_dev_ptr[dev] = p;
-    }
-    *ptr = g_dev_ptr[dev];
-    *max_smem = g_max_smem[dev];
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int sm = 0;
+    e = cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = set_bucketize_smem_limit(sm);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *ptr = p;
+    *max_smem = sm;
     return SFFT_OK;
+}
+
+// The prime-factor maps of a stage's layout must be inverse permutations: position p holds
+// bin j = sum_a k_a crt_a mod B (k_a the p's coordinate on axis a), and bin j sits at
+// sum_a (j mod P_a) S_a.  Checked on the host without allocating; a layout that fails it
+// would store bins in the wrong places.
+bool crt_maps_consistent(const StageDesc& s)
+{
+    for (int32_t pos = 0; pos < s.B; ++pos) {
+        int64_t j = 0;
+        for (int a = 0; a < s.n_axes; ++a) j += (int64_t)((pos / s.ax[a].S) % s.ax[a].P) * s.ax[a].crt;
+        if (bin_to_pos(s, (int32_t)(j % s.B)) != pos) return false;
+    }
+    return true;
 }
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
@@ -178,6 +185,7 @@ extern "C" int sfft_bucketize_static(int64_t N, int32_t n_stages, const int64_t*
         if (!pfa_layout_stage(&s, esz, max_smem, tile_target, &a.pass[d], &pass2[d], &l1, &l2,
                               &n_tw, &two))
             return SFFT_EINVAL;
+        if (!crt_maps_consistent(s)) return SFFT_EINVAL;
         for (int r = 0; r < n_delays; ++r) s.tau[r] = (int32_t)delays[(int64_t)d * n_delays + r];
         s.r0 = s.r1 = -1;
         s.bin_base = bin_base;

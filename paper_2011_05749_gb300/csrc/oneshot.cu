@@ -34,6 +34,11 @@ namespace sfft {
 namespace {
 
 constexpr int kSolveThreads = 256;           // 8 warps, one bucket each
+// per-warp shared scratch of the matrix pencil (pencil_points): moments W[0 .. 6], H at
+// W[8 .. 23], its eigenvectors at W[24 .. 39], G (3 x 3) at W[40 .. 48]; rounded up to a
+// multiple of 4 entries so that every warp's slice starts on a 64-byte boundary
+constexpr int kPencilWords = 52;
+static_assert(40 + 3 * 3 <= kPencilWords, "pencil scratch must hold G for a_m = 3");
 constexpr int kMaxAtoms = 9;                 // 3 a_m
 constexpr int kMaxFit = 6;                   // 2 a_m atoms in a union fit
 
@@ -503,8 +508,9 @@ template <typename T>
 __device__ void pencil_points(const typename C2<T>::t* Y, int b, int B, int am, int na,
                               double invB, Cd* A, Cd* rhs, Cd* W, Cd* z)
 {
-    // W (shared, 48 entries): m_k at W[k + na] (k = -na .. na), H = Y^H Y at W[8 ..] and its
-    // eigenvectors at W[24 ..] (row stride 4), G = V_1^{-1} V_2 at W[40 ..] (row stride 3)
+    // W (shared, kPencilWords entries): m_k at W[k + na] (k = -na .. na), H = Y^H Y at
+    // W[8 ..] and its eigenvectors at W[24 ..] (row stride 4), G = V_1^{-1} V_2 at W[40 ..]
+    // (row stride 3, up to W[48] for na = 3)
     Cd* m = W;
     Cd* H = W + 8;
     Cd* V = W + 24;
@@ -619,7 +625,7 @@ __device__ __noinline__ void dt_solve_bucket(const DecodeArgs& a, int sig, int b
     if (method == 1 || method == 3) {
         // methods 1 and 3: lane 0 finds the points z_j and snaps them to candidates
         __shared__ int s_pos[kSolveThreads / 32][3];
-        __shared__ Cd s_w[kSolveThreads / 32][48];
+        __shared__ Cd s_w[kSolveThreads / 32][kPencilWords];
         if (lane == 0) {
             Cd z[3];
             if (method == 1)

@@ -96,3 +96,26 @@ def test_pageable_signal_is_copied(sfft):
     np.testing.assert_array_equal(hi[:n], di[:n].cpu().numpy())
     np.testing.assert_array_equal(hv[:n], dv[:n].cpu().numpy())
     plan.close()
+
+
+@pytest.mark.parametrize("prec,dtype", [("fp32", "c64"), ("fp64", "c128")])
+def test_host_gather_matches_oracle(sfft, oracle_mod, prec, dtype):
+    """N = 49*50*51, 6 delays (0, 1 and 4 random), K = 100, 20 dB, read in place from
+    page-locked host memory: the FP64 oracle's support bit for bit (its naive-DFT bins and
+    peeling decoder, ML locate) and its values within 1e-5 (FP32) or 1e-12 (FP64)."""
+    p = synth.config_problem("rffast_124950", seed=15)
+    eta = 3e-3 if prec == "fp32" else 1e-6
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x)
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K,
+                            oracle_mod.OracleOpts(noise_var=p.noise_var, locate=1, eta=eta))
+    npdt = np.complex64 if dtype == "c64" else np.complex128
+    plan = sfft.Plan(p.N, p.K, p.f, p.delays, dtype=dtype, precision=prec, locate="ml",
+                     noise_var=p.noise_var, host_gather=True)
+    xh = pinned(p.x, npdt)
+    idx, val, info = (t.cpu().numpy() for t in plan.execute(xh, out=plan.empty_outputs("cuda")))
+    plan.close()
+    n = int(info[0])
+    assert int(info[1]) == ref["status"]
+    np.testing.assert_array_equal(idx[:n], ref["idx"])
+    err = np.linalg.norm(val[:n] - ref["val"]) / np.linalg.norm(ref["val"])
+    assert err <= (1e-5 if prec == "fp32" else 1e-12), err

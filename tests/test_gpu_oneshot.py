@@ -178,3 +178,40 @@ def test_method_out_of_range_rejected(sfft):
     dl = synth.oneshot_delays(N, 3, 7, np.random.default_rng(3))
     with pytest.raises(Exception):
         sfft.Plan(N, 10, (L,), dl, decoder="oneshot", a_m=3, dt_method=4)
+
+
+def packed_problem(N, L, n_buckets, seed, snr_db=None, a_m=3, P=7):
+    """Exactly a_m tones in each of n_buckets random buckets, none elsewhere, so that every
+    voted bucket holds a_m tones and every warp of every solve CTA works on one."""
+    B = N // L
+    rng = np.random.default_rng(seed)
+    dl = synth.oneshot_delays(N, a_m, P, rng)
+    js = rng.choice(B, size=n_buckets, replace=False)
+    sup = np.sort(np.concatenate([j + rng.choice(L, size=a_m, replace=False) * B for j in js]))
+    vals = rng.uniform(1.0, 10.0, sup.size) * np.exp(2j * np.pi * rng.uniform(size=sup.size))
+    p = synth.make_problem(N, (L,), sup.size, seed=seed + 1, delays=dl, support=sup, values=vals,
+                           snr_db=snr_db)
+    return p, dl
+
+
+@pytest.mark.parametrize("snr_db", [None, 30.0])
+def test_pencil_every_warp_three_tones(sfft, oracle_mod, snr_db):
+    """Method 3 (matrix pencil) with a_m = 3 in every bucket the solve kernel takes:
+    N = 2^18, B = 4096, 128 buckets of 3 tones (K = 384), so all 8 warps of each solve CTA
+    build their 3 x 3 pencil in their own shared scratch at once.  FP32 and FP64: the
+    oracle's support and values (1e-5 / 1e-12), exact and at 30 dB, and the same bits on
+    five repeated executions.  (The FP32 vote floor, and the noise at 30 dB, leave out the
+    buckets whose smallest singular value is below them; the oracle leaves out the same.)"""
+    p, dl = packed_problem(1 << 18, 64, 128, 91, snr_db=snr_db)
+    for prec in ("fp64", "fp32"):
+        eta = 3e-3 if prec == "fp32" else 1e-6
+        ref = oracle_decode(oracle_mod, p, dl, 3, eta, method=3)
+        if snr_db is None and prec == "fp64":
+            np.testing.assert_array_equal(ref.idx, p.support)
+        runs = [run_gpu(sfft, p, dl, 3, prec, method=3)[0] for _ in range(5)]
+        check(runs[0], ref, prec)
+        for got in runs[1:]:
+            n = int(runs[0][2][0])
+            assert int(got[2][0]) == n and int(got[2][1]) == int(runs[0][2][1])
+            np.testing.assert_array_equal(got[0][:n], runs[0][0][:n])
+            np.testing.assert_array_equal(got[1][:n].view(np.uint8), runs[0][1][:n].view(np.uint8))
