@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=20000.0,
                     help="mean Poisson arrival rate of the serving measurement (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--mix-seconds", type=float, default=10.0,
+                    help="length of the serving-mix Poisson stream")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large single-signal measurement (N = 511*512*513)")
     ap.add_argument("--only", choices=["large", "oneshot", "locate", "noise", "dsfft", "mix",
@@ -537,10 +539,11 @@ def measure_batched_mix(sfft, n_signals=4096, steps=3, warmup=1, plain_per_size=
     call, N drawn from {9660, 124950 = 49*50*51, 2097024 = 127*128*129} (three stages, 6
     delays: 0, 1 and 4 random), K uniform in [10, 500], SNR uniform in [10, 40] dB, |xhat|
     ~ U[1,10].  Each signal's noise variance is estimated from its own bins (noise_auto), so
-    one plan per N serves every SNR.  The batch is ordered by N (one launch set per plan).
-    Beside it: the plain FP64 path, one signal per sfft_execute, on plain_per_size signals
-    of each N; the ratio is the batched rate over the plain rate of the same mix.
-    Inputs: 8 distinct signals per N, each stored n_signals / 24 times."""
+    one plan per N serves every SNR.  The batch is timed in a shuffled order (the library
+    groups each plan's signals wherever they sit: one launch set per plan) and, beside it,
+    ordered by N.  Beside them: the plain FP64 path, one signal per sfft_execute, on
+    plain_per_size signals of each N; the ratio is the batched rate over the plain rate of
+    the same mix.  Inputs: 8 distinct signals per N, each stored n_signals / 24 times."""
     import torch
     sizes = [(9660, (20, 21, 23)), (124950, (49, 50, 51)), (2097024, (127, 128, 129))]
     rng = np.random.default_rng(2024)
@@ -569,16 +572,28 @@ def measure_batched_mix(sfft, n_signals=4096, steps=3, warmup=1, plain_per_size=
     idx = [torch.zeros(500, dtype=torch.int64, device="cuda") for _ in range(n)]
     val = [torch.zeros(500, dtype=torch.complex64, device="cuda") for _ in range(n)]
     infos = torch.zeros((n, 4), dtype=torch.int32, device="cuda")
-    for _ in range(warmup):
-        sfft.execute_batch(plan_of, xs, (idx, val, infos))
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        sfft.execute_batch(plan_of, xs, (idx, val, infos))
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+    perm = np.random.default_rng(77).permutation(n)
+
+    def timed(order):
+        po = [plan_of[i] for i in order]
+        xo = [xs[i] for i in order]
+        io = [idx[i] for i in order]
+        vo = [val[i] for i in order]
+        inf_o = torch.zeros((n, 4), dtype=torch.int32, device="cuda")
+        for _ in range(warmup):
+            sfft.execute_batch(po, xo, (io, vo, inf_o))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            sfft.execute_batch(po, xo, (io, vo, inf_o))
+        e1.record()
+        torch.cuda.synchronize()
+        infos[torch.from_numpy(np.asarray(order)).cuda()] = inf_o
+        return e0.elapsed_time(e1) / steps
+
+    ms_sorted = timed(np.arange(n))
+    ms = timed(perm)
     inf = infos.cpu().numpy()
     k = 0
     plain_s = 0.0
@@ -608,7 +623,8 @@ def measure_batched_mix(sfft, n_signals=4096, steps=3, warmup=1, plain_per_size=
         plan.close()
     batched = n * 1e3 / ms
     plain = len(sizes) / plain_s  # signals/s over the same mix, one per call
-    out.update({"signals_per_s": batched, "ms_per_batch": ms,
+    out.update({"signals_per_s": batched, "ms_per_batch": ms, "order": "shuffled",
+                "sorted_by_n": {"signals_per_s": n * 1e3 / ms_sorted, "ms_per_batch": ms_sorted},
                 "plain_fp64_signals_per_s": plain, "speedup_vs_plain_fp64": batched / plain})
     return out
 
@@ -621,7 +637,7 @@ def measure_serving(sfft, plan, signals, rate, seconds, seed):
     n = max(1, int(rate * seconds))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
     srv = sfft.Server(hbm_budget=16 << 30, max_slots=16)
-    # warm-up burst: the server creates its worker workspaces on first use
+    srv.reserve(plan, 16)
     warm = [srv.submit(plan, signals[i % len(signals)], plan.empty_outputs())
             for i in range(16 * 32)]
     srv.drain()
@@ -681,8 +697,10 @@ def measure_serving_mix(sfft, rate=20000.0, seconds=1.0, seed=4):
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
     which = rng.integers(0, len(sizes), size=n)
     srv = sfft.Server(hbm_budget=120 << 30, max_slots=16)
+    for plan in plans:  # every plan's workspaces before the stream (none made mid-stream)
+        srv.reserve(plan, 16)
     warm = []
-    for j, plan in enumerate(plans):  # the server creates its worker workspaces on first use
+    for j, plan in enumerate(plans):
         warm += [srv.submit(plan, sigs[j][i % 8], plan.empty_outputs()) for i in range(64)]
     srv.drain()
     del warm
@@ -925,7 +943,7 @@ def run_gpu(args):
         mix = {"error": repr(exc)[:200]}
     serving_mix = None
     try:
-        serving_mix = measure_serving_mix(sfft, args.serve_rate, args.serve_seconds)
+        serving_mix = measure_serving_mix(sfft, args.serve_rate, args.mix_seconds)
     except Exception as exc:  # report, never fall back
         serving_mix = {"error": repr(exc)[:200]}
 
@@ -1029,7 +1047,7 @@ def run_only(args):
     elif args.only == "mix":
         out = measure_batched_mix(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     elif args.only == "serve":
-        out = measure_serving_mix(sfft, args.serve_rate, args.serve_seconds)
+        out = measure_serving_mix(sfft, args.serve_rate, args.mix_seconds)
     elif args.only == "dft":
         out = measure_dft_paths(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     else:

@@ -141,6 +141,13 @@ typedef struct {
                                  P-point DFTs: a cosine and a sine matrix applied to every
                                  sub-DFT) run on the tensor cores as 3-term split TF32 products,
                                  with FP32-level accuracy */
+    int32_t peel_atomic;      /* peeling subtraction (Sec. 3.2 subproblem 3, Eq. 20).  0 (default):
+                                 every accepted frequency's subtraction is queued on the bins it
+                                 aliases into and applied in increasing order of frequency, each
+                                 delay's sum compensated (TwoSum), so the results are the same
+                                 bits on every run.  1 = subtract with unordered float atomics
+                                 on the bins as frequencies are accepted (results may differ in
+                                 the last bits from run to run) */
 } sfft_opts;
 
 /* Fill *opts with the defaults above. */
@@ -249,10 +256,19 @@ int sfft_plan_set_profiling(sfft_plan_t plan, int enable);
 int sfft_plan_profile(sfft_plan_t plan, double* ms, int64_t* launches, int64_t* calls, int reset);
 
 /* Serving: continuous batching of requests of any plans on one GPU.  A host thread
- * admits requests while their workspace fits hbm_budget bytes and fewer than max_slots
- * are in flight, launches each admitted group on its own stream (so groups overlap on
- * the device), and retires them as their events complete.                                */
+ * admits queued requests onto idle workspaces of their plan while fewer than max_slots
+ * groups are in flight, launches each admitted group (up to 32 requests of one plan) on
+ * its workspace's stream (so groups overlap on the device), and a host function at the
+ * end of each group's stream work retires it.  Workspaces fit in hbm_budget bytes.       */
 int sfft_server_create(sfft_server_t* out, size_t hbm_budget, int32_t max_slots);
+/* Create up to n_workspaces (at most max_slots) workspaces for requests of `plan` now,
+ * within the memory budget: clones of the plan sized for a launch group of 32 requests,
+ * each with its own stream.  The scheduler only reuses workspaces, so once they exist no
+ * request waits for an allocation; a plan's first sfft_submit reserves max_slots
+ * workspaces itself if none exist.  Idle workspaces of other plans with no queued
+ * request are freed when the budget is full.  Synchronises the device (plan creation).
+ * Errors: SFFT_EINVAL, SFFT_EADMIT (not even one workspace fits), SFFT_ENOMEM, SFFT_ECUDA. */
+int sfft_server_reserve(sfft_server_t srv, sfft_plan_t plan, int32_t n_workspaces);
 /* Queue one request (device pointers, as sfft_execute).  The buffers must stay valid until
  * sfft_poll reports a final status.  *ticket identifies it.  DSFFT plans (host-driven
  * layer search) are refused with SFFT_EINVAL.                                             */

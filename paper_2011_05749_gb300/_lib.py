@@ -52,7 +52,8 @@ class Opts(ctypes.Structure):
                 ("decode_ctas", ctypes.c_int32), ("decoder", ctypes.c_int32),
                 ("oneshot_am", ctypes.c_int32), ("kay_m", ctypes.c_int32),
                 ("noise_auto", ctypes.c_int32), ("host_gather", ctypes.c_int32),
-                ("oneshot_method", ctypes.c_int32), ("dft_fma_only", ctypes.c_int32)]
+                ("oneshot_method", ctypes.c_int32), ("dft_fma_only", ctypes.c_int32),
+                ("peel_atomic", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -75,6 +76,7 @@ EXPORTS = {
     "sfft_plan_profile": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int]),
     "sfft_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t,
                                           ctypes.c_int32]),
+    "sfft_server_reserve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "sfft_submit": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.POINTER(ctypes.c_uint64)]),
     "sfft_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64,
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),

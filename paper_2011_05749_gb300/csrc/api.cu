@@ -258,6 +258,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     pd.mode = o.decoder == SFFT_DECODER_ONESHOT ? 1 : 0;
     pd.kay_m = o.locate == SFFT_LOCATE_KAY ? o.kay_m : 0;
     pd.noise_auto = o.noise_auto;
+    pd.peel_atomic = o.peel_atomic ? 1 : 0;
     {
         // median of Gamma(R, 1): CDF(x) = 1 - e^{-x} sum_{k<R} x^k / k! = 1/2, by Newton's
         // method from x = R - 1/3 (the density x^{R-1} e^{-x} / (R-1)! is the derivative)
@@ -465,6 +466,11 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     const size_t o_ctr = carve(4 * (size_t)p->ctr_stride * mb);
     const size_t o_sv = pd.mode == 1 ? carve(8 * (nb * pd.am + 1) * mb) : 0;
     const size_t o_s2 = pd.noise_auto ? carve(8 * mb) : 0;
+    // peeling's per-bin subtraction lists: heads, and D entries per bin (each bin becomes a
+    // candidate at most once, and an accepted candidate queues at most one entry per stage)
+    const bool lists = pd.mode == 0;
+    const size_t o_sh = lists ? carve(4 * nb * mb) : 0;
+    const size_t o_se = lists ? carve(8 * (size_t)n_stages * nb * mb) : 0;
     p->dec_bytes = off;
     p->ctr_bytes_per_sig = 4 * (size_t)p->ctr_stride;
 
@@ -479,10 +485,10 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     dmalloc(&p->d_bins, ybytes);
     if (p->need_pass2) dmalloc(&p->d_scratch, ybytes);
     dmalloc(&p->d_dec, p->dec_bytes);
-    dmalloc((void**)&p->d_ptrs, 3 * sizeof(void*) * mb);
+    dmalloc((void**)&p->d_ptrs, 4 * sizeof(void*) * mb);
     dmalloc((void**)&p->d_sortbuf, 2 * sizeof(uint64_t) * (size_t)p->sort_cap * mb);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        e = cudaHostAlloc((void**)&p->h_ptrs[i], 3 * sizeof(void*) * mb, cudaHostAllocDefault);
+        e = cudaHostAlloc((void**)&p->h_ptrs[i], 4 * sizeof(void*) * mb, cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ptr_ev[i], cudaEventDisableTiming);
     }
     int32_t* d_twP = nullptr;
@@ -521,6 +527,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     w.ctr = (int32_t*)(base + o_ctr);
     w.sv = pd.mode == 1 ? (double*)(base + o_sv) : nullptr;
     w.sig2 = pd.noise_auto ? (double*)(base + o_s2) : nullptr;
+    w.sub_head = lists ? (int32_t*)(base + o_sh) : nullptr;
+    w.sub_ent = lists ? (int2*)(base + o_se) : nullptr;
     p->footprint = 4 * 3 * h_nidx.size() + p->esz * tw_P.size() + ybytes * (p->need_pass2 ? 2 : 1) +
                    p->dec_bytes + 2 * sizeof(uint64_t) * (size_t)p->sort_cap * mb;
     p->decode_occ = decode_occupancy(p->prec, 512);
@@ -606,18 +614,23 @@ static DecodeWs ws_at(const sfft_plan_s* p, int slot0)
     w.ctr += (size_t)slot0 * p->ctr_stride;
     if (w.sv) w.sv += (size_t)slot0 * ((size_t)p->pd.sumB * p->pd.am + 1);
     if (w.sig2) w.sig2 += slot0;
+    if (w.sub_head) {
+        w.sub_head += so;
+        w.sub_ent += so * p->pd.D;
+    }
     return w;
 }
 
 // Enqueue the whole path for n signals of one plan in workspace slots [slot0, slot0 + n)
 // (slot0 + n <= max_batch).  For n > 1 the signal and output pointers come from device
-// tables d_xs / d_idx / d_val; for n == 1 from x0 / idx0 / val0.  The decode counters of
-// the slots are zero on entry (plan creation zeroes them, every compaction re-zeroes
-// them after reading).
+// tables d_xs / d_idx / d_val; for n == 1 from x0 / idx0 / val0.  Info rows: signal i's at
+// d_rows[i] when d_rows is given, else at infos + 4 i.  The decode counters of the slots
+// are zero on entry (plan creation zeroes them, every compaction re-zeroes them after
+// reading).
 int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
               int64_t* idx0, void* val0, int64_t* const* d_idx, void* const* d_val,
               int32_t* infos, const void* bins_in, cudaStream_t st, int slot0 = 0,
-              bool x_sys = false)
+              bool x_sys = false, int32_t* const* d_rows = nullptr)
 {
     PlanDesc& pd = p->pd;
     void* bins = (unsigned char*)p->d_bins + (size_t)slot0 * pd.y_per_sig * p->esz;
@@ -701,6 +714,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     ca.out_idx = d_idx;
     ca.out_val = d_val;
     ca.infos = infos;
+    ca.info_rows = d_rows;
     ca.idx0 = idx0;
     ca.val0 = val0;
     {
@@ -804,7 +818,7 @@ extern "C" int sfft_execute(sfft_plan_t p, const void* x, int64_t* out_idx, void
 namespace sfft {
 
 static int fill_ptr_table(sfft_plan_s* p, int m, const void* const* xs, int64_t* const* idx,
-                          void* const* val, cudaStream_t st)
+                          void* const* val, int32_t* const* rows, cudaStream_t st)
 {
     const int slot = p->ptr_slot;
     p->ptr_slot ^= 1;
@@ -815,8 +829,9 @@ static int fill_ptr_table(sfft_plan_s* p, int m, const void* const* xs, int64_t*
         h[i] = (void*)xs[i];
         h[mb + i] = (void*)idx[i];
         h[2 * mb + i] = val[i];
+        h[3 * mb + i] = rows ? (void*)rows[i] : nullptr;
     }
-    CK(cudaMemcpyAsync(p->d_ptrs, h, 3 * sizeof(void*) * mb, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->d_ptrs, h, 4 * sizeof(void*) * mb, cudaMemcpyHostToDevice, st));
     CK(cudaEventRecord(p->ptr_ev[slot], st));
     return SFFT_OK;
 }
@@ -836,20 +851,20 @@ static int ensure_aux(sfft_plan_s* p)
 // next one's bucketization, measured slower: the kernels contend and the smaller launches
 // leave longer wave tails.)
 static int execute_group_device(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
-                                void* const* val, int32_t* infos, cudaStream_t st)
+                                void* const* val, int32_t* const* rows, cudaStream_t st)
 {
     const size_t mb = (size_t)p->max_batch;
     for (int c0 = 0; c0 < n; c0 += p->max_batch) {
         const int m = std::min(p->max_batch, n - c0);
         int rc;
         if (m == 1) {
-            rc = run_chunk(p, 1, xs[c0], nullptr, idx[c0], val[c0], nullptr, nullptr, infos + 4 * c0,
+            rc = run_chunk(p, 1, xs[c0], nullptr, idx[c0], val[c0], nullptr, nullptr, rows[c0],
                            nullptr, st);
         } else {
-            if ((rc = fill_ptr_table(p, m, xs + c0, idx + c0, val + c0, st))) return rc;
+            if ((rc = fill_ptr_table(p, m, xs + c0, idx + c0, val + c0, rows + c0, st))) return rc;
             rc = run_chunk(p, m, nullptr, (const void* const*)p->d_ptrs, nullptr, nullptr,
                            (int64_t* const*)(p->d_ptrs + mb), (void* const*)(p->d_ptrs + 2 * mb),
-                           infos + 4 * c0, nullptr, st);
+                           nullptr, nullptr, st, 0, false, (int32_t* const*)(p->d_ptrs + 3 * mb));
         }
         if (rc) return rc;
     }
@@ -860,7 +875,7 @@ static int execute_group_device(sfft_plan_s* p, int n, const void* const* xs, in
 // that alternate between two streams, so the copies of one sub-batch overlap the kernels
 // of the other; the call returns when every output is in host memory.
 static int execute_group_host(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
-                              void* const* val, int32_t* infos, cudaStream_t st)
+                              void* const* val, int32_t* const* rows, cudaStream_t st)
 {
     const size_t mb = (size_t)p->max_batch;
     const size_t xb = (size_t)p->pd.N * p->xesz;
@@ -883,7 +898,7 @@ static int execute_group_host(sfft_plan_s* p, int n, const void* const* xs, int6
     CK(cudaEventRecord(p->aux_ev, st));
     CK(cudaStreamWaitEvent(p->aux[0], p->aux_ev, 0));
     CK(cudaStreamWaitEvent(p->aux[1], p->aux_ev, 0));
-    int rc = fill_ptr_table(p, (int)mb, sx.data(), si.data(), sv.data(), p->aux[0]);
+    int rc = fill_ptr_table(p, (int)mb, sx.data(), si.data(), sv.data(), nullptr, p->aux[0]);
     if (rc) return rc;
     CK(cudaEventRecord(p->aux_ev, p->aux[0]));
     CK(cudaStreamWaitEvent(p->aux[1], p->aux_ev, 0));
@@ -908,7 +923,15 @@ static int execute_group_host(sfft_plan_s* p, int n, const void* const* xs, int6
                 CK(cudaMemcpyAsync(idx[c0 + i], si[i], (size_t)p->pd.K * 8, cudaMemcpyDeviceToHost, ss));
                 CK(cudaMemcpyAsync(val[c0 + i], sv[i], (size_t)p->pd.K * p->xesz, cudaMemcpyDeviceToHost, ss));
             }
-            CK(cudaMemcpyAsync(infos + 4 * (c0 + s0), dinf + 4 * s0, 16 * (size_t)ms, cudaMemcpyDeviceToHost, ss));
+            // info rows: one copy when the caller's rows are consecutive, else one per row
+            bool consecutive = true;
+            for (int i = s0 + 1; i < s1; ++i) consecutive &= rows[c0 + i] == rows[c0 + s0] + 4 * (i - s0);
+            if (consecutive) {
+                CK(cudaMemcpyAsync(rows[c0 + s0], dinf + 4 * s0, 16 * (size_t)ms, cudaMemcpyDeviceToHost, ss));
+            } else {
+                for (int i = s0; i < s1; ++i)
+                    CK(cudaMemcpyAsync(rows[c0 + i], dinf + 4 * i, 16, cudaMemcpyDeviceToHost, ss));
+            }
         }
         // the staging buffers are reused by the next launch group
         CK(cudaStreamSynchronize(p->aux[0]));
@@ -917,18 +940,19 @@ static int execute_group_host(sfft_plan_s* p, int n, const void* const* xs, int6
     return SFFT_OK;
 }
 
+// n signals of one plan; rows[i] is signal i's info row (int32[4])
 int execute_group(sfft_plan_s* p, int n, const void* const* xs, int64_t* const* idx,
-                  void* const* val, int32_t* infos, cudaStream_t st, bool host = false)
+                  void* const* val, int32_t* const* rows, cudaStream_t st, bool host = false)
 {
     if (!p->layers.empty()) {  // DSFFT: each signal searches its own layers
         for (int i = 0; i < n; ++i) {
-            const int rc = sfft_execute(p, xs[i], idx[i], val[i], infos + 4 * i, st);
+            const int rc = sfft_execute(p, xs[i], idx[i], val[i], rows[i], st);
             if (rc) return rc;
         }
         return SFFT_OK;
     }
-    return host ? execute_group_host(p, n, xs, idx, val, infos, st)
-                : execute_group_device(p, n, xs, idx, val, infos, st);
+    return host ? execute_group_host(p, n, xs, idx, val, rows, st)
+                : execute_group_device(p, n, xs, idx, val, rows, st);
 }
 }  // namespace sfft
 
@@ -947,7 +971,8 @@ extern "C" int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const voi
             return SFFT_EINVAL;
     if (is_host_ptr(infos) != host) return SFFT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    // group signals by plan, keep first-seen order of plans
+    // group signals by plan (first-seen order of plans); a group need not be consecutive in
+    // the batch: each signal's info row is passed by pointer
     std::vector<char> done(n, 0);
     for (int i = 0; i < n; ++i) {
         if (done[i]) continue;
@@ -955,30 +980,18 @@ extern "C" int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const voi
         std::vector<const void*> gx;
         std::vector<int64_t*> gi;
         std::vector<void*> gv;
-        std::vector<int> who;
+        std::vector<int32_t*> gr;
         for (int k = i; k < n; ++k)
             if (!done[k] && plans[k] == p) {
                 done[k] = 1;
                 gx.push_back(xs[k]);
                 gi.push_back(idx[k]);
                 gv.push_back(val[k]);
-                who.push_back(k);
+                gr.push_back(infos + 4 * (size_t)k);
             }
-        // info rows are written contiguously: a group that is a run of consecutive signals
-        // goes as one; otherwise signal by signal
-        bool run = true;
-        for (size_t q = 0; q < who.size(); ++q)
-            if (who[q] != who[0] + (int)q) run = false;
-        if (run) {
-            int rc = execute_group(p, (int)who.size(), gx.data(), gi.data(), gv.data(),
-                                   infos + 4 * who[0], st, host);
-            if (rc) return rc;
-        } else {
-            for (size_t q = 0; q < who.size(); ++q) {
-                int rc = execute_group(p, 1, &gx[q], &gi[q], &gv[q], infos + 4 * who[q], st, host);
-                if (rc) return rc;
-            }
-        }
+        const int rc = execute_group(p, (int)gx.size(), gx.data(), gi.data(), gv.data(), gr.data(),
+                                     st, host);
+        if (rc) return rc;
     }
     return SFFT_OK;
 }

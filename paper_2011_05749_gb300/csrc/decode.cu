@@ -5,10 +5,14 @@
 // flight, then locate/fit of the tile's non-zero bins.  The later rounds touch O(K) bins and
 // run in peel_kernel, one group of G CTAs per signal:
 //   P   every candidate frequency f not already taken (earlier round, or a lower stage in
-//       this round): recorded, and B_e v a_r(f) subtracted from bin f mod B_e of every
-//       stage e and delay r where that bin is still open (atomics; resolved bins are never
-//       read again); the bins that change are queued;
-//   D1  every queued bin: energy sum_r |Y_r|^2 against T0 -> zero-ton, else non-zero;
+//       this round): recorded, and the subtraction of B_e v a_r(f) from bin f mod B_e of
+//       every stage e and delay r where that bin is still open (resolved bins are never
+//       read again) appended to that bin's list; the bins that change are queued;
+//   D1  every queued bin: its listed subtractions applied in increasing order of f, each
+//       delay's sum compensated (TwoSum), so the result does not depend on the order in
+//       which the candidates were accepted; then the energy sum_r |Y_r|^2 against T0 ->
+//       zero-ton, else non-zero.  (peel_atomic plans subtract in P instead, with unordered
+//       float atomics on the bins.)
 //   D2  every non-zero bin: location (ARG phase or ML candidate search), least-squares
 //       value v and residual rho; rho <= T1 -> single-ton candidate (the bin is resolved).
 // Phases are separated by a group barrier (a bounded spin when G > 1, so a lost CTA turns
@@ -419,9 +423,25 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     const int R = pd.R;
     // only open bins are updated: a resolved bin (zero-ton, or single-ton -- f's own bin
     // among them) is never read again, so its value no longer matters
+    if (!pd.peel_atomic) {
+        // the subtraction is queued on the bin's list and applied in D1 (at most D entries
+        // per accepted candidate, each bin a candidate at most once: D sumB entries)
+        const int cap = D * pd.sumB;
+#pragma unroll
+        for (int e = 0; e < kMaxStages; ++e) {
+            if (e >= D || !open[e]) continue;
+            const int sl = atomicAdd(ctr + kCtrSub, 1);
+            if (sl >= cap) {
+                atomicExch(ctr + kCtrErr, 1);
+                continue;
+            }
+            const int prev = atomicExch(w.sub_head + be[e], sl);
+            __stcg(w.sub_ent + sl, int2{c, prev});
+        }
+    }
 #pragma unroll
     for (int e = 0; e < kMaxStages; ++e) {
-        if (e >= D || !open[e]) continue;
+        if (e >= D || !open[e] || !pd.peel_atomic) continue;
         const StageDesc& se = pd.st[e];
         const T Bv = (T)se.B;
         V* Yb = Y + se.y_off + (be[e] - se.bin_base);
@@ -468,6 +488,90 @@ __device__ __forceinline__ bool bin_is_zero(const PlanDesc& pd, const typename C
     return below(E, thr[d].T0f, thr[d].T0);
 }
 
+// s = a + b and the rounding error e of that sum, a + b = s + e exactly (Knuth's TwoSum)
+template <typename T>
+__device__ __forceinline__ T two_sum(T a, T b, T* e)
+{
+    const T s = a + b;
+    const T bb = s - a;
+    *e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+// D1 of one bin with ordered peeling: apply the bin's listed subtractions (Eq. 20) in
+// increasing order of frequency f -- each delay's y_r - sum_f B v_f a_r(f) summed with
+// TwoSum and its error terms added back at the end -- store the bin, clear its list, and
+// test its energy against T0.  The order and the arithmetic depend only on the set of
+// listed frequencies, so the bits do not depend on which CTA accepted what first.
+template <typename T>
+__device__ bool apply_and_test(const DecodeArgs& a, const DecodeWs& w, typename C2<T>::t* Y, int b,
+                               const Thr* thr)
+{
+    using V = typename C2<T>::t;
+    const PlanDesc& pd = a.pd;
+    const int d = stage_of(pd, b);
+    const StageDesc& st = pd.st[d];
+    V* Yb = Y + st.y_off + (b - st.bin_base);
+    V y[kMaxDelays], cmp[kMaxDelays];
+#pragma unroll
+    for (int r = 0; r < kMaxDelays; ++r) {
+        cmp[r] = V{0, 0};
+        if (r < pd.R) y[r] = __ldcg(Yb + (int64_t)r * st.B);
+    }
+    const int head = __ldcg(w.sub_head + b);
+    if (head >= 0) {
+        __stcg(w.sub_head + b, -1);
+        const T Bv = (T)st.B;
+        const V* cv = reinterpret_cast<const V*>(w.cv);
+        int64_t last = -1;
+        while (true) {
+            // the listed subtraction with the smallest frequency above the last one applied
+            int64_t fmin = INT64_MAX;
+            int cmin = -1;
+            for (int e = head; e >= 0;) {
+                const int2 en = __ldcg(w.sub_ent + e);
+                const int64_t f = (int64_t)__ldcg((const long long*)w.cf + en.x);
+                if (f > last && f < fmin) {
+                    fmin = f;
+                    cmin = en.x;
+                }
+                e = en.y;
+            }
+            if (cmin < 0) break;
+            last = fmin;
+            const V v = __ldcg(cv + cmin);
+            V ar[kMaxDelays];
+#pragma unroll
+            for (int r = 0; r < kMaxDelays; ++r)
+                if (r < pd.R) ar[r] = delay_phasor<T>(a, fmin, st.tau[r]);
+#pragma unroll
+            for (int r = 0; r < kMaxDelays; ++r) {
+                if (r < pd.R) {
+                    const T tx = Bv * (v.x * ar[r].x - v.y * ar[r].y);
+                    const T ty = Bv * (v.x * ar[r].y + v.y * ar[r].x);
+                    T ex, ey;
+                    y[r].x = two_sum<T>(y[r].x, -tx, &ex);
+                    y[r].y = two_sum<T>(y[r].y, -ty, &ey);
+                    cmp[r].x += ex;
+                    cmp[r].y += ey;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kMaxDelays; ++r) {
+            if (r < pd.R) {
+                y[r] = V{y[r].x + cmp[r].x, y[r].y + cmp[r].y};
+                __stcg(Yb + (int64_t)r * st.B, y[r]);
+            }
+        }
+    }
+    T E = 0;
+#pragma unroll
+    for (int r = 0; r < kMaxDelays; ++r)
+        if (r < pd.R) E += y[r].x * y[r].x + y[r].y * y[r].y;
+    return below(E, thr[d].T0f, thr[d].T0);
+}
+
 template <typename T>
 __device__ __forceinline__ DecodeWs slot_ws(const DecodeArgs& a, int sig)
 {
@@ -486,6 +590,10 @@ __device__ __forceinline__ DecodeWs slot_ws(const DecodeArgs& a, int sig)
     w.rec_f += so;
     w.rec_v = reinterpret_cast<V*>(w.rec_v) + so;
     w.ctr += (int64_t)sig * a.ctr_stride;
+    if (w.sub_head) {
+        w.sub_head += so;
+        w.sub_ent += so * a.pd.D;
+    }
     return w;
 }
 
@@ -586,6 +694,7 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
             if (bu >= b1) continue;
             __stcg((long long*)w.cand + bu, -1ll);
             __stcg(w.dirty + bu, 0u);
+            if (w.sub_head) __stcg(w.sub_head + bu, -1);
             __stcg(w.state + bu, (uint8_t)(z[u] ? 1 : 0));
             if (z[u])
                 atomicAdd(&s_res, 1);
@@ -648,7 +757,9 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
         for (int i = wt; i < n_next; i += nw) {
             const int b = __ldcg(act + i);
             __stcg(w.dirty + b, 0u);
-            if (bin_is_zero<T>(pd, Y, b, s_thr)) {
+            const bool zero = pd.peel_atomic ? bin_is_zero<T>(pd, Y, b, s_thr)
+                                             : apply_and_test<T>(a, w, Y, b, s_thr);
+            if (zero) {
                 __stcg(w.state + b, (uint8_t)1);
                 atomicAdd(ctr + kCtrResolved, 1);
             } else {
@@ -763,7 +874,7 @@ __global__ void __launch_bounds__(1024) compact_kernel(const __grid_constant__ C
         ov[i] = XV{(XS)v.x, (XS)v.y};
     }
     if (threadIdx.x == 0) {
-        int32_t* info = a.infos + 4 * sig;
+        int32_t* info = a.info_rows ? a.info_rows[sig] : a.infos + 4 * sig;
         const int err = ldv(ctr + kCtrErr);
         const int resolved = ldv(ctr + kCtrResolved);
         info[0] = cnt;

@@ -53,7 +53,8 @@ struct CompactArgs {
     void* const* out_val;
     int64_t* idx0;              // the outputs when out_idx == nullptr (one signal)
     void* val0;
-    int32_t* infos;             // int32[4 * n_sig]
+    int32_t* infos;             // int32[4 * n_sig], when info_rows == nullptr
+    int32_t* const* info_rows;  // device array of n_sig pointers to int32[4] rows, or nullptr
 };
 
 // precision: 0 = double arithmetic, 1 = float; xdouble: input/output complex128

@@ -86,7 +86,9 @@ struct PlanDesc {
     double sp_tol2;          // one-shot: residual tolerance of the subspace pursuit
     double gmed;             // median of Gamma(R, 1), for the sigma^2 estimate
     int32_t noise_auto;      // 1: thresholds from each signal's estimated sigma^2
-    int32_t pad2;
+    int32_t peel_atomic;     // 1: peeling subtracts with unordered atomics on the bins;
+                             // 0: per-bin subtraction lists applied in frequency order with
+                             //    compensated sums (deterministic)
     StageDesc st[kMaxStages];
 };
 
@@ -195,6 +197,8 @@ struct DecodeWs {
     int32_t* ctr;        // counters, see Ctr
     double* sv;          // one-shot: sumB * a_m singular values, then the vote threshold
     double* sig2;        // noise_auto: the signal's estimated sigma^2 (one per slot)
+    int32_t* sub_head;   // peeling: head of the bin's list of pending subtractions, -1 none
+    int2* sub_ent;       // peeling: list entries {candidate index, next entry} (D sumB per slot)
 };
 
 // the two thresholds of a stage for one signal (Sec. 3.2 subproblem 1), in both types
@@ -213,7 +217,8 @@ enum Ctr : int {
     kCtrBarCount = 5,   // group barrier arrivals
     kCtrBarGen = 6,     // group barrier generation
     kCtrDtList = 7,     // one-shot decoder: buckets listed for the FP64 work (in nzl)
-    kCtrRoundBase = 8,  // per round r (1-based): [3 r + 0] next-list size, [+1] non-zero
+    kCtrSub = 8,        // peeling: subtraction-list entries used (all rounds)
+    kCtrRoundBase = 9,  // per round r (1-based): [3 r + 0] next-list size, [+1] non-zero
                         // bins, [+2] single-ton candidates
 };
 constexpr int ctr_words(int max_rounds) { return kCtrRoundBase + 3 * (max_rounds + 2); }

@@ -36,7 +36,8 @@ struct sfft_plan_s {
     size_t ctr_bytes_per_sig = 0;
     uint64_t* d_sortbuf = nullptr;
     int32_t sort_cap = 1, smem_cap = 1;
-    // batch pointer tables: device copy + two pinned host slots
+    // batch pointer tables (signals, outputs, info rows: 4 x max_batch pointers): device
+    // copy + two pinned host slots
     void** d_ptrs = nullptr;
     void** h_ptrs[2] = {nullptr, nullptr};
     cudaEvent_t ptr_ev[2] = {nullptr, nullptr};

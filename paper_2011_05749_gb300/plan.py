@@ -25,7 +25,8 @@ class Plan:
                  max_rounds: int = 64, max_batch: int = 1, max_tile: int = 0,
                  wait_limit_log2: int = 0, fault_inject: int = 0, decode_ctas: int = 0,
                  decoder: str = "peel", a_m: int = 3, kay_m: int = 2, noise_auto: bool = False,
-                 host_gather: bool = False, dft_fma_only: bool = False, dt_method: int = 2):
+                 host_gather: bool = False, dft_fma_only: bool = False, dt_method: int = 2,
+                 peel_atomic: bool = False):
         lib = load()
         f = np.ascontiguousarray(f, dtype=np.int64)
         delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -38,6 +39,7 @@ class Plan:
         o.noise_auto = 1 if noise_auto else 0
         o.host_gather = 1 if host_gather else 0
         o.dft_fma_only = 1 if dft_fma_only else 0
+        o.peel_atomic = 1 if peel_atomic else 0
         o.oneshot_method = dt_method
         o.max_rounds = max_rounds
         o.max_batch = max_batch
@@ -194,6 +196,7 @@ def autotune(N: int, K: int, f, delays, xs, stream=None, **plan_kw):
             setattr(o, k, plan_kw[k])
     o.noise_auto = 1 if plan_kw.get("noise_auto") else 0
     o.dft_fma_only = 1 if plan_kw.get("dft_fma_only") else 0
+    o.peel_atomic = 1 if plan_kw.get("peel_atomic") else 0
     tmp.close()
     f = np.ascontiguousarray(f, dtype=np.int64)
     delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -238,6 +241,10 @@ class Server:
         check(load().sfft_server_create(ctypes.byref(h), hbm_budget, max_slots),
               "sfft_server_create")
         self._h = h
+
+    def reserve(self, plan: Plan, n: int):
+        """sfft_server_reserve: create up to n workspaces for plan's requests now."""
+        check(load().sfft_server_reserve(self._h, plan._h, n), "sfft_server_reserve")
 
     def submit(self, plan: Plan, x, out) -> int:
         idx, val, info = out

@@ -395,3 +395,131 @@ def test_autotune_returns_working_schedule(sfft):
     torch.cuda.synchronize()
     for i, p in enumerate(probs):
         np.testing.assert_array_equal(idx[i, :int(infos[i, 0])].cpu().numpy(), p.support)
+
+
+# ---------------------------------------------------------------------- deterministic peeling
+def run_batch_bits(sfft, probs, reps, **kw):
+    """Execute the batch reps times with one plan; every run's outputs as raw bytes."""
+    p0 = probs[0]
+    plan = sfft.Plan(p0.N, p0.K, p0.f, p0.delays, max_batch=len(probs), **kw)
+    xs = torch.stack([to_dev(p.x, np.complex64) for p in probs])
+    out = plan.empty_outputs("cuda", len(probs))
+    runs = []
+    for _ in range(reps):
+        for t in out:
+            t.zero_()
+        plan.execute_many(xs, out)
+        torch.cuda.synchronize()
+        runs.append(tuple(t.cpu().numpy().tobytes() for t in out))
+    plan.close()
+    return runs, out
+
+
+@pytest.mark.parametrize("name,K,ctas", [("rffast_2097024", 1000, 0), ("rffast_124950", 400, 4)])
+def test_peeling_is_deterministic(sfft, oracle_mod, name, K, ctas):
+    """The same noisy batch (20 dB), decoded ten times by one plan with the ordered,
+    compensated peeling subtraction: identical bits every time -- support, values, status,
+    rounds.  The benchmark shape (N = 127*128*129, K = 1000) and a crowded one (N = 49*50*51,
+    K = 400 in B ~ 2500, four CTAs per signal, so the accept order across CTAs varies).  The
+    first signal also matches the oracle."""
+    probs = [synth.config_problem(name, seed=300 + i, K=K) for i in range(8)]
+    for p in probs[1:]:
+        p.delays = probs[0].delays
+        p.x = synth.make_problem(p.N, p.f, p.K, seed=p.seed, R=p.R, delays=probs[0].delays,
+                                 mag=(1.0, 10.0), snr_db=20.0).x
+    kw = dict(precision="fp32", locate="ml", noise_var=probs[0].noise_var, decode_ctas=ctas)
+    runs, out = run_batch_bits(sfft, probs, 10, **kw)
+    for r in runs[1:]:
+        assert r == runs[0]
+    p = probs[0]
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x.astype(np.complex64).astype(np.complex128))
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    info = out[2][0].cpu().numpy()
+    n = int(info[0])
+    assert_matches_oracle(out[0][0, :n].cpu().numpy(), out[1][0, :n].cpu().numpy(), info, ref,
+                          "fp32")
+
+
+def test_atomic_peeling_matches_oracle(sfft, oracle_mod):
+    """peel_atomic plans (unordered float atomics on the bins) still give the oracle's
+    support and values within 1e-5 on the crowded 20 dB case."""
+    p = synth.config_problem("rffast_124950", seed=310, K=400)
+    kw = dict(precision="fp32", locate="ml", noise_var=p.noise_var, peel_atomic=True,
+              decode_ctas=4)
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x.astype(np.complex64).astype(np.complex128))
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    plan, idx, val, info = run_plan(sfft, p, **kw)
+    assert_matches_oracle(idx, val, info, ref, "fp32")
+    plan.close()
+
+
+# ---------------------------------------------------------------------- batched mix vs oracle
+def test_shuffled_mix_matches_oracle(sfft, oracle_mod):
+    """The batched configuration's mix in one sfft_execute_batch call, shuffled: N from
+    {9660, 124950, 2097024} (6 delays: 0, 1, 4 random), K in [10, 500], SNR in [10, 40] dB,
+    sigma^2 estimated per signal (noise_auto).  Three sampled signals per N: the oracle's
+    support bit for bit (its noise estimate, thresholds and peeling on its FP64 bins) and
+    its values within 1e-5; and every signal the same bits as when run alone."""
+    sizes = [(9660, (20, 21, 23)), (124950, (49, 50, 51)), (2097024, (127, 128, 129))]
+    rng = np.random.default_rng(2024)
+    plans, probs, plan_of = [], [], []
+    for N, f in sizes:
+        delays = synth.draw_delays(N, 3, 6, rng)
+        pl = sfft.Plan(N, 500, f, delays, precision="fp32", locate="ml", noise_auto=True,
+                       max_batch=8)
+        plans.append(pl)
+        for i in range(3):
+            K = int(rng.integers(10, 501))
+            snr = float(rng.uniform(10.0, 40.0))
+            q = synth.make_problem(N, f, K, seed=int(rng.integers(1 << 30)), delays=delays,
+                                   mag=(1.0, 10.0), snr_db=snr)
+            probs.append(q)
+            plan_of.append(pl)
+    order = np.random.default_rng(5).permutation(len(probs))
+    probs = [probs[i] for i in order]
+    plan_of = [plan_of[i] for i in order]
+    xs = [to_dev(q.x, np.complex64) for q in probs]
+    outs = [pl.empty_outputs() for pl in plan_of]
+    infos = torch.zeros((len(probs), 4), dtype=torch.int32, device="cuda")
+    sfft.execute_batch(plan_of, xs, ([o[0] for o in outs], [o[1] for o in outs], infos))
+    torch.cuda.synchronize()
+    inf = infos.cpu().numpy()
+    for i, (pl, q) in enumerate(zip(plan_of, probs)):
+        n = int(inf[i, 0])
+        got_i, got_v = outs[i][0][:n].cpu().numpy(), outs[i][1][:n].cpu().numpy()
+        i1, v1, f1 = pl.execute(xs[i])
+        torch.cuda.synchronize()
+        assert int(f1[0]) == n and int(f1[1]) == int(inf[i, 1])
+        np.testing.assert_array_equal(got_i, i1[:n].cpu().numpy())
+        np.testing.assert_array_equal(got_v, v1[:n].cpu().numpy())
+        Y = oracle_mod.bucketize(q.N, q.f, q.delays, q.x.astype(np.complex64).astype(np.complex128))
+        ref = oracle_mod.decode(q.N, q.f, q.delays, Y, 500,
+                                oracle_mod.OracleOpts(locate=1, eta=3e-3, noise_auto=1))
+        assert_matches_oracle(got_i, got_v, inf[i], ref, "fp32")
+    for pl in plans:
+        pl.close()
+
+
+def test_shuffled_batch_host_buffers(sfft):
+    """A shuffled two-plan batch with host (numpy) buffers: info rows land on the right
+    signals, and the outputs equal the device-buffer run's."""
+    a = [synth.make_problem(9660, (20, 21, 23), 30 + i, seed=40 + i, R=3) for i in range(3)]
+    b = [synth.make_problem(124950, (49, 50, 51), 60, seed=50 + i, R=6,
+                            delays=np.array([[0, 1, 7, 99, 1234, 50000]] * 3), mag=(1.0, 10.0))
+         for i in range(3)]
+    pa = sfft.Plan(9660, 64, (20, 21, 23), a[0].delays, precision="fp32", locate="arg",
+                   max_batch=4)
+    pb = sfft.Plan(124950, 64, (49, 50, 51), b[0].delays, precision="fp32", max_batch=4)
+    probs = [a[0], b[0], a[1], b[1], b[2], a[2]]
+    plans = [pa, pb, pa, pb, pb, pa]
+    hx = [q.x.astype(np.complex64) for q in probs]
+    hidx = [np.zeros(64, np.int64) for _ in probs]
+    hval = [np.zeros(64, np.complex64) for _ in probs]
+    hinf = np.zeros((len(probs), 4), np.int32)
+    sfft.execute_batch(plans, hx, (hidx, hval, hinf))
+    for i, q in enumerate(probs):
+        n = int(hinf[i, 0])
+        assert n == q.K and hinf[i, 1] == 0
+        np.testing.assert_array_equal(hidx[i][:n], q.support)
+    pa.close()
+    pb.close()
