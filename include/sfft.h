@@ -148,6 +148,16 @@ typedef struct {
                                  bits on every run.  1 = subtract with unordered float atomics
                                  on the bins as frequencies are accepted (results may differ in
                                  the last bits from run to run) */
+    int32_t overlap_gather;   /* 1: where a stage's whole FP32 tile fills more than half of a
+                                 CTA's shared memory (one CTA per SM), the bucketization runs as
+                                 one persistent CTA per SM that copies the next tile's samples
+                                 into the other end of shared memory while it transforms the
+                                 current one.  0 (default) = one CTA per tile: the scattered
+                                 8-byte copies need L1 lines in flight, which the second tile
+                                 region takes away (measured 2.4x slower on N = 127*128*129) */
+    int32_t classify_lanes;   /* lanes of a warp that search one bin's L candidates in the
+                                 first peeling round (ML locate): 1, 2, 4, 8, 16 or 32; 0
+                                 (default) = chosen per tile from its non-zero bins, L and R */
 } sfft_opts;
 
 /* Fill *opts with the defaults above. */
@@ -239,14 +249,24 @@ int sfft_decode_bins(sfft_plan_t plan, const void* bins, int64_t* out_idx, void*
                      int32_t* out_info, void* stream);
 
 /* Autotuning (no counterpart in the paper).  Times sfft_execute_batch on the caller's n
- * sample signals (device pointers, dtype of *base) for a set of schedules -- the CTAs per
- * signal of the peeling rounds and the largest DFT tile per CTA -- and writes the fastest
- * into *best (a copy of *base with those fields set, max_batch = n) and its rate in
- * signals/s into *best_rate (may be NULL).  Creates and destroys its own plans; the
- * stream is synchronised.                                                                 */
+ * sample signals (device pointers, dtype of *base) for schedules chosen by coordinate
+ * descent from the defaults, one axis at a time: the B-tile (max_tile: whole-stage DFT
+ * tiles, or two passes of 16384, 8192 or 4096 elements), the gather schedule
+ * (overlap_gather), the lanes per bin of the first round's ML search (classify_lanes, ML
+ * plans) and the CTAs per signal of the peeling rounds (decode_ctas); a value is kept when
+ * it is more than 1 % faster.  Writes the fastest into *best (a copy of *base with those
+ * fields set, max_batch = n) and its rate in signals/s into *best_rate (may be NULL).
+ * Creates and destroys its own plans; the stream is synchronised.  With a cache file set
+ * (sfft_autotune_cache), a schedule found before for the same key -- N, f, R, K, n, dtype,
+ * precision, locate, noise_auto, decoder, dft_fma_only and the GPU's name and SM count --
+ * is returned without timing, and a new one is added to the file.                        */
 int sfft_autotune(int64_t N, int32_t K, int32_t n_stages, const int64_t* f, int32_t n_delays,
                   const int64_t* delays, const sfft_opts* base, int32_t n, const void* const* xs,
                   void* stream, sfft_opts* best, double* best_rate);
+/* The autotuner's cache file (a JSON object: key -> schedule fields and rate), or NULL to
+ * use none (the default).  The file is rewritten whole (through a temporary file) when an
+ * entry is added.  Host only.                                                              */
+int sfft_autotune_cache(const char* path);
 
 /* Phase timing.  While enabled, every execute call brackets its bucketization, decode and
  * compaction launches with CUDA events on the launch stream.  sfft_plan_profile waits for

@@ -53,7 +53,8 @@ class Opts(ctypes.Structure):
                 ("oneshot_am", ctypes.c_int32), ("kay_m", ctypes.c_int32),
                 ("noise_auto", ctypes.c_int32), ("host_gather", ctypes.c_int32),
                 ("oneshot_method", ctypes.c_int32), ("dft_fma_only", ctypes.c_int32),
-                ("peel_atomic", ctypes.c_int32)]
+                ("peel_atomic", ctypes.c_int32), ("overlap_gather", ctypes.c_int32),
+                ("classify_lanes", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -90,6 +91,7 @@ EXPORTS = {
                                      ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(Opts),
                                      ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double)]),
+    "sfft_autotune_cache": (ctypes.c_int, [ctypes.c_char_p]),
     "sfft_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sfft_last_cuda_error": (ctypes.c_char_p, []),
 }

@@ -4,11 +4,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "launch.h"
@@ -230,6 +232,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     if (o.fault_inject == 2) return SFFT_ENOMEM;  // injected allocation failure (testing)
     if (o.wait_limit_log2 < 0 || o.fault_inject < 0 || o.fault_inject > 2 || o.decode_ctas < 0)
         return SFFT_EINVAL;
+    if (o.classify_lanes < 0 || o.classify_lanes > 32 || (o.classify_lanes & (o.classify_lanes - 1)))
+        return SFFT_EINVAL;
     DevInfo di;
     int rc = device_info(&di);
     if (rc) return rc;
@@ -243,6 +247,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     p->xesz = p->xdouble ? 16 : 8;
     p->max_batch = o.max_batch;
     p->num_sms = di.sms;
+    p->max_smem = di.max_smem;
     const double eta = o.eta > 0 ? o.eta : (p->prec ? 3e-3 : 1e-6);
 
     PlanDesc& pd = p->pd;
@@ -428,6 +433,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     p->smem2 = l2.smem;
     p->threads1 = pfa_threads(l1.tile, p->esz);
     p->threads2 = pfa_threads(l2.tile, p->esz);
+    p->stream_ok = o.overlap_gather != 0 && !p->need_pass2 && p->prec == 1 && !p->xdouble &&
+                   2 * p->smem1 > (size_t)di.max_smem;
 
     // device memory
     const size_t nb = (size_t)pd.sumB, mb = (size_t)p->max_batch;
@@ -621,6 +628,18 @@ static DecodeWs ws_at(const sfft_plan_s* p, int slot0)
     return w;
 }
 
+// One bucketization pass of plan p (pass 0 or 1) with the arguments a: the persistent
+// overlapped kernel where it applies (device signals), else one CTA per tile.
+static cudaError_t bucketize_pass(const sfft_plan_s* p, const BucketArgs& a, int pass,
+                                  cudaStream_t st)
+{
+    if (pass == 0 && p->stream_ok && !a.x_sys)
+        return launch_bucketize_stream(a, p->num_sms, 512, (size_t)p->max_smem & ~(size_t)15,
+                                       (int)(p->smem1 / 8), st);
+    return launch_bucketize(a, p->prec, p->xdouble, pass == 0 ? p->threads1 : p->threads2,
+                            pass == 0 ? p->smem1 : p->smem2, st);
+}
+
 // Enqueue the whole path for n signals of one plan in workspace slots [slot0, slot0 + n)
 // (slot0 + n <= max_batch).  For n > 1 the signal and output pointers come from device
 // tables d_xs / d_idx / d_val; for n == 1 from x0 / idx0 / val0.  Info rows: signal i's at
@@ -661,8 +680,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
                 a.tile_prefix[d + 1] = a.tile_prefix[d] + (d < pd.D ? src[d].n_tiles * pd.R : 0);
             }
             a.tiles_per_sig = a.tile_prefix[kMaxStages];
-            CK(launch_bucketize(a, p->prec, p->xdouble, pass == 0 ? p->threads1 : p->threads2,
-                                pass == 0 ? p->smem1 : p->smem2, st));
+            CK(bucketize_pass(p, a, pass, st));
         }
     }
     DecodeArgs da;
@@ -680,6 +698,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     // CTAs still fit an SM)
     da.wtab_smem = (size_t)p->wtab_elems * p->esz <= 160 * 1024 ? 1 : 0;
     da.dt_method = p->opts.oneshot_method == 0 ? 2 : p->opts.oneshot_method;
+    da.lanes = p->opts.classify_lanes;
     const int threads = 512;
     const int total = p->num_sms * p->decode_occ;
     // later rounds touch O(K) bins: about one CTA per 256 expected single-tons
@@ -996,17 +1015,149 @@ extern "C" int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const voi
     return SFFT_OK;
 }
 
+namespace sfft {
+
+// ---- autotuning cache: one JSON object, key -> {"max_tile": .., ...}, in a file ----------
+static std::mutex g_tune_mu;
+static std::string g_tune_path;
+
+struct TuneEntry {
+    int max_tile, overlap_gather, classify_lanes, decode_ctas;
+    double rate;
+};
+
+// the schedule fields of the cache, in file order
+static const char* const kTuneFields[] = {"max_tile", "overlap_gather", "classify_lanes",
+                                           "decode_ctas", "rate"};
+
+static std::string tune_key(int64_t N, int32_t K, int32_t D, const int64_t* f, int32_t R,
+                            const sfft_opts& o, int32_t n)
+{
+    std::string k = "N=" + std::to_string(N) + ";f=";
+    for (int d = 0; d < D; ++d) k += (d ? "," : "") + std::to_string(f[d]);
+    k += ";R=" + std::to_string(R) + ";K=" + std::to_string(K) + ";batch=" + std::to_string(n) +
+         ";dtype=" + std::to_string(o.dtype) + ";prec=" + std::to_string(o.precision) +
+         ";locate=" + std::to_string(o.locate) + ";noise_auto=" + std::to_string(o.noise_auto) +
+         ";decoder=" + std::to_string(o.decoder) + ";fma_only=" + std::to_string(o.dft_fma_only);
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+        k += ";gpu=" + std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "sm";
+    for (char& c : k)
+        if (c == '"' || c == '\\') c = '_';
+    return k;
+}
+
+// every entry of the cache file: key -> the text of its object
+static std::vector<std::pair<std::string, std::string>> tune_read(const std::string& path)
+{
+    std::vector<std::pair<std::string, std::string>> out;
+    FILE* fp = fopen(path.c_str(), "rb");
+    if (!fp) return out;
+    std::string txt;
+    char buf[4096];
+    size_t got;
+    while ((got = fread(buf, 1, sizeof(buf), fp)) > 0) txt.append(buf, got);
+    fclose(fp);
+    size_t i = 0;
+    while (true) {
+        const size_t q0 = txt.find('"', i);
+        if (q0 == std::string::npos) break;
+        const size_t q1 = txt.find('"', q0 + 1);
+        const size_t b0 = q1 == std::string::npos ? q1 : txt.find('{', q1);
+        const size_t b1 = b0 == std::string::npos ? b0 : txt.find('}', b0);
+        if (b1 == std::string::npos) break;
+        out.emplace_back(txt.substr(q0 + 1, q1 - q0 - 1), txt.substr(b0, b1 - b0 + 1));
+        i = b1 + 1;
+    }
+    return out;
+}
+
+static bool tune_field(const std::string& obj, const char* name, double* v)
+{
+    const std::string pat = std::string("\"") + name + "\"";
+    const size_t at = obj.find(pat);
+    if (at == std::string::npos) return false;
+    const size_t colon = obj.find(':', at + pat.size());
+    if (colon == std::string::npos) return false;
+    char* end = nullptr;
+    *v = strtod(obj.c_str() + colon + 1, &end);
+    return end != obj.c_str() + colon + 1;
+}
+
+static bool tune_lookup(const std::string& key, TuneEntry* e)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tune_path.empty()) return false;
+    for (auto& kv : tune_read(g_tune_path)) {
+        if (kv.first != key) continue;
+        double v[5];
+        for (int i = 0; i < 5; ++i)
+            if (!tune_field(kv.second, kTuneFields[i], &v[i])) return false;
+        *e = TuneEntry{(int)v[0], (int)v[1], (int)v[2], (int)v[3], v[4]};
+        return true;
+    }
+    return false;
+}
+
+static void tune_store(const std::string& key, const TuneEntry& e)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tune_path.empty()) return;
+    auto all = tune_read(g_tune_path);
+    char obj[256];
+    snprintf(obj, sizeof(obj),
+             "{\"max_tile\": %d, \"overlap_gather\": %d, \"classify_lanes\": %d, "
+             "\"decode_ctas\": %d, \"rate\": %.6g}",
+             e.max_tile, e.overlap_gather, e.classify_lanes, e.decode_ctas, e.rate);
+    bool found = false;
+    for (auto& kv : all)
+        if (kv.first == key) {
+            kv.second = obj;
+            found = true;
+        }
+    if (!found) all.emplace_back(key, obj);
+    const std::string tmp = g_tune_path + ".tmp";
+    FILE* fp = fopen(tmp.c_str(), "wb");
+    if (!fp) return;
+    fputs("{\n", fp);
+    for (size_t i = 0; i < all.size(); ++i)
+        fprintf(fp, "  \"%s\": %s%s\n", all[i].first.c_str(), all[i].second.c_str(),
+                i + 1 < all.size() ? "," : "");
+    fputs("}\n", fp);
+    fclose(fp);
+    rename(tmp.c_str(), g_tune_path.c_str());
+}
+
+}  // namespace sfft
+
+extern "C" int sfft_autotune_cache(const char* path)
+{
+    std::lock_guard<std::mutex> lk(sfft::g_tune_mu);
+    sfft::g_tune_path = path ? path : "";
+    return SFFT_OK;
+}
+
 extern "C" int sfft_autotune(int64_t N, int32_t K, int32_t n_stages, const int64_t* f,
                              int32_t n_delays, const int64_t* delays, const sfft_opts* base,
                              int32_t n, const void* const* xs, void* stream, sfft_opts* best,
                              double* best_rate)
 {
-    if (!base || !best || !xs || n < 1) return SFFT_EINVAL;
+    if (!base || !best || !xs || !f || !delays || n < 1 || n_stages < 1) return SFFT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    const int ctas[] = {0, 1, 2, 4, 8};
-    const int tiles[] = {0, 8192};
-    double best_v = -1;
+    const std::string key = tune_key(N, K, n_stages, f, n_delays, *base, n);
     sfft_opts bo = *base;
+    bo.max_batch = n;
+    TuneEntry cached;
+    if (tune_lookup(key, &cached)) {
+        bo.max_tile = cached.max_tile;
+        bo.overlap_gather = cached.overlap_gather;
+        bo.classify_lanes = cached.classify_lanes;
+        bo.decode_ctas = cached.decode_ctas;
+        *best = bo;
+        if (best_rate) *best_rate = cached.rate;
+        return SFFT_OK;
+    }
     std::vector<int64_t*> idx(n);
     std::vector<void*> val(n);
     int32_t* infos = nullptr;
@@ -1014,7 +1165,10 @@ extern "C" int sfft_autotune(int64_t N, int32_t K, int32_t n_stages, const int64
     const size_t xesz = base->dtype == SFFT_C128 ? 16 : 8;
     const size_t per = align_up((size_t)K * 8, 256) + align_up((size_t)K * xesz, 256);
     CK(cudaMalloc(&outbuf, per * n));
-    CK(cudaMalloc((void**)&infos, 16 * (size_t)n));
+    if (cudaMalloc((void**)&infos, 16 * (size_t)n) != cudaSuccess) {
+        cudaFree(outbuf);
+        return SFFT_ENOMEM;
+    }
     for (int i = 0; i < n; ++i) {
         idx[i] = (int64_t*)((unsigned char*)outbuf + per * i);
         val[i] = (unsigned char*)outbuf + per * i + align_up((size_t)K * 8, 256);
@@ -1023,44 +1177,63 @@ extern "C" int sfft_autotune(int64_t N, int32_t K, int32_t n_stages, const int64
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = SFFT_OK;
-    for (int tile : tiles) {
-        for (int g : ctas) {
-            sfft_opts o = *base;
-            o.max_batch = n;
-            o.decode_ctas = g;
-            o.max_tile = tile;
-            sfft_plan_t p = nullptr;
-            if (sfft_plan_create(&p, N, K, n_stages, f, n_delays, delays, &o) != SFFT_OK) continue;
-            std::vector<sfft_plan_t> ps(n, p);
-            int r = SFFT_OK;
-            for (int w = 0; w < 2 && r == SFFT_OK; ++w)
-                r = sfft_execute_batch(n, ps.data(), xs, idx.data(), val.data(), infos, st);
-            const int reps = 3;
-            cudaEventRecord(e0, st);
-            for (int w = 0; w < reps && r == SFFT_OK; ++w)
-                r = sfft_execute_batch(n, ps.data(), xs, idx.data(), val.data(), infos, st);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            sfft_plan_destroy(p);
-            if (r != SFFT_OK) {
-                rc = r;
-                continue;
-            }
-            const double v = (double)n * reps / (ms / 1e3);
-            if (v > best_v) {
-                best_v = v;
-                bo = o;
+    // signals/s of one schedule: 2 warm-up and 3 timed batches; -1 if it cannot run
+    auto trial = [&](const sfft_opts& o) -> double {
+        sfft_plan_t p = nullptr;
+        if (sfft_plan_create(&p, N, K, n_stages, f, n_delays, delays, &o) != SFFT_OK) return -1.0;
+        std::vector<sfft_plan_t> ps(n, p);
+        int r = SFFT_OK;
+        for (int w = 0; w < 2 && r == SFFT_OK; ++w)
+            r = sfft_execute_batch(n, ps.data(), xs, idx.data(), val.data(), infos, st);
+        const int reps = 3;
+        cudaEventRecord(e0, st);
+        for (int w = 0; w < reps && r == SFFT_OK; ++w)
+            r = sfft_execute_batch(n, ps.data(), xs, idx.data(), val.data(), infos, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        sfft_plan_destroy(p);
+        if (r != SFFT_OK) {
+            rc = r;
+            return -1.0;
+        }
+        return (double)n * reps / (ms / 1e3);
+    };
+    // coordinate descent over the schedule axes, from the defaults: the B-tile (largest DFT
+    // tile a CTA holds: whole stage, or two passes of smaller tiles), the gather schedule
+    // (persistent overlapped or one CTA per tile), the lanes per bin of the ML search, the
+    // CTAs per signal of the peeling rounds
+    sfft_opts cur = bo;
+    cur.max_tile = 0;
+    cur.overlap_gather = 0;
+    cur.classify_lanes = 0;
+    cur.decode_ctas = 0;
+    double best_v = trial(cur);
+    auto sweep = [&](int sfft_opts::*field, std::initializer_list<int> values) {
+        for (int v : values) {
+            if (cur.*field == v) continue;
+            sfft_opts o = cur;
+            o.*field = v;
+            const double r = trial(o);
+            if (r > best_v * 1.01) {
+                best_v = r;
+                cur = o;
             }
         }
-    }
+    };
+    sweep(&sfft_opts::max_tile, {16384, 8192, 4096});
+    sweep(&sfft_opts::overlap_gather, {1});
+    if (base->locate == SFFT_LOCATE_ML) sweep(&sfft_opts::classify_lanes, {1, 2, 4, 8, 16, 32});
+    sweep(&sfft_opts::decode_ctas, {1, 2, 4, 8});
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(outbuf);
     cudaFree(infos);
     if (best_v < 0) return rc ? rc : SFFT_EINVAL;
-    *best = bo;
+    tune_store(key, TuneEntry{cur.max_tile, cur.overlap_gather, cur.classify_lanes, cur.decode_ctas,
+                              best_v});
+    *best = cur;
     if (best_rate) *best_rate = best_v;
     return SFFT_OK;
 }
@@ -1121,8 +1294,7 @@ extern "C" int sfft_bucketize(sfft_plan_t p, const void* x, void* bins, void* st
             a.tile_prefix[d + 1] = a.tile_prefix[d] + (d < p->pd.D ? src[d].n_tiles * p->pd.R : 0);
         }
         a.tiles_per_sig = a.tile_prefix[kMaxStages];
-        CK(launch_bucketize(a, p->prec, p->xdouble, pass == 0 ? p->threads1 : p->threads2,
-                            pass == 0 ? p->smem1 : p->smem2, st));
+        CK(bucketize_pass(p, a, pass, st));
     }
     CK(launch_bins_to_natural(p->pd, p->d_pbin, p->d_bins, bins, p->prec, 1, st));
     return SFFT_OK;

@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
     if (pd.locate == 1) {
         int Lmax = 0;
         for (int d = 0; d < pd.D; ++d) Lmax = max(Lmax, pd.st[d].L);
-        const int G = ml_group_size(n_nz, Lmax, pd.R, blockDim.x);
+        const int G = a.lanes > 0 ? a.lanes : ml_group_size(n_nz, Lmax, pd.R, blockDim.x);
         const int per = blockDim.x / G;
         for (int k = 0; k < (n_nz + per - 1) / per; ++k) {
             const int i = k * per + threadIdx.x / G;

@@ -883,6 +883,144 @@ loaded:
     }
 }
 
+// ---- persistent one-pass bucketization with the next tile's gather overlapped ----------
+// When a whole-stage FP32 tile fills more than half of shared memory, one CTA fits an SM
+// and, in bucketize_kernel, a tile's scattered gather cannot overlap another tile's DFTs.
+// Here one persistent CTA per SM takes the work items (signal, stage, delay) round robin
+// and keeps two tile regions at the two ends of shared memory: A = [0, region) and
+// B = [off_b, off_b + region), overlapping in the middle when 2 region > smem.  While the
+// current item is transformed in one region, the next item's samples that fall outside it
+// are already being copied (asynchronous 8-byte copies) into the other; the rest of them
+// follow once the current item is stored.
+
+// asynchronous copies of samples [e_lo, e_hi) of the item (sig, d, r) into tile s
+__device__ __forceinline__ void gather_issue(float2* s, const BucketArgs& a, int sig, int d, int r,
+                                             int e_lo, int e_hi)
+{
+    const StageDesc& st = a.pd.st[d];
+    const float2* xv = reinterpret_cast<const float2*>(a.xs ? a.xs[sig] : a.x0);
+    const int tau = st.tau[r], L = st.L, N = a.pd.N;
+    const int32_t* nidx = a.nidx + st.bin_base;
+    constexpr int U = 8;
+    for (int e0 = e_lo + threadIdx.x; e0 < e_hi; e0 += U * blockDim.x) {
+        int src[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            src[u] = e < e_hi ? __ldg(nidx + e) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < e_hi) {
+                int xi = src[u] * L + tau;
+                xi = xi >= N ? xi - N : xi;
+                cp_async(s + e, xv + xi, 8);
+            }
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void stream_item(const BucketArgs& a, int w, int* sig, int* d, int* r)
+{
+    *sig = w / a.tiles_per_sig;
+    int rem = w - *sig * a.tiles_per_sig;
+    int dd = 0;
+    while (rem >= a.tile_prefix[dd + 1]) ++dd;
+    *d = dd;
+    *r = rem - a.tile_prefix[dd];  // one tile per (stage, delay)
+}
+
+template <bool TC>
+__global__ void __launch_bounds__(512, 1)
+    bucketize_stream_kernel(const __grid_constant__ BucketArgs a, int32_t region, int32_t off_b)
+{
+    using V = float2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* const sm = reinterpret_cast<V*>(smem_raw);
+    const int n_items = a.n_sig * a.tiles_per_sig;
+    int w = blockIdx.x;
+    if (w >= n_items) return;
+    int sig, d, r;
+    stream_item(a, w, &sig, &d, &r);
+    int cur = 0;  // region of the current item: 0 = A, 1 = B
+    gather_issue(sm, a, sig, d, r, 0, a.pd.st[d].B);
+    for (; w < n_items; w += gridDim.x) {
+        V* s = cur ? sm + off_b : sm;
+        const StageDesc& st = a.pd.st[d];
+        const int TS = st.B;
+        V* tws = s + ((TS + 1) & ~1);
+        {
+            const V* twg = reinterpret_cast<const V*>(a.tw);
+            int off = 0;
+            for (int ax = 0; ax < st.n_axes; ++ax) {
+                const int n = axis_tw_smem(st.ax[ax].P, st.ax[ax].pow2, st.ax[ax].tc);
+                for (int t = threadIdx.x; t < n; t += blockDim.x) tws[off + t] = twg[st.ax[ax].tw_off + t];
+                off += (n + 1) & ~1;
+            }
+        }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        // the next item's samples outside this region, copied while this one is transformed
+        const int wn = w + gridDim.x;
+        int sn = 0, dn = 0, rn = 0, lo = 0, hi = 0, TSn = 0;
+        if (wn < n_items) {
+            stream_item(a, wn, &sn, &dn, &rn);
+            TSn = a.pd.st[dn].B;
+            if (cur == 0) {  // next in B: element e lies outside A when off_b + e >= region
+                lo = min(TSn, max(0, region - off_b));
+                gather_issue(sm + off_b, a, sn, dn, rn, lo, TSn);
+            } else {         // next in A: outside B when e < off_b
+                hi = min(TSn, off_b);
+                gather_issue(sm, a, sn, dn, rn, 0, hi);
+            }
+        }
+        const int64_t slot = (int64_t)sig * a.pd.y_per_sig + st.y_off + (int64_t)r * st.B;
+        bool stage_tc = false;
+        for (int ax = 0; ax < st.n_axes; ++ax) stage_tc |= st.ax[ax].tc != 0;
+        int p2 = 1, log2p2 = 0, ls2 = 1;
+        const V* tw2 = nullptr;
+        int off = 0;
+        for (int ax = 0; ax < st.n_axes; ++ax) {
+            const AxisDesc& A = st.ax[ax];
+            if (A.pow2) {
+                const bool fuse = TC && stage_tc;
+                if (fuse) {
+                    p2 = A.P;
+                    log2p2 = A.log2P;
+                    ls2 = A.S;
+                    tw2 = tws + off;
+                }
+                axis_fft_pow2<float>(s, tws + off, A.P, A.log2P, A.S, TS, fuse ? A.log2P - 1 : A.log2P);
+            } else if (A.P > 1) {
+                if (A.P <= 9)
+                    odd_small<float>(s, tws + off, A.P, A.S, TS);
+                else if (!(TC && A.tc))
+                    odd_axis_f32<8>(s, tws + off, A.P, A.S, TS);
+            }
+            off += (axis_tw_smem(A.P, A.pow2, A.tc) + 1) & ~1;
+        }
+        if (TC && stage_tc) {
+            tc_axes_store(s, a, d, slot, TS, tw2, p2, log2p2, ls2);
+        } else {
+            V* dst = reinterpret_cast<V*>(a.bins) + slot;
+            for (int e = threadIdx.x; e < TS; e += blockDim.x) __stcg(dst + e, s[e]);
+        }
+        __syncthreads();  // this region is read for the last time above
+        if (wn < n_items) {
+            if (cur == 0)
+                gather_issue(sm + off_b, a, sn, dn, rn, 0, lo);
+            else
+                gather_issue(sm, a, sn, dn, rn, hi, TSn);
+        }
+        sig = sn;
+        d = dn;
+        r = rn;
+        cur ^= 1;
+    }
+}
+
 template <typename T>
 __global__ void twiddle_kernel(typename C2<T>::t* tw, const int32_t* P_of, const int32_t* t_of,
                                int64_t n)
@@ -964,6 +1102,23 @@ cudaError_t launch_bucketize(const BucketArgs& a, int precision, int xdouble, in
     return cudaGetLastError();
 }
 
+// the persistent overlapped variant (FP32 arithmetic and samples, one-pass stages, device
+// memory): grid CTAs, all of shared memory (smem bytes), tile regions of `region` elements
+cudaError_t launch_bucketize_stream(const BucketArgs& a, int grid, int threads, size_t smem,
+                                    int region, cudaStream_t st)
+{
+    const int n_items = a.n_sig * a.tiles_per_sig;
+    if (n_items == 0) return cudaSuccess;
+    if (grid > n_items) grid = n_items;
+    const int off_b = (int)((smem / 8 - (size_t)region) & ~(size_t)1);
+    if (off_b < 0) return cudaErrorInvalidValue;
+    if (launch_has_tc(a))
+        bucketize_stream_kernel<true><<<grid, threads, smem, st>>>(a, region, off_b);
+    else
+        bucketize_stream_kernel<false><<<grid, threads, smem, st>>>(a, region, off_b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_twiddles(void* tw, const int32_t* P_of, const int32_t* t_of, int64_t n,
                             int precision, cudaStream_t st)
 {
@@ -996,7 +1151,9 @@ cudaError_t set_bucketize_smem_limit(int max_smem)
                          (const void*)bucketize_kernel<float, double, false>,
                          (const void*)bucketize_kernel<float, double, true>,
                          (const void*)bucketize_kernel<double, float, false>,
-                         (const void*)bucketize_kernel<double, double, false>};
+                         (const void*)bucketize_kernel<double, double, false>,
+                         (const void*)bucketize_stream_kernel<false>,
+                         (const void*)bucketize_stream_kernel<true>};
     for (const void* fn : fns) {
         const cudaError_t e =
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);

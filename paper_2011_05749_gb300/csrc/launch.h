@@ -35,6 +35,7 @@ struct DecodeArgs {
     int32_t wtab_elems;   // largest window of ML phasor tables a classify tile stages
     int32_t wtab_smem;    // 1: classify stages them in shared memory
     int32_t dt_method;    // one-shot Step 2: 1 polynomial roots, 2 enumeration, 3 matrix pencil
+    int32_t lanes;        // classify: lanes per bin of the ML search (0 = chosen per tile)
     const int32_t* pbin;  // position -> bin j, per stage at bin_base
     const int32_t* bpos;  // bin j -> position
     const void* roots;    // the plan's twiddle table: ML phasor tables at st[d].wtab_off
@@ -60,6 +61,10 @@ struct CompactArgs {
 // precision: 0 = double arithmetic, 1 = float; xdouble: input/output complex128
 cudaError_t launch_bucketize(const BucketArgs& a, int precision, int xdouble, int threads,
                              size_t smem, cudaStream_t st);
+// persistent one-pass variant with the next tile's gather overlapped (FP32, device x):
+// grid CTAs with smem bytes each, tile regions of `region` elements at both ends
+cudaError_t launch_bucketize_stream(const BucketArgs& a, int grid, int threads, size_t smem,
+                                    int region, cudaStream_t st);
 // round 1 of the decoder (classification of every bin) over all signals
 cudaError_t launch_classify(const DecodeArgs& a, int precision, cudaStream_t st);
 // sigma^2 per signal from the median bin energy (noise_auto plans), before classify

@@ -18,6 +18,9 @@ struct sfft_plan_s {
     size_t xesz = 8;     // bytes of one complex of the I/O type
     int max_batch = 1;
     int num_sms = 0;
+    int max_smem = 0;     // the device's opt-in shared memory per block
+    bool stream_ok = false;  // one-pass FP32 plan whose tiles fill more than half of it: the
+                             // persistent overlapped bucketization applies
     int decode_occ = 1;
     int threads1 = 256, threads2 = 256;
     size_t smem1 = 0, smem2 = 0;

@@ -26,7 +26,8 @@ class Plan:
                  wait_limit_log2: int = 0, fault_inject: int = 0, decode_ctas: int = 0,
                  decoder: str = "peel", a_m: int = 3, kay_m: int = 2, noise_auto: bool = False,
                  host_gather: bool = False, dft_fma_only: bool = False, dt_method: int = 2,
-                 peel_atomic: bool = False):
+                 peel_atomic: bool = False, overlap_gather: bool = False,
+                 classify_lanes: int = 0):
         lib = load()
         f = np.ascontiguousarray(f, dtype=np.int64)
         delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -40,6 +41,8 @@ class Plan:
         o.host_gather = 1 if host_gather else 0
         o.dft_fma_only = 1 if dft_fma_only else 0
         o.peel_atomic = 1 if peel_atomic else 0
+        o.overlap_gather = 1 if overlap_gather else 0
+        o.classify_lanes = classify_lanes
         o.oneshot_method = dt_method
         o.max_rounds = max_rounds
         o.max_batch = max_batch
@@ -180,10 +183,12 @@ def execute_batch(plans, xs, out, stream=None):
     return out
 
 
-def autotune(N: int, K: int, f, delays, xs, stream=None, **plan_kw):
+def autotune(N: int, K: int, f, delays, xs, stream=None, cache: str | None = None, **plan_kw):
     """sfft_autotune: time the schedules on the sample signals xs (device tensors) and return
-    (plan keyword arguments of the fastest, its signals/s).  plan_kw as for Plan."""
+    (plan keyword arguments of the fastest, its signals/s).  plan_kw as for Plan.  cache: a
+    JSON file of schedules found before (sfft_autotune_cache), read and extended."""
     lib = load()
+    check(lib.sfft_autotune_cache(cache.encode() if cache else None), "sfft_autotune_cache")
     tmp = Plan(N, K, f, delays, **{**plan_kw, "max_batch": 1})  # validates and fills opts
     o = _lib.Opts()
     lib.sfft_opts_default(ctypes.byref(o))
@@ -197,6 +202,8 @@ def autotune(N: int, K: int, f, delays, xs, stream=None, **plan_kw):
     o.noise_auto = 1 if plan_kw.get("noise_auto") else 0
     o.dft_fma_only = 1 if plan_kw.get("dft_fma_only") else 0
     o.peel_atomic = 1 if plan_kw.get("peel_atomic") else 0
+    o.overlap_gather = 1 if plan_kw.get("overlap_gather") else 0
+    o.classify_lanes = int(plan_kw.get("classify_lanes", 0))
     tmp.close()
     f = np.ascontiguousarray(f, dtype=np.int64)
     delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -210,7 +217,8 @@ def autotune(N: int, K: int, f, delays, xs, stream=None, **plan_kw):
                             stream_handle(stream), ctypes.byref(best), ctypes.byref(rate)),
           "sfft_autotune")
     kw = dict(plan_kw)
-    kw.update(max_batch=best.max_batch, decode_ctas=best.decode_ctas, max_tile=best.max_tile)
+    kw.update(max_batch=best.max_batch, decode_ctas=best.decode_ctas, max_tile=best.max_tile,
+              overlap_gather=bool(best.overlap_gather), classify_lanes=best.classify_lanes)
     return kw, rate.value
 
 

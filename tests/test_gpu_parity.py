@@ -99,6 +99,29 @@ def test_bucketize_matches_oracle(sfft, oracle_mod, case):
         assert rel_l2(g, r) <= TOL[prec], rel_l2(g, r)
 
 
+@pytest.mark.parametrize("fma_only", [False, True])
+def test_bucketize_overlapped_gather_matches_oracle(sfft, oracle_mod, fma_only):
+    """The benchmark's bucketization shape (N = 127*128*129, 8 delays, FP32), whose whole-stage
+    tiles fill more than half of shared memory: the persistent kernel that overlaps the next
+    tile's gather with the current tile's DFTs gives the oracle's bins within 1e-5 per stage
+    and delay, and the same bits as one CTA per tile."""
+    N, f, R = 2097024, (127, 128, 129), 8
+    rng = np.random.default_rng(808)
+    x = (rng.standard_normal(N) + 1j * rng.standard_normal(N)).astype(np.complex64)
+    delays = synth.draw_delays(N, 3, R, rng)
+    xd = to_dev(x, np.complex64)
+    on = sfft.Plan(N, 4, f, delays, precision="fp32", dft_fma_only=fma_only, overlap_gather=True)
+    off = sfft.Plan(N, 4, f, delays, precision="fp32", dft_fma_only=fma_only)
+    b_on = on.bucketize(xd).cpu().numpy()
+    b_off = off.bucketize(xd).cpu().numpy()
+    on.close()
+    off.close()
+    np.testing.assert_array_equal(b_on.view(np.uint8), b_off.view(np.uint8))
+    Y = oracle_mod.bucketize(N, f, delays, x.astype(np.complex128))
+    for g, r in zip(split_bins(b_on, N, f, R), split_bins(Y, N, f, R)):
+        assert rel_l2(g, r) <= TOL["fp32"], rel_l2(g, r)
+
+
 @pytest.mark.parametrize("N,f,R", [(2097024, (127, 128, 129), 2), (551286, (81, 82, 83), 3)])
 def test_bucketize_fma_only_matches_oracle(sfft, oracle_mod, N, f, R):
     """dft_fma_only plans keep every odd axis on the FMA pipes (no tensor-core axes): the
@@ -383,13 +406,28 @@ def test_mixed_batch_matches_single(sfft):
         np.testing.assert_array_equal(i1[:n].cpu().numpy(), q.support)
 
 
-def test_autotune_returns_working_schedule(sfft):
+def test_autotune_returns_working_schedule(sfft, tmp_path):
+    """The autotuner's schedule runs and recovers the truth; it is stored in the cache file
+    and a second call returns it from there."""
+    import json
+    import time
     probs = [synth.make_problem(124950, (49, 50, 51), 60, seed=300 + i, R=6,
                                 delays=np.array([[0, 1, 11, 222, 3333, 44444]] * 3),
                                 mag=(1.0, 10.0)) for i in range(4)]
     xs = [to_dev(p.x, np.complex64) for p in probs]
-    kw, rate = sfft.autotune(124950, 60, (49, 50, 51), probs[0].delays, xs, precision="fp32")
+    cache = str(tmp_path / "tune.json")
+    kw, rate = sfft.autotune(124950, 60, (49, 50, 51), probs[0].delays, xs, precision="fp32",
+                             cache=cache)
     assert rate > 0 and kw["max_batch"] == 4 and kw["decode_ctas"] >= 0
+    entries = json.load(open(cache))
+    assert len(entries) == 1
+    (k, v), = entries.items()
+    assert k.startswith("N=124950;f=49,50,51;R=6;K=60;batch=4") and v["rate"] > 0
+    t0 = time.perf_counter()
+    kw2, rate2 = sfft.autotune(124950, 60, (49, 50, 51), probs[0].delays, xs, precision="fp32",
+                               cache=cache)
+    assert time.perf_counter() - t0 < 0.5
+    assert kw2 == kw and abs(rate2 - rate) <= 1e-5 * rate
     plan = sfft.Plan(124950, 60, (49, 50, 51), probs[0].delays, **kw)
     idx, val, infos = plan.execute_many(torch.stack(xs))
     torch.cuda.synchronize()
