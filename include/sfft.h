@@ -99,8 +99,10 @@ typedef struct {
     int32_t locate;      /* SFFT_LOCATE_ARG or SFFT_LOCATE_ML (default ML) */
     int32_t max_rounds;  /* peeling rounds at most (default 64) */
     int32_t max_batch;   /* signals per execute call at most; sizes the workspace (default 1) */
-    int32_t max_tile;    /* largest DFT tile in elements held by one CTA; 0 = whatever shared
-                            memory allows (stages larger than it run as two passes) */
+    int32_t max_tile;    /* B-tile: largest DFT tile in elements held by one CTA; 0 = whatever
+                            shared memory allows (stages larger than it run as two passes, with
+                            tiles of about max_tile elements, or 4096 (FP32) / 2048 (FP64) when
+                            max_tile is 0) */
     double noise_var;    /* sigma^2 of the noise per time sample, 0 = exactly sparse */
     double a_min;        /* smallest significant |xhat| (default 1) */
     double eta;          /* relative numerical floor of the thresholds; 0 = default

@@ -594,14 +594,127 @@ __device__ __forceinline__ void odd_axis_tc(float2* s, const float2* tw, int P, 
     }
 }
 
+// The store of a one-pass tile to the bins, with up to two axes done on the way (the axes of
+// the prime-factor map commute, so they can run last): the last radix-2 stage of the
+// power-of-two axis a2 (half size H = P2 / 2, twiddles tw2) and the whole small odd axis a3
+// (3 <= P3 <= 9, conjugate-pair table tw3 as odd_small reads it).  A work item holds the
+// 2 P3 (or P3, or 2) elements that differ only in those coordinates: one thread reads them,
+// transforms them in registers and writes them to the bins, which saves the trips through
+// shared memory (and the barriers) those axes would take on their own.  a2 / a3 = -1: none.
+template <typename T, int P3>
+__device__ __forceinline__ void store_fused_p(const typename C2<T>::t* s, typename C2<T>::t* dst,
+                                              const StageDesc& st, int TS, int a2,
+                                              const typename C2<T>::t* tw2, int a3,
+                                              const typename C2<T>::t* tw3)
+{
+    using V = typename C2<T>::t;
+    constexpr int pairs = (P3 - 1) / 2;
+    const int S3 = a3 >= 0 ? st.ax[a3].S : 0;
+    const int H = a2 >= 0 ? st.ax[a2].P >> 1 : 1, HS2 = a2 >= 0 ? H * st.ax[a2].S : 0;
+    const int J = a2 >= 0 ? 2 : 1;
+    const int KP = odd_row_len(P3);
+    const int W = TS / (P3 * J);
+    // the item index in mixed radix over the other axes (axis a2 with radix H), innermost
+    // first; the last digit needs no division
+    // (fully unrolled over the axis slots so that the digits stay in registers)
+    int Rr[kMaxAxes], Sr[kMaxAxes];
+    float inv[kMaxAxes];
+    const int nax = st.n_axes;
+#pragma unroll
+    for (int ax = 0; ax < kMaxAxes; ++ax) {
+        const bool live = ax < nax && ax != a3;
+        Rr[ax] = !live ? 1 : ax == a2 ? H : st.ax[ax].P;
+        Sr[ax] = live ? st.ax[ax].S : 0;
+        inv[ax] = 1.0f / (float)Rr[ax];
+    }
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        // position of the item's first element, and its coordinate k < H on axis a2
+        int rem = w, base = 0, k = 0;
+#pragma unroll
+        for (int ax = 0; ax < kMaxAxes; ++ax) {
+            if (ax >= nax) break;
+            int c;
+            rem = fdivmod(rem, Rr[ax], inv[ax], &c);
+            if (ax == a2) k = c;
+            base += c * Sr[ax];
+        }
+        V v[2][P3];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int i = 0; i < P3; ++i)
+                if (j < J) v[j][i] = s[base + i * S3 + j * HS2];
+        if (a2 >= 0) {
+            const V wv = tw2[k];
+#pragma unroll
+            for (int i = 0; i < P3; ++i) {
+                const V u = v[0][i], x = v[1][i];
+                const V xt = {fma(x.x, wv.x, x.y * wv.y), fma(x.y, wv.x, -(x.x * wv.y))};
+                v[0][i] = V{u.x + xt.x, u.y + xt.y};
+                v[1][i] = V{u.x - xt.x, u.y - xt.y};
+            }
+        }
+        if constexpr (P3 > 1) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (j >= J) break;
+                const V x0 = v[j][0];
+                V av[pairs], bv[pairs], dc = x0;
+#pragma unroll
+                for (int n = 1; n <= pairs; ++n) {
+                    const V xa = v[j][n], xb = v[j][P3 - n];
+                    av[n - 1] = V{xa.x + xb.x, xa.y + xb.y};
+                    bv[n - 1] = V{xa.x - xb.x, xa.y - xb.y};
+                    dc.x += av[n - 1].x;
+                    dc.y += av[n - 1].y;
+                }
+                v[j][0] = dc;
+#pragma unroll
+                for (int kk = 1; kk <= pairs; ++kk) {
+                    V A = x0, S = {0, 0};
+#pragma unroll
+                    for (int n = 1; n <= pairs; ++n) {
+                        const V c = tw3[(n - 1) * KP + (kk - 1)];
+                        A.x = fma(av[n - 1].x, c.x, A.x);
+                        A.y = fma(av[n - 1].y, c.x, A.y);
+                        S.x = fma(bv[n - 1].x, c.y, S.x);
+                        S.y = fma(bv[n - 1].y, c.y, S.y);
+                    }
+                    v[j][kk] = V{A.x + S.y, A.y - S.x};
+                    v[j][P3 - kk] = V{A.x - S.y, A.y + S.x};
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int i = 0; i < P3; ++i)
+                if (j < J) __stcg(dst + base + i * S3 + j * HS2, v[j][i]);
+    }
+}
+
+template <typename T>
+__device__ __noinline__ void store_fused(const typename C2<T>::t* s, typename C2<T>::t* dst,
+                                         const StageDesc& st, int TS, int a2,
+                                         const typename C2<T>::t* tw2, int a3,
+                                         const typename C2<T>::t* tw3)
+{
+    switch (a3 >= 0 ? st.ax[a3].P : 1) {
+        case 3: store_fused_p<T, 3>(s, dst, st, TS, a2, tw2, a3, tw3); break;
+        case 5: store_fused_p<T, 5>(s, dst, st, TS, a2, tw2, a3, tw3); break;
+        case 7: store_fused_p<T, 7>(s, dst, st, TS, a2, tw2, a3, tw3); break;
+        case 9: store_fused_p<T, 9>(s, dst, st, TS, a2, tw2, a3, tw3); break;
+        default: store_fused_p<T, 1>(s, dst, st, TS, a2, tw2, -1, tw3); break;
+    }
+}
+
 // The tensor-core axes of a one-pass tile (run after its other axes: the axes of the
-// prime-factor map commute), then the tile's store to the bins.  When the stage has a
-// power-of-two axis (P2 > 1), its last radix-2 stage (half-size P2 / 2, twiddles tw2 in
-// shared memory) runs here: each thread reads a butterfly's two inputs and stores its two
-// outputs, which saves a trip through shared memory.  Out of line, so that the kernel holds
-// nothing live across the MMA code.
+// prime-factor map commute), then the tile's fused store to the bins (store_fused, with the
+// deferred radix-2 stage of axis a2 and the small odd axis a3).  Out of line, so that the
+// kernel holds nothing live across the MMA code.
 __device__ __noinline__ void tc_axes_store(float2* s, const BucketArgs& a, int d, int64_t slot,
-                                           int TS, const float2* tw2, int P2, int log2P2, int LS2)
+                                           int TS, int a2, const float2* tw2, int a3,
+                                           const float2* tw3)
 {
     const StageDesc& st = a.pd.st[d];
     const float2* twg = reinterpret_cast<const float2*>(a.tw);
@@ -609,30 +722,7 @@ __device__ __noinline__ void tc_axes_store(float2* s, const BucketArgs& a, int d
         const AxisDesc& A = st.ax[ax];
         if (A.tc) odd_axis_tc(s, twg + A.tw_off, A.P, A.S, TS);  // one pass: stride A.S
     }
-    float2* dst = reinterpret_cast<float2*>(a.bins) + slot;
-    if (P2 <= 1) {
-        for (int e = threadIdx.x; e < TS; e += blockDim.x) __stcg(dst + e, s[e]);
-        return;
-    }
-    const int H = P2 >> 1, M = TS / P2;
-    const float invM = 1.0f / (float)M, invLS = 1.0f / (float)LS2;
-    for (int w = threadIdx.x; w < M * H; w += blockDim.x) {
-        int k, m;
-        if (LS2 == 1) {
-            k = w & (H - 1);
-            m = w >> (log2P2 - 1);
-        } else {
-            k = fdivmod(w, M, invM, &m);
-        }
-        int lo = 0;
-        const int hi = LS2 == 1 ? m : fdivmod(m, LS2, invLS, &lo);
-        const int base = LS2 == 1 ? m * P2 : lo + hi * LS2 * P2;
-        const int p0 = base + k * LS2, p1 = p0 + H * LS2;
-        const float2 u = s[p0], x = s[p1], wv = tw2[k];
-        const float2 xt = {fmaf(x.x, wv.x, x.y * wv.y), fmaf(x.y, wv.x, -(x.x * wv.y))};
-        __stcg(dst + p0, float2{u.x + xt.x, u.y + xt.y});
-        __stcg(dst + p1, float2{u.x - xt.x, u.y - xt.y});
-    }
+    store_fused<float>(s, reinterpret_cast<float2*>(a.bins) + slot, st, TS, a2, tw2, a3, tw3);
 }
 
 __device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc, int bytes)
@@ -707,7 +797,7 @@ __global__ void __launch_bounds__(512, 1) bucketize_kernel(const __grid_constant
         const V* twg = reinterpret_cast<const V*>(a.tw);
         int off = 0;
         for (int ax = a0; ax < a1; ++ax) {
-            const int n = axis_tw_smem(st.ax[ax].P, st.ax[ax].pow2, st.ax[ax].tc);
+            const int n = axis_tw_smem(st.ax[ax].P, st.ax[ax].pow2, st.ax[ax].tc, st.ax[ax].gmem);
             for (int t = threadIdx.x; t < n; t += blockDim.x) tws[off + t] = twg[st.ax[ax].tw_off + t];
             off += (n + 1) & ~1;
         }
@@ -829,40 +919,54 @@ loaded:
 
     bool stage_tc = false;  // stages with tensor-core axes are one-pass (whole stage, to the bins)
     for (int ax = a0; ax < a1; ++ax) stage_tc |= st.ax[ax].tc != 0;
-    int p2 = 1, log2p2 = 0, ls2 = 1;
+    // a tile holding the whole stage (one pass, straight to the bins) defers the last radix-2
+    // stage of its power-of-two axis and its first small odd axis to the fused store
+    const bool whole = Tb == 1 && Ta == 1 && a0 == 0 && a1 == st.n_axes && ps.dst_bins;
+    int a2 = -1, a3 = -1;
     const V* tw2 = nullptr;
+    const V* tw3 = nullptr;
     int off = 0;
     for (int ax = a0; ax < a1; ++ax) {
         const AxisDesc& A = st.ax[ax];
         const int LS = Tb * (A.S / Sb);
         if (A.pow2) {
-            // with tensor-core axes, the last radix-2 stage runs in the store (tc_axes_store)
-            const bool fuse = TC && stage_tc;
-            if (fuse) {
-                p2 = A.P;
-                log2p2 = A.log2P;
-                ls2 = LS;
+            const bool defer = whole;
+            if (defer) {
+                a2 = ax;
                 tw2 = tws + off;
             }
-            axis_fft_pow2<T>(s, tws + off, A.P, A.log2P, LS, TS, fuse ? A.log2P - 1 : A.log2P);
+            axis_fft_pow2<T>(s, tws + off, A.P, A.log2P, LS, TS, defer ? A.log2P - 1 : A.log2P);
         } else if (A.P > 1) {
             if (A.P <= 9) {
-                odd_small<T>(s, tws + off, A.P, LS, TS);
+                if (whole && a3 < 0) {
+                    a3 = ax;
+                    tw3 = tws + off;
+                } else {
+                    odd_small<T>(s, tws + off, A.P, LS, TS);
+                }
             } else {
+                // the matrix of a larger odd axis: in shared memory, or read from the plan
+                // table in global memory (gmem)
+                const V* twa = A.gmem ? reinterpret_cast<const V*>(a.tw) + A.tw_off : tws + off;
                 if constexpr (sizeof(T) == 4) {
-                    if (!(TC && A.tc)) odd_axis_f32<8>(s, tws + off, A.P, LS, TS);
+                    if (!(TC && A.tc)) odd_axis_f32<8>(s, twa, A.P, LS, TS);
                 } else
-                    axis_dft_odd_dispatch<T>(s, tws + off, A.P, LS, TS);
+                    axis_dft_odd_dispatch<T>(s, twa, A.P, LS, TS);
             }
         }
-        off += (axis_tw_smem(A.P, A.pow2, A.tc) + 1) & ~1;
+        off += (axis_tw_smem(A.P, A.pow2, A.tc, A.gmem) + 1) & ~1;
     }
     if constexpr (TC && sizeof(T) == 4) {
         if (stage_tc) {
-            tc_axes_store(reinterpret_cast<float2*>(s), a, d, slot, TS,
-                          reinterpret_cast<const float2*>(tw2), p2, log2p2, ls2);
+            tc_axes_store(reinterpret_cast<float2*>(s), a, d, slot, TS, a2,
+                          reinterpret_cast<const float2*>(tw2), a3,
+                          reinterpret_cast<const float2*>(tw3));
             return;
         }
+    }
+    if (whole) {
+        store_fused<T>(s, reinterpret_cast<V*>(a.bins) + slot, st, TS, a2, tw2, a3, tw3);
+        return;
     }
 
     V* dst = reinterpret_cast<V*>(ps.dst_bins ? a.bins : a.scratch);
@@ -955,7 +1059,7 @@ __global__ void __launch_bounds__(512, 1)
             const V* twg = reinterpret_cast<const V*>(a.tw);
             int off = 0;
             for (int ax = 0; ax < st.n_axes; ++ax) {
-                const int n = axis_tw_smem(st.ax[ax].P, st.ax[ax].pow2, st.ax[ax].tc);
+                const int n = axis_tw_smem(st.ax[ax].P, st.ax[ax].pow2, st.ax[ax].tc, st.ax[ax].gmem);
                 for (int t = threadIdx.x; t < n; t += blockDim.x) tws[off + t] = twg[st.ax[ax].tw_off + t];
                 off += (n + 1) & ~1;
             }
@@ -979,34 +1083,35 @@ __global__ void __launch_bounds__(512, 1)
         const int64_t slot = (int64_t)sig * a.pd.y_per_sig + st.y_off + (int64_t)r * st.B;
         bool stage_tc = false;
         for (int ax = 0; ax < st.n_axes; ++ax) stage_tc |= st.ax[ax].tc != 0;
-        int p2 = 1, log2p2 = 0, ls2 = 1;
+        int a2 = -1, a3 = -1;
         const V* tw2 = nullptr;
+        const V* tw3 = nullptr;
         int off = 0;
         for (int ax = 0; ax < st.n_axes; ++ax) {
             const AxisDesc& A = st.ax[ax];
             if (A.pow2) {
-                const bool fuse = TC && stage_tc;
-                if (fuse) {
-                    p2 = A.P;
-                    log2p2 = A.log2P;
-                    ls2 = A.S;
-                    tw2 = tws + off;
-                }
-                axis_fft_pow2<float>(s, tws + off, A.P, A.log2P, A.S, TS, fuse ? A.log2P - 1 : A.log2P);
+                a2 = ax;
+                tw2 = tws + off;
+                axis_fft_pow2<float>(s, tws + off, A.P, A.log2P, A.S, TS, A.log2P - 1);
             } else if (A.P > 1) {
-                if (A.P <= 9)
-                    odd_small<float>(s, tws + off, A.P, A.S, TS);
-                else if (!(TC && A.tc))
-                    odd_axis_f32<8>(s, tws + off, A.P, A.S, TS);
+                if (A.P <= 9) {
+                    if (a3 < 0) {
+                        a3 = ax;
+                        tw3 = tws + off;
+                    } else {
+                        odd_small<float>(s, tws + off, A.P, A.S, TS);
+                    }
+                } else if (!(TC && A.tc)) {
+                    odd_axis_f32<8>(s, A.gmem ? reinterpret_cast<const V*>(a.tw) + A.tw_off : tws + off,
+                                    A.P, A.S, TS);
+                }
             }
-            off += (axis_tw_smem(A.P, A.pow2, A.tc) + 1) & ~1;
+            off += (axis_tw_smem(A.P, A.pow2, A.tc, A.gmem) + 1) & ~1;
         }
-        if (TC && stage_tc) {
-            tc_axes_store(s, a, d, slot, TS, tw2, p2, log2p2, ls2);
-        } else {
-            V* dst = reinterpret_cast<V*>(a.bins) + slot;
-            for (int e = threadIdx.x; e < TS; e += blockDim.x) __stcg(dst + e, s[e]);
-        }
+        if (TC && stage_tc)
+            tc_axes_store(s, a, d, slot, TS, a2, tw2, a3, tw3);
+        else
+            store_fused<float>(s, reinterpret_cast<V*>(a.bins) + slot, st, TS, a2, tw2, a3, tw3);
         __syncthreads();  // this region is read for the last time above
         if (wn < n_items) {
             if (cur == 0)

@@ -82,9 +82,9 @@ inline int64_t pfa_tw_elems(int32_t P, int tc)
 {
     return pfa_even(axis_tw_count(P, pfa_is_pow2(P) ? 1 : 0, tc));
 }
-inline int64_t pfa_tw_smem(int32_t P, int tc)
+inline int64_t pfa_tw_smem(int32_t P, int tc, int gmem)
 {
-    return pfa_even(axis_tw_smem(P, pfa_is_pow2(P) ? 1 : 0, tc));
+    return pfa_even(axis_tw_smem(P, pfa_is_pow2(P) ? 1 : 0, tc, gmem));
 }
 
 struct PassPlan {
@@ -115,8 +115,12 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
     // passes of a two-pass stage keep every axis on the FMA pipes
     const int fp32 = esz == 8 ? 1 : 0;
     auto tc_of = [&](int32_t P) { return allow_tc && !pfa_is_pow2(P) && odd_tc(P, fp32) ? 1 : 0; };
+    // a one-pass tile filling more than half of shared memory (one CTA per SM): the matrices
+    // of odd axes above P = 9 stay in global memory
+    const bool big = 2 * pfa_even(B) * (int64_t)esz > (int64_t)max_smem;
+    auto gmem_of = [&](int32_t P) { return big && !pfa_is_pow2(P) && P > 9 ? 1 : 0; };
     int64_t tw_one = 0;
-    for (int i = 0; i < n; ++i) tw_one += pfa_tw_smem(Ps[i], tc_of(Ps[i]));
+    for (int i = 0; i < n; ++i) tw_one += pfa_tw_smem(Ps[i], tc_of(Ps[i]), gmem_of(Ps[i]));
     int32_t order[kMaxAxes];
     int split = n;
     for (int i = 0; i < n; ++i) order[i] = Ps[i];
@@ -129,9 +133,9 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
             for (int i = 0; i < n; ++i) {
                 if (mask >> i & 1) {
                     pi *= Ps[i];
-                    twi += pfa_tw_smem(Ps[i], 0);
+                    twi += pfa_tw_smem(Ps[i], 0, 0);
                 } else {
-                    two += pfa_tw_smem(Ps[i], 0);
+                    two += pfa_tw_smem(Ps[i], 0, 0);
                 }
             }
             const int64_t po = B / pi;
@@ -167,9 +171,10 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
         A.rur = (int32_t)(Bp % B);
         A.crt = (int32_t)((Bp * pfa_inv_mod(Bp % A.P, A.P)) % B);
         A.tc = one_pass ? tc_of(A.P) : 0;
+        A.gmem = A.tc || (one_pass && gmem_of(A.P)) ? 1 : 0;
         A.tw_off = *tw_cursor;
         *tw_cursor += (int32_t)pfa_tw_elems(A.P, A.tc);
-        (i < split ? tw_in : tw_out) += pfa_tw_smem(A.P, A.tc);
+        (i < split ? tw_in : tw_out) += pfa_tw_smem(A.P, A.tc, A.gmem);
     }
     auto note = [&](PassPlan* l, int64_t tile, int64_t tw) {
         const size_t b = (size_t)(pfa_even(tile) + tw) * esz;
@@ -186,7 +191,7 @@ inline bool pfa_layout_stage(StageDesc* s, size_t esz, int max_smem, int64_t til
     int64_t inner = 1, outer = 1;
     for (int i = 0; i < split; ++i) inner *= s->ax[i].P;
     for (int i = split; i < n; ++i) outer *= s->ax[i].P;
-    if (max_tile > 0 && max_tile < tile_target) tile_target = max_tile;
+    if (max_tile > 0) tile_target = max_tile;  // the caller's B-tile sets the two-pass tiles
     int64_t Tb = tile_target / outer;
     if (Tb < 1) Tb = 1;
     if (Tb > inner) Tb = inner;

@@ -31,6 +31,7 @@ struct AxisDesc {
     int32_t crt;     // CRT coefficient
     int32_t tw_off;  // offset of this axis' twiddles in the plan twiddle table
     int32_t tc;      // 1: odd axis done on the tensor cores (fragment table, see odd_tc)
+    int32_t gmem;    // 1: the axis' table is read from global memory (not copied to shared)
 };
 
 // One DFT pass over a contiguous range of axes [a0, a1) of a stage.  A tile is Tb
@@ -131,12 +132,17 @@ __host__ __device__ __forceinline__ int axis_tw_count(int P, int pow2, int tc)
     if (tc) return tc_mtiles(P) * tc_ktiles(P) * 256;  // 8-byte entries
     return pow2 ? (P >> 1) : ((P - 1) >> 1) * odd_row_len(P);
 }
-// Entries of the axis' table that the bucketization copies into shared memory: the fragment
-// tables of tensor-core axes stay in global memory (read through the read-only cache), so
-// that shared memory keeps room for the L1 lines of the gather's copies in flight.
-__host__ __device__ __forceinline__ int axis_tw_smem(int P, int pow2, int tc)
+// Entries of the axis' table that the bucketization copies into shared memory.  Tables with
+// gmem set stay in global memory and are read through the read-only cache: the fragment
+// tables of tensor-core axes, and the conjugate-pair matrices of odd axes above P = 9 in
+// stages whose one-pass tile fills more than half of shared memory -- there every KB of
+// shared memory beyond the tile takes L1 away from the gather's loads in flight (measured:
+// 16 KB more made the gather of a 16k-sample tile 16 % slower, 36 KB 56 %), while smaller
+// tiles (two-pass stages, two or more CTAs per SM) read the matrices faster from shared
+// memory.
+__host__ __device__ __forceinline__ int axis_tw_smem(int P, int pow2, int tc, int gmem)
 {
-    return tc ? 0 : axis_tw_count(P, pow2, 0);
+    return (tc || gmem) ? 0 : axis_tw_count(P, pow2, 0);
 }
 // v = hi + lo + e with hi = v cut to TF32 (sign, exponent, 10 mantissa bits) and lo the
 // exact remainder cut to TF32 as well, so |e| < 2^-20 |v|

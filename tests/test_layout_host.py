@@ -98,14 +98,17 @@ def test_twiddle_offsets_and_sizes(probe, B, allow):
     assert lay["tw_total"] == off
 
 
-def test_tensor_core_tables_stay_out_of_shared_memory(probe):
-    """The one-pass launch's shared memory holds the tile plus the FMA axes' twiddles only:
-    B = 16383 (127, 43, 3) needs the tile and the 3-point table with tensor-core axes, and
-    the 127- and 43-point matrices as well without."""
+def test_large_odd_tables_stay_out_of_shared_memory(probe):
+    """The one-pass launch's shared memory holds the tile plus the radix-2 and small odd
+    axes' twiddles only: B = 16383 (127, 43, 3) needs the tile and the 3-point table, with
+    tensor-core axes or without (the 127- and 43-point tables are read from global memory
+    either way)."""
     with_tc, without = probe(16383), probe(16383, allow_tc=0)
     tile = (16383 + 1) * 8
     assert with_tc["smem1"] == tile + 2 * 8  # the 3-point table: one pair row of 2
-    assert without["smem1"] > with_tc["smem1"] + 63 * 64 * 8
+    assert without["smem1"] == with_tc["smem1"]
+    # B = 16512 (43, 3, 128): the 3-point table and the 64 radix-2 twiddles
+    assert probe(16512)["smem1"] == (16512 + 64 + 2) * 8
 
 
 @pytest.mark.parametrize("B", [16512, 16383, 2550])
