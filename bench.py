@@ -66,7 +66,7 @@ def parse():
                     help="length of the serving-mix Poisson stream")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large single-signal measurement (N = 511*512*513)")
-    ap.add_argument("--only", choices=["large", "oneshot", "locate", "noise", "dsfft", "mix",
+    ap.add_argument("--only", choices=["large", "sweep", "oneshot", "locate", "noise", "dsfft", "mix",
                                        "serve", "dft"],
                     default=None,
                     help="run only that block (a short run for profiling) and print its JSON")
@@ -315,6 +315,97 @@ def measure_large(sfft, hbm_peak, reps=10):
                                             if dram else None),
                        "sector_efficiency": (alg / dram if dram else None),
                        "peak_gbs": hbm_peak}}
+
+
+def errors_vs(idx, val, n, ref_idx, ref_val, K):
+    """L0, L1 and L2 of one result against a reference result over the union of the supports
+    (L1 = sum |difference| / K, L2 relative to the reference's norm)."""
+    got = dict(zip(idx[:n].tolist(), val[:n].tolist()))
+    ref = dict(zip(ref_idx.tolist(), ref_val.tolist()))
+    keys = sorted(set(got) | set(ref))
+    d = np.array([got.get(k, 0) - ref.get(k, 0) for k in keys]) if keys else np.zeros(1)
+    nr = np.linalg.norm(np.array(list(ref.values()))) if ref else 1.0
+    return {"l0": len(set(got) ^ set(ref)), "l1": float(np.abs(d).sum() / max(K, 1)),
+            "l2": float(np.linalg.norm(d) / (nr if nr > 0 else 1.0))}
+
+
+def measure_large_sweep(sfft, reps=3):
+    """The large-signal configuration over its SNR sweep: N = 511*512*513 complex64, f =
+    (511, 512, 513), 10 delays per stage (0, 1, 8 random), K = 10,000, |xhat| ~ U[1,10], SNR in
+    {inf, 30, 10} dB (one sparse spectrum, one draw of white noise scaled per SNR).  Per SNR:
+    the FP32 path (FP64 location and fit; ordered, compensated peeling) and, beside it, the
+    same with unordered float atomics in the peeling subtraction, and the plain FP64 path --
+    each with L0/L1/L2 against the truth, and the FP32 results against the FP64 path's.
+    Then the location precision experiment on the exactly sparse signal with ARG locate
+    (delays 0 and 1 of every stage): the angle in FP64 or FP32, with or without the snap to
+    the bin's candidate set, on FP32 bins and on FP64 bins."""
+    import torch
+    base = synth.config_problem("rffast_134217216", seed=5, snr_db=None)
+    N, f, K = base.N, base.f, base.K
+    w = synth.awgn(N, 1.0, np.random.default_rng(555))
+    truth_i, truth_v = base.support, base.values
+    out = {"workload": "rffast_134217216: N=511*512*513 complex64 (1.07 GB), 10 delays/stage, "
+                       "K=10000, |xhat|~U[1,10]; SNR sweep {inf, 30, 10} dB", "snr": {}}
+
+    def run(plan, x):
+        o = plan.execute(x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            o = plan.execute(x)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) / reps * 1e3
+        inf = o[2].cpu().numpy()
+        n = int(inf[0])
+        return ms, o[0].cpu().numpy(), o[1].cpu().numpy().astype(np.complex128), n, int(inf[1])
+
+    for snr in (None, 30.0, 10.0):
+        var = synth.noise_variance(truth_v, snr)
+        x = base.x + np.sqrt(var) * w if var > 0 else base.x
+        x32 = torch.from_numpy(x.astype(np.complex64)).cuda()
+        rec = {"noise_var": var}
+        res = {}
+        for name, kw in (("fp32", {}), ("fp32_atomic_peel", {"peel_atomic": True})):
+            plan = sfft.Plan(N, K, f, base.delays, precision="fp32", locate="ml", noise_var=var, **kw)
+            ms, i, v, n, st = run(plan, x32)
+            plan.close()
+            res[name] = (i, v, n)
+            rec[name] = {"ms_per_signal": ms, "status": st, "count": n,
+                         "vs_truth": errors_vs(i, v, n, truth_i, truth_v, K)}
+        del x32
+        x64 = torch.from_numpy(x.astype(np.complex64).astype(np.complex128)).cuda()
+        plan = sfft.Plan(N, K, f, base.delays, precision="fp64", dtype="c128", locate="ml",
+                         noise_var=var)
+        ms, i64, v64, n64, st = run(plan, x64)
+        plan.close()
+        del x64
+        rec["fp64_plain"] = {"ms_per_signal": ms, "status": st, "count": n64,
+                             "vs_truth": errors_vs(i64, v64, n64, truth_i, truth_v, K)}
+        for name in ("fp32", "fp32_atomic_peel"):
+            i, v, n = res[name]
+            rec[name]["vs_fp64_plain"] = errors_vs(i, v, n, i64[:n64], v64[:n64], K)
+        out["snr"]["inf" if snr is None else f"{snr:g}dB"] = rec
+    # location precision on the exactly sparse signal, ARG locate
+    loc = {}
+    x32 = torch.from_numpy(base.x.astype(np.complex64)).cuda()
+    for mode, name in ((0, "fp64_angle_snapped"), (1, "fp32_angle_snapped"),
+                       (2, "fp64_angle_unsnapped"), (3, "fp32_angle_unsnapped")):
+        plan = sfft.Plan(N, K, f, base.delays, precision="fp32", locate="arg", arg_mode=mode)
+        ms, i, v, n, st = run(plan, x32)
+        plan.close()
+        loc[f"fp32_bins/{name}"] = {"status": st, "count": n,
+                                    "l0_vs_truth": errors_vs(i, v, n, truth_i, truth_v, K)["l0"]}
+    del x32
+    x64 = torch.from_numpy(base.x).cuda()
+    for mode, name in ((0, "fp64_angle_snapped"), (2, "fp64_angle_unsnapped")):
+        plan = sfft.Plan(N, K, f, base.delays, precision="fp64", dtype="c128", locate="arg",
+                         arg_mode=mode)
+        ms, i, v, n, st = run(plan, x64)
+        plan.close()
+        loc[f"fp64_bins/{name}"] = {"status": st, "count": n,
+                                    "l0_vs_truth": errors_vs(i, v, n, truth_i, truth_v, K)["l0"]}
+    out["arg_locate_precision"] = loc
+    return out
 
 
 def measure_oneshot(sfft, batch=64, steps=20, warmup=3):
@@ -948,11 +1039,16 @@ def run_gpu(args):
         serving_mix = {"error": repr(exc)[:200]}
 
     large = None
+    large_sweep = None
     if not args.no_large:
         try:
             large = measure_large(sfft, hbm_peak)
         except Exception as exc:  # report, never fall back
             large = {"error": repr(exc)[:200]}
+        try:
+            large_sweep = measure_large_sweep(sfft)
+        except Exception as exc:  # report, never fall back
+            large_sweep = {"error": repr(exc)[:200]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1010,6 +1106,7 @@ def run_gpu(args):
         "e2e": e2e,
         "serving": serving,
         "large_signal": large,
+        "large_signal_snr_sweep": large_sweep,
         "oneshot": oneshot,
         "locate_ml_vs_kay": locate_modes,
         "noise_auto": noise_auto,
@@ -1038,6 +1135,8 @@ def run_only(args):
         peak = 6800.0
     if args.only == "large":
         out = measure_large(sfft, peak, reps=max(1, args.steps))
+    elif args.only == "sweep":
+        out = measure_large_sweep(sfft, reps=max(1, args.steps))
     elif args.only == "locate":
         out = measure_locate_modes(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     elif args.only == "noise":

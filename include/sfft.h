@@ -160,6 +160,12 @@ typedef struct {
     int32_t classify_lanes;   /* lanes of a warp that search one bin's L candidates in the
                                  first peeling round (ML locate): 1, 2, 4, 8, 16 or 32; 0
                                  (default) = chosen per tile from its non-zero bins, L and R */
+    int32_t arg_mode;         /* SFFT_LOCATE_ARG precision experiment (Sec. 3.2 subproblem 2):
+                                 0 (default) = the angle of Y(1) conj(Y(0)) in FP64, snapped to
+                                 the bin's candidate set {j + q B_d}; bit 0 = the angle and its
+                                 scaling by N / 2 pi in FP32; bit 1 = no snap, f = the integer
+                                 nearest the estimate.  Modes 1-3 exist to measure what the FP64
+                                 angle and the snap buy; they are not meant for use */
 } sfft_opts;
 
 /* Fill *opts with the defaults above. */

@@ -234,6 +234,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         return SFFT_EINVAL;
     if (o.classify_lanes < 0 || o.classify_lanes > 32 || (o.classify_lanes & (o.classify_lanes - 1)))
         return SFFT_EINVAL;
+    if (o.arg_mode < 0 || o.arg_mode > 3) return SFFT_EINVAL;
     DevInfo di;
     int rc = device_info(&di);
     if (rc) return rc;
@@ -264,6 +265,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     pd.kay_m = o.locate == SFFT_LOCATE_KAY ? o.kay_m : 0;
     pd.noise_auto = o.noise_auto;
     pd.peel_atomic = o.peel_atomic ? 1 : 0;
+    pd.arg_mode = o.arg_mode;
     {
         // median of Gamma(R, 1): CDF(x) = 1 - e^{-x} sum_{k<R} x^k / k! = 1/2, by Newton's
         // method from x = R - 1/3 (the density x^{R-1} e^{-x} / (R-1)! is the derivative)

@@ -331,15 +331,30 @@ __device__ void locate_phase_thread(const DecodeArgs& a, int32_t* ctr, const Dec
     } else {
         // ARG (FFAST phase encoding): angle of y(1) conj(y(0)) times N / 2 pi
         const V u0 = __ldcg(Yb + (int64_t)st.r0 * B), u1 = __ldcg(Yb + (int64_t)st.r1 * B);
-        const double rx = (double)u1.x * u0.x + (double)u1.y * u0.y;
-        const double ry = (double)u1.y * u0.x - (double)u1.x * u0.y;
-        fe = atan2(ry, rx) * (double)N / kTwoPi;
+        if (pd.arg_mode & 1) {
+            // angle and scaling in FP32 (a precision experiment, not the library's path)
+            const float rxf = (float)u1.x * (float)u0.x + (float)u1.y * (float)u0.y;
+            const float ryf = (float)u1.y * (float)u0.x - (float)u1.x * (float)u0.y;
+            fe = (double)(atan2f(ryf, rxf) * ((float)N / 6.28318531f));
+        } else {
+            const double rx = (double)u1.x * u0.x + (double)u1.y * u0.y;
+            const double ry = (double)u1.y * u0.x - (double)u1.x * u0.y;
+            fe = atan2(ry, rx) * (double)N / kTwoPi;
+        }
     }
-    // the bin's candidate j + q B nearest fe
-    const double qd = floor((fe - (double)j) / (double)B + 0.5);
-    int64_t q = (int64_t)qd % L;
-    if (q < 0) q += L;
-    const int64_t f = (int64_t)j + q * B;
+    int64_t f;
+    if (pd.locate == 0 && (pd.arg_mode & 2)) {
+        // no residue snap (a precision experiment): the integer nearest the estimate, which
+        // the single-ton test rejects unless it is the bin's frequency
+        f = (int64_t)floor(fe + 0.5) % N;
+        if (f < 0) f += N;
+    } else {
+        // the bin's candidate j + q B nearest fe
+        const double qd = floor((fe - (double)j) / (double)B + 0.5);
+        int64_t q = (int64_t)qd % L;
+        if (q < 0) q += L;
+        f = (int64_t)j + q * B;
+    }
 #pragma unroll
     for (int r = 0; r < kMaxDelays; ++r)
         if (r < R) ar[r] = delay_phasor<T>(a, f, st.tau[r]);

@@ -90,6 +90,9 @@ struct PlanDesc {
     int32_t peel_atomic;     // 1: peeling subtracts with unordered atomics on the bins;
                              // 0: per-bin subtraction lists applied in frequency order with
                              //    compensated sums (deterministic)
+    int32_t arg_mode;        // ARG locate: bit 0 = angle in FP32 (else FP64), bit 1 = no
+                             // residue snap (f = the integer nearest the estimate)
+    int32_t pad3;
     StageDesc st[kMaxStages];
 };
 

@@ -561,3 +561,18 @@ def test_shuffled_batch_host_buffers(sfft):
         np.testing.assert_array_equal(hidx[i][:n], q.support)
     pa.close()
     pb.close()
+
+
+def test_arg_mode_precision_experiment(sfft, oracle_mod):
+    """The ARG-locate precision modes run and, on N = 20*21*23 exactly sparse (small N, so
+    even the FP32 angle unsnapped is exact), every mode recovers the oracle's support; invalid
+    modes are refused."""
+    p = synth.config_problem("ffast_exact_9660", seed=3)
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x)
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_mod.OracleOpts(locate=0, eta=3e-3))
+    for mode in range(4):
+        plan, idx, val, info = run_plan(sfft, p, precision="fp32", locate="arg", arg_mode=mode)
+        np.testing.assert_array_equal(idx, ref["idx"])
+        plan.close()
+    with pytest.raises(sfft.SfftError):
+        sfft.Plan(p.N, p.K, p.f, p.delays, locate="arg", arg_mode=4)
