@@ -195,7 +195,9 @@ __device__ void locate_ml_group(const DecodeArgs& a, int32_t* ctr, const DecodeW
     const V* W = wtab + (st.wtab_off - wtab_base);
     T best = (T)-1;
     int bq = 0;
-    for (int q = li; q < L; q += G) {
+    // the score of candidate q: the sum over delays in two interleaved halves (even and odd
+    // r), as before; two candidates (q, q + G) per trip so that their FMA chains interleave
+    auto score = [&](int q) {
         T cx0 = 0, cy0 = 0, cx1 = 0, cy1 = 0;
 #pragma unroll
         for (int r = 0; r < RM; r += 2) {
@@ -212,9 +214,24 @@ __device__ void locate_ml_group(const DecodeArgs& a, int32_t* ctr, const DecodeW
             }
         }
         const T cx = cx0 + cx1, cy = cy0 + cy1;
-        const T sc = cx * cx + cy * cy;
-        if (sc > best) {
-            best = sc;
+        return cx * cx + cy * cy;
+    };
+    int q = li;
+    for (; q + G < L; q += 2 * G) {
+        const T s0 = score(q), s1 = score(q + G);
+        if (s0 > best) {
+            best = s0;
+            bq = q;
+        }
+        if (s1 > best) {
+            best = s1;
+            bq = q + G;
+        }
+    }
+    if (q < L) {
+        const T s0 = score(q);
+        if (s0 > best) {
+            best = s0;
             bq = q;
         }
     }
@@ -416,14 +433,14 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
     }
     int64_t cw[kMaxStages];
     uint8_t open[kMaxStages];
+    uint8_t stt[kMaxStages];
+#pragma unroll
+    for (int e = 0; e < kMaxStages; ++e) stt[e] = e < D ? __ldcg(w.state + be[e]) : (uint8_t)1;
 #pragma unroll
     for (int e = 0; e < kMaxStages; ++e) {
-        cw[e] = -1;
-        open[e] = 0;
-        if (e < D) {
-            if (e != d) cw[e] = (int64_t)__ldcg((const long long*)w.cand + be[e]);
-            open[e] = __ldcg(w.state + be[e]) == 0;
-        }
+        // a bin's candidate word is written with its single-ton state and only read then
+        cw[e] = (e < D && e != d && stt[e] == 2) ? (int64_t)__ldcg((const long long*)w.cand + be[e]) : -1;
+        open[e] = stt[e] == 0;
     }
 #pragma unroll
     for (int e = 0; e < kMaxStages; ++e) {
@@ -452,7 +469,10 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
             }
             const int prev = atomicExch(w.sub_head + be[e], sl);
             __stcg(w.sub_ent + sl, int2{c, prev});
+            // the bin's first entry this round queues it for the next round
+            if (prev < 0) __stcg(((round & 1) ? w.list1 : w.list0) + atomicAdd(ctr + kCtrRoundBase + 3 * round + 0, 1), be[e]);
         }
+        return;
     }
 #pragma unroll
     for (int e = 0; e < kMaxStages; ++e) {
@@ -474,6 +494,7 @@ __device__ void peel_candidate(const DecodeArgs& a, int32_t* ctr, const DecodeWs
             }
         }
     }
+    // unordered atomics: the dirty flag's first setter queues the bin
     uint32_t was[kMaxStages];
 #pragma unroll
     for (int e = 0; e < kMaxStages; ++e) was[e] = (e < D && open[e]) ? atomicExch(w.dirty + be[e], 1u) : 1u;
@@ -707,14 +728,19 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
         for (int u = 0; u < NB; ++u) {
             const int bu = b + u * blockDim.x;
             if (bu >= b1) continue;
-            __stcg((long long*)w.cand + bu, -1ll);
-            __stcg(w.dirty + bu, 0u);
-            if (w.sub_head) __stcg(w.sub_head + bu, -1);
+            // per-bin decode state: the state of every bin; the subtraction list head (ordered
+            // peeling) or the dirty flag (atomic peeling) of the bins that can stay open; the
+            // candidate word is written only with a single-ton state
             __stcg(w.state + bu, (uint8_t)(z[u] ? 1 : 0));
-            if (z[u])
+            if (z[u]) {
                 atomicAdd(&s_res, 1);
-            else
+            } else {
                 s_nz[atomicAdd(&s_cnt, 1)] = bu;
+                if (pd.peel_atomic)
+                    __stcg(w.dirty + bu, 0u);
+                else
+                    __stcg(w.sub_head + bu, -1);
+            }
         }
     }
     __syncthreads();
@@ -771,7 +797,7 @@ __global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ Decod
         const int32_t* act = ((round - 1) & 1) ? w.list1 : w.list0;
         for (int i = wt; i < n_next; i += nw) {
             const int b = __ldcg(act + i);
-            __stcg(w.dirty + b, 0u);
+            if (pd.peel_atomic) __stcg(w.dirty + b, 0u);
             const bool zero = pd.peel_atomic ? bin_is_zero<T>(pd, Y, b, s_thr)
                                              : apply_and_test<T>(a, w, Y, b, s_thr);
             if (zero) {
