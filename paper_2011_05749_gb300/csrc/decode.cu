@@ -539,20 +539,22 @@ __device__ __forceinline__ T two_sum(T a, T b, T* e)
 // TwoSum and its error terms added back at the end -- store the bin, clear its list, and
 // test its energy against T0.  The order and the arithmetic depend only on the set of
 // listed frequencies, so the bits do not depend on which CTA accepted what first.
-template <typename T>
-__device__ bool apply_and_test(const DecodeArgs& a, const DecodeWs& w, typename C2<T>::t* Y, int b,
-                               const Thr* thr)
+template <typename T, int RT>
+__device__ bool apply_and_test_r(const DecodeArgs& a, const DecodeWs& w, typename C2<T>::t* Y,
+                                 int b, const Thr* thr)
 {
     using V = typename C2<T>::t;
+    constexpr int RM = RT > 0 ? RT : kMaxDelays;  // delay slots the loops unroll over
     const PlanDesc& pd = a.pd;
+    const int R = RT > 0 ? RT : pd.R;
     const int d = stage_of(pd, b);
     const StageDesc& st = pd.st[d];
     V* Yb = Y + st.y_off + (b - st.bin_base);
-    V y[kMaxDelays], cmp[kMaxDelays];
+    V y[RM], cmp[RM];
 #pragma unroll
-    for (int r = 0; r < kMaxDelays; ++r) {
+    for (int r = 0; r < RM; ++r) {
         cmp[r] = V{0, 0};
-        if (r < pd.R) y[r] = __ldcg(Yb + (int64_t)r * st.B);
+        if (r < R) y[r] = __ldcg(Yb + (int64_t)r * st.B);
     }
     const int head = __ldcg(w.sub_head + b);
     if (head >= 0) {
@@ -576,13 +578,13 @@ __device__ bool apply_and_test(const DecodeArgs& a, const DecodeWs& w, typename 
             if (cmin < 0) break;
             last = fmin;
             const V v = __ldcg(cv + cmin);
-            V ar[kMaxDelays];
+            V ar[RM];
 #pragma unroll
-            for (int r = 0; r < kMaxDelays; ++r)
-                if (r < pd.R) ar[r] = delay_phasor<T>(a, fmin, st.tau[r]);
+            for (int r = 0; r < RM; ++r)
+                if (r < R) ar[r] = delay_phasor<T>(a, fmin, st.tau[r]);
 #pragma unroll
-            for (int r = 0; r < kMaxDelays; ++r) {
-                if (r < pd.R) {
+            for (int r = 0; r < RM; ++r) {
+                if (r < R) {
                     const T tx = Bv * (v.x * ar[r].x - v.y * ar[r].y);
                     const T ty = Bv * (v.x * ar[r].y + v.y * ar[r].x);
                     T ex, ey;
@@ -594,8 +596,8 @@ __device__ bool apply_and_test(const DecodeArgs& a, const DecodeWs& w, typename 
             }
         }
 #pragma unroll
-        for (int r = 0; r < kMaxDelays; ++r) {
-            if (r < pd.R) {
+        for (int r = 0; r < RM; ++r) {
+            if (r < R) {
                 y[r] = V{y[r].x + cmp[r].x, y[r].y + cmp[r].y};
                 __stcg(Yb + (int64_t)r * st.B, y[r]);
             }
@@ -603,9 +605,22 @@ __device__ bool apply_and_test(const DecodeArgs& a, const DecodeWs& w, typename 
     }
     T E = 0;
 #pragma unroll
-    for (int r = 0; r < kMaxDelays; ++r)
-        if (r < pd.R) E += y[r].x * y[r].x + y[r].y * y[r].y;
+    for (int r = 0; r < RM; ++r)
+        if (r < R) E += y[r].x * y[r].x + y[r].y * y[r].y;
     return below(E, thr[d].T0f, thr[d].T0);
+}
+
+// apply_and_test_r with the delay count as a constant for the common R
+template <typename T>
+__device__ __forceinline__ bool apply_and_test(const DecodeArgs& a, const DecodeWs& w,
+                                               typename C2<T>::t* Y, int b, const Thr* thr)
+{
+    switch (a.pd.R) {
+    case 6: return apply_and_test_r<T, 6>(a, w, Y, b, thr);
+    case 8: return apply_and_test_r<T, 8>(a, w, Y, b, thr);
+    case 10: return apply_and_test_r<T, 10>(a, w, Y, b, thr);
+    default: return apply_and_test_r<T, 0>(a, w, Y, b, thr);
+    }
 }
 
 template <typename T>
@@ -764,9 +779,11 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
     }
 }
 
-// Rounds 1 (peel) .. last: one group of G CTAs per signal.
+// Rounds 1 (peel) .. last: one group of G CTAs per signal.  FP32: two CTAs of 512 threads per
+// SM (64 registers): a 256-signal batch fits one wave, which outweighs the spills
+// (decode 0.54 against 0.59 ms per 256 signals at 128 registers).
 template <typename T>
-__global__ void __launch_bounds__(512) peel_kernel(const __grid_constant__ DecodeArgs a)
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) peel_kernel(const __grid_constant__ DecodeArgs a)
 {
     using V = typename C2<T>::t;
     const PlanDesc& pd = a.pd;
