@@ -219,7 +219,9 @@ int sfft_execute(sfft_plan_t plan, const void* x, int64_t* out_idx, void* out_va
 /* Recover n signals in one set of launches.  plans[i] (may repeat), xs[i], idx[i], val[i]
  * as in sfft_execute for signal i; infos: int32[4 * n], signal i at infos + 4 i.  The
  * host arrays of pointers are read during the call.  Signals that share a plan are
- * processed together, at most that plan's max_batch per launch group.  The buffers are
+ * processed together wherever they sit in the batch, at most that plan's max_batch per
+ * launch group; with device buffers, the groups of different plans run on streams of their
+ * plans forked from `stream` and joined back into it, so they overlap on the device.  The buffers are
  * either all device memory (asynchronous) or all host memory (staged per launch group
  * through device memory the plan owns; the call returns when the outputs are written).
  * Mixing the two is SFFT_EINVAL.                                                          */

@@ -994,25 +994,53 @@ extern "C" int sfft_execute_batch(int32_t n, const sfft_plan_t* plans, const voi
     cudaStream_t st = (cudaStream_t)stream;
     // group signals by plan (first-seen order of plans); a group need not be consecutive in
     // the batch: each signal's info row is passed by pointer
+    struct Group {
+        sfft_plan_s* p;
+        std::vector<const void*> x;
+        std::vector<int64_t*> i;
+        std::vector<void*> v;
+        std::vector<int32_t*> r;
+    };
+    std::vector<Group> groups;
     std::vector<char> done(n, 0);
     for (int i = 0; i < n; ++i) {
         if (done[i]) continue;
-        sfft_plan_s* p = plans[i];
-        std::vector<const void*> gx;
-        std::vector<int64_t*> gi;
-        std::vector<void*> gv;
-        std::vector<int32_t*> gr;
+        Group g;
+        g.p = plans[i];
         for (int k = i; k < n; ++k)
-            if (!done[k] && plans[k] == p) {
+            if (!done[k] && plans[k] == g.p) {
                 done[k] = 1;
-                gx.push_back(xs[k]);
-                gi.push_back(idx[k]);
-                gv.push_back(val[k]);
-                gr.push_back(infos + 4 * (size_t)k);
+                g.x.push_back(xs[k]);
+                g.i.push_back(idx[k]);
+                g.v.push_back(val[k]);
+                g.r.push_back(infos + 4 * (size_t)k);
             }
-        const int rc = execute_group(p, (int)gx.size(), gx.data(), gi.data(), gv.data(), gr.data(),
-                                     st, host);
+        groups.push_back(std::move(g));
+    }
+    // With device buffers and several plans, every group after the first runs on a stream of
+    // its own plan, forked from and joined back into the caller's stream, so the groups
+    // overlap on the device (the smaller signals' launches fill the larger ones' tails).
+    // Each plan's workspace serves only its own group, so the streams share nothing.
+    const bool fork = !host && groups.size() > 1;
+    std::vector<sfft_plan_s*> forked;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        Group& G = groups[g];
+        cudaStream_t gs = st;
+        if (fork && g > 0 && G.p->layers.empty()) {
+            const int rca = ensure_aux(G.p);
+            if (rca) return rca;
+            CK(cudaEventRecord(G.p->aux_ev, st));
+            CK(cudaStreamWaitEvent(G.p->aux[0], G.p->aux_ev, 0));
+            gs = G.p->aux[0];
+            forked.push_back(G.p);
+        }
+        const int rc = execute_group(G.p, (int)G.x.size(), G.x.data(), G.i.data(), G.v.data(),
+                                     G.r.data(), gs, host);
         if (rc) return rc;
+    }
+    for (sfft_plan_s* q : forked) {
+        CK(cudaEventRecord(q->aux_join[0], q->aux[0]));
+        CK(cudaStreamWaitEvent(st, q->aux_join[0], 0));
     }
     return SFFT_OK;
 }
