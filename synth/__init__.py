@@ -58,6 +58,25 @@ def time_signal(N: int, support, values) -> np.ndarray:
     return np.fft.ifft(spec) * N
 
 
+def time_signal_torch(N: int, support, values, device="cuda", chunk: int = 1 << 26):
+    """The same time signal as time_signal, x_n = sum_k xhat_k e^{+2 pi i k n / N}, built
+    directly on a torch device in complex64 for N too large for numpy's FFT: each phase from
+    the exact integer residue (k n) mod N, then cos/sin in float64, in chunks of n."""
+    import torch
+    x = torch.empty(N, dtype=torch.complex64, device=device)
+    sup = torch.as_tensor(np.asarray(support, dtype=np.int64), device=device)
+    val = torch.as_tensor(np.asarray(values, dtype=np.complex128), device=device)
+    two_pi_over_n = 2.0 * math.pi / N
+    for n0 in range(0, N, chunk):
+        n = torch.arange(n0, min(N, n0 + chunk), dtype=torch.int64, device=device)
+        acc = torch.zeros(n.numel(), dtype=torch.complex128, device=device)
+        for k, v in zip(sup.tolist(), val.tolist()):
+            ph = torch.remainder(n * k, N).to(torch.float64) * two_pi_over_n
+            acc += complex(v) * torch.polar(torch.ones_like(ph), ph)
+        x[n0:n0 + n.numel()] = acc.to(torch.complex64)
+    return x
+
+
 def noise_variance(values, snr_db) -> float:
     if snr_db is None or math.isinf(snr_db):
         return 0.0

@@ -576,3 +576,78 @@ def test_arg_mode_precision_experiment(sfft, oracle_mod):
         plan.close()
     with pytest.raises(sfft.SfftError):
         sfft.Plan(p.N, p.K, p.f, p.delays, locate="arg", arg_mode=4)
+
+
+# ---------------------------------------------------------------------- edge cases against the oracle
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_four_stages_sixteen_delays(sfft, oracle_mod, prec):
+    """The plan's limits: four stages (N = 7*8*9*11, B = 792, 693, 616, 504) and sixteen
+    delays per stage (0, 1 and 14 random), K = 40 at 30 dB, ML locate: the oracle's
+    support, values, rounds and identifications."""
+    p = synth.make_problem(5544, (7, 8, 9, 11), 40, seed=3, R=16, delays="random",
+                           mag=(1.0, 10.0), snr_db=30.0)
+    kw = dict(precision=prec, locate="ml", noise_var=p.noise_var,
+              dtype="c64" if prec == "fp32" else "c128")
+    x = p.x.astype(np.complex64).astype(np.complex128) if prec == "fp32" else p.x
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, x)
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    plan, idx, val, info = run_plan(sfft, p, **kw)
+    assert_matches_oracle(idx, val, info, ref, prec)
+    np.testing.assert_array_equal(idx, p.support)
+    plan.close()
+
+
+def test_single_coefficient_and_single_bin_stage(sfft, oracle_mod):
+    """K = 1; a degenerate stage of one bin per delay (f = N, B = 1) beside the full-length
+    one (f = 1, B = N, the only co-prime partner); and the one-bin stage alone: the oracle's
+    support and values, exactly sparse, ARG locate."""
+    for f, seed in (((20, 21, 23), 4), ((9660, 1), 6), ((9660,), 7)):
+        p = synth.make_problem(9660, f, 1, seed=seed, R=3)
+        Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x)
+        kw = dict(precision="fp64", locate="arg", dtype="c128")
+        ref = oracle_mod.decode(p.N, p.f, p.delays, Y, 1, oracle_opts(oracle_mod, kw, p))
+        plan, idx, val, info = run_plan(sfft, p, **kw)
+        assert_matches_oracle(idx, val, info, ref, "fp64")
+        np.testing.assert_array_equal(idx, p.support)
+        plan.close()
+
+
+@pytest.mark.parametrize("K", [1100, 1300])
+def test_long_and_failing_peeling(sfft, oracle_mod, K):
+    """N = 20*21*23 with 6 delays and K close to and past what peeling resolves in
+    B ~ 450 bins per stage: K = 1100 takes 28 rounds and recovers everything; K = 1300 stops
+    with most bins unresolved (status incomplete).  Both: the oracle's support (the partial
+    one too), values, rounds, identifications and status."""
+    p = synth.make_problem(9660, (20, 21, 23), K, seed=5, R=6, delays="random", mag=(1.0, 10.0))
+    kw = dict(precision="fp32", locate="ml")
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x.astype(np.complex64).astype(np.complex128))
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    plan, idx, val, info = run_plan(sfft, p, **kw)
+    assert_matches_oracle(idx, val, info, ref, "fp32")
+    assert (ref["status"] == 1) == (K == 1300)
+    plan.close()
+
+
+def test_largest_signal_exact_recovery(sfft):
+    """The largest three-factor shape under the library's N < 2^30 limit: N = 1023*1024*1025
+    = 1,073,740,800 (8.6 GB of complex64), B = (1049600, 1048575, 1047552) two-pass stages,
+    delays 0, 1 and 2 random, K = 20 exactly sparse, ML locate.  Too large for the oracle, so
+    the check is the property that holds at any size: the truth's support, and its values to
+    FP32 rounding."""
+    N, f, K = 1073740800, (1023, 1024, 1025), 20
+    rng = np.random.default_rng(77)
+    support, values = synth.sparse_spectrum(N, K, rng, mag=(1.0, 10.0))
+    delays = synth.draw_delays(N, 3, 4, rng)
+    x = synth.time_signal_torch(N, support, values)
+    plan = sfft.Plan(N, K, f, delays, precision="fp32", locate="ml")
+    idx, val, info = plan.execute(x)
+    torch.cuda.synchronize()
+    info = info.cpu().numpy()
+    n = int(info[0])
+    assert info[1] == 0 and n == K, info
+    np.testing.assert_array_equal(idx[:n].cpu().numpy(), support)
+    got = val[:n].cpu().numpy()
+    assert np.linalg.norm(got - values) / np.linalg.norm(values) <= 1e-5
+    plan.close()
+    del x
+    torch.cuda.empty_cache()
