@@ -524,6 +524,34 @@ __device__ __forceinline__ bool bin_is_zero(const PlanDesc& pd, const typename C
     return below(E, thr[d].T0f, thr[d].T0);
 }
 
+// D1 of NB bins b, b + stride, ... (those at or past b1 count as zero) with a compile-time
+// delay count: all NB RT loads in flight before the energies (the same sums as bin_is_zero)
+template <typename T, int RT, int NB>
+__device__ __forceinline__ void bins_are_zero(const PlanDesc& pd, const typename C2<T>::t* Y, int b,
+                                              int stride, int b1, const Thr* thr, bool* z)
+{
+    using V = typename C2<T>::t;
+    V y[NB][RT];
+    int dd[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int bu = b + u * stride < b1 ? b + u * stride : b;
+        const int d = stage_of(pd, bu);
+        dd[u] = d;
+        const StageDesc& st = pd.st[d];
+        const V* Yb = Y + st.y_off + (bu - st.bin_base);
+#pragma unroll
+        for (int r = 0; r < RT; ++r) y[u][r] = __ldcg(Yb + (int64_t)r * st.B);
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        T E = 0;
+#pragma unroll
+        for (int r = 0; r < RT; ++r) E += y[u][r].x * y[u][r].x + y[u][r].y * y[u][r].y;
+        z[u] = b + u * stride >= b1 || below(E, thr[dd[u]].T0f, thr[dd[u]].T0);
+    }
+}
+
 // s = a + b and the rounding error e of that sum, a + b = s + e exactly (Knuth's TwoSum)
 template <typename T>
 __device__ __forceinline__ T two_sum(T a, T b, T* e)
@@ -694,7 +722,7 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
     using V = typename C2<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_nz[kClassifyTile];
-    __shared__ int s_cnt, s_res;
+    __shared__ int s_cnt;
     const PlanDesc& pd = a.pd;
     const int tiles = (pd.sumB + kClassifyTile - 1) / kClassifyTile;
     const int sig = blockIdx.x / tiles;
@@ -726,18 +754,26 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
     __shared__ Thr s_thr[kMaxStages];
     if (threadIdx.x == 0) {
         s_cnt = 0;
-        s_res = 0;
         signal_thresholds(a, sig, s_thr);
     }
     __syncthreads();
-    // D1, four bins per thread in flight
+    // D1: the zero-ton test of every bin, NB bins per thread with all their loads in flight
+    // (a compile-time delay count for the common R)
     constexpr int NB = 4;
     for (int b = b0 + threadIdx.x; b < b1; b += NB * blockDim.x) {
         bool z[NB];
+        if (pd.R == 8) {
+            bins_are_zero<T, 8, 2>(pd, Y, b, blockDim.x, b1, s_thr, z);
+            bins_are_zero<T, 8, 2>(pd, Y, b + 2 * blockDim.x, blockDim.x, b1, s_thr, z + 2);
+        } else if (pd.R == 6) {
+            bins_are_zero<T, 6, 2>(pd, Y, b, blockDim.x, b1, s_thr, z);
+            bins_are_zero<T, 6, 2>(pd, Y, b + 2 * blockDim.x, blockDim.x, b1, s_thr, z + 2);
+        } else {
 #pragma unroll
-        for (int u = 0; u < NB; ++u) {
-            const int bu = b + u * blockDim.x;
-            z[u] = bu < b1 ? bin_is_zero<T>(pd, Y, bu, s_thr) : true;
+            for (int u = 0; u < NB; ++u) {
+                const int bu = b + u * blockDim.x;
+                z[u] = bu < b1 ? bin_is_zero<T>(pd, Y, bu, s_thr) : true;
+            }
         }
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
@@ -747,9 +783,7 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
             // peeling) or the dirty flag (atomic peeling) of the bins that can stay open; the
             // candidate word is written only with a single-ton state
             __stcg(w.state + bu, (uint8_t)(z[u] ? 1 : 0));
-            if (z[u]) {
-                atomicAdd(&s_res, 1);
-            } else {
+            if (!z[u]) {
                 s_nz[atomicAdd(&s_cnt, 1)] = bu;
                 if (pd.peel_atomic)
                     __stcg(w.dirty + bu, 0u);
@@ -774,7 +808,7 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
             locate_phase_thread<T>(a, w.ctr, w, Y, 1, s_nz[i], s_thr);
     }
     if (threadIdx.x == 0) {
-        atomicAdd(w.ctr + kCtrResolved, s_res);
+        atomicAdd(w.ctr + kCtrResolved, b1 - b0 - n_nz);  // the zero-tons
         atomicAdd(w.ctr + kCtrIdents, b1 - b0);
     }
 }
