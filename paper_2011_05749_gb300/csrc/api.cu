@@ -111,7 +111,7 @@ extern "C" void sfft_opts_default(sfft_opts* o)
 
 static void free_plan_memory(sfft_plan_s* p)
 {
-    void* dev[] = {p->d_nidx, p->d_pbin, p->d_bpos, p->d_tw, p->d_bins, p->d_scratch,
+    void* dev[] = {p->d_nidx, p->d_pbin, p->d_bpos, p->d_tw, p->d_mltc, p->d_bins, p->d_scratch,
                    p->d_dec, p->d_ptrs, p->d_sortbuf, p->d_x_stage, p->d_out_stage,
                    p->d_bins_in, p->d_xb_stage, p->d_ob_stage};
     for (void* q : dev)
@@ -408,6 +408,37 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         tw_P.push_back((int32_t)N);
         tw_t.push_back((int32_t)((h << pd.ph_shift) % N));
     }
+    // the first round's ML search on the tensor cores (FP32 peeling plans, R <= 16): per
+    // stage the split fragments of A (ml_tc_rp), from the same phasors in FP64 rounded to FP32
+    std::vector<uint32_t> h_mltc;
+    const bool ml_tc = p->prec == 1 && o.locate == SFFT_LOCATE_ML && pd.mode == 0 && n_delays <= 16;
+    for (int d = 0; d < n_stages; ++d) {
+        StageDesc& s = pd.st[d];
+        s.mltc_off = -1;
+        if (!ml_tc) continue;
+        s.mltc_off = (int32_t)(h_mltc.size() / 256);
+        const int L = s.L, RP = ml_tc_rp(n_delays), KT = RP / 4, MT = (L + 7) / 8;
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int mt = 0; mt < MT; ++mt)
+            for (int kt = 0; kt < KT; ++kt)
+                for (int h = 0; h < 2; ++h)
+                    for (int l = 0; l < 32; ++l)
+                        for (int e = 0; e < 4; ++e) {
+                            const int row = (l >> 2) + (e & 1) * 8, k = kt * 8 + (l & 3) + (e >> 1) * 4;
+                            const int q = mt * 8 + (row & 7), im = row >> 3;
+                            const int part = k / RP, r = k % RP;
+                            float v = 0.0f;
+                            if (q < L && r < n_delays) {
+                                const double th = two_pi * (double)(((int64_t)q * s.tauL[r]) % L) / (double)L;
+                                const double cv = cos(th), sv = sin(th);
+                                v = (float)(im == 0 ? (part == 0 ? cv : sv) : (part == 0 ? -sv : cv));
+                            }
+                            uint32_t bits, hi, lo;
+                            memcpy(&bits, &v, 4);
+                            tf32_split_bits(bits, &hi, &lo);
+                            h_mltc.push_back(h == 0 ? hi : lo);
+                        }
+    }
     // ML candidate phasors per stage: W[r][q] = e^{2 pi i (q tauL_r mod L) / L}, a row of L
     // candidates per delay
     for (int d = 0; d < n_stages; ++d) {
@@ -491,6 +522,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     dmalloc((void**)&p->d_pbin, 4 * h_pbin.size());
     dmalloc((void**)&p->d_bpos, 4 * h_bpos.size());
     dmalloc(&p->d_tw, p->esz * tw_P.size());
+    dmalloc((void**)&p->d_mltc, 4 * h_mltc.size());
     dmalloc(&p->d_bins, ybytes);
     if (p->need_pass2) dmalloc(&p->d_scratch, ybytes);
     dmalloc(&p->d_dec, p->dec_bytes);
@@ -507,6 +539,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     if (e == cudaSuccess) e = cudaMemcpy(p->d_nidx, h_nidx.data(), 4 * h_nidx.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_pbin, h_pbin.data(), 4 * h_pbin.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_bpos, h_bpos.data(), 4 * h_bpos.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !h_mltc.empty())
+        e = cudaMemcpy(p->d_mltc, h_mltc.data(), 4 * h_mltc.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_twP, tw_P.data(), 4 * tw_P.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_twt, tw_t.data(), 4 * tw_t.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = launch_twiddles(p->d_tw, d_twP, d_twt, (int64_t)tw_P.size(), p->prec, 0);
@@ -538,7 +572,8 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     w.sig2 = pd.noise_auto ? (double*)(base + o_s2) : nullptr;
     w.sub_head = lists ? (int32_t*)(base + o_sh) : nullptr;
     w.sub_ent = lists ? (int2*)(base + o_se) : nullptr;
-    p->footprint = 4 * 3 * h_nidx.size() + p->esz * tw_P.size() + ybytes * (p->need_pass2 ? 2 : 1) +
+    p->footprint = 4 * 3 * h_nidx.size() + p->esz * tw_P.size() + 4 * h_mltc.size() +
+                   ybytes * (p->need_pass2 ? 2 : 1) +
                    p->dec_bytes + 2 * sizeof(uint64_t) * (size_t)p->sort_cap * mb;
     p->decode_occ = decode_occupancy(p->prec, 512);
     *out = p;
@@ -695,6 +730,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     da.bpos = p->d_bpos;
     da.bins = bins;
     da.roots = p->d_tw;
+    da.mltc = reinterpret_cast<const uint4*>(p->d_mltc);
     da.wtab_elems = p->wtab_elems;
     // a tile's phasor tables go to shared memory up to 160 KB (up to 96 KB two classify
     // CTAs still fit an SM)

@@ -133,6 +133,40 @@ __device__ __forceinline__ void record_candidate(int32_t* ctr, const DecodeWs& w
     atomicAdd(ctr + kCtrResolved, 1);
 }
 
+// The fit of non-zero bin b (stage d, bin j, Z_r in zx / zy, RM >= R slots) at candidate
+// bq: v = sum_r Z_r conj(W[r][bq]) / (R B) and rho = sum_r |Z_r - B v W[r][bq]|^2;
+// rho <= T1 records f = j + bq B as a single-ton.
+template <typename T, int RM>
+__device__ __forceinline__ void ml_fit(int32_t* ctr, const DecodeWs& w, const typename C2<T>::t* W,
+                                       int L, int B, int R, const T* zx, const T* zy, int j, int bq,
+                                       int d, int b, int round, const Thr* thr)
+{
+    using V = typename C2<T>::t;
+    T cx = 0, cy = 0;
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        if (r < R) {
+            const V e = W[r * L + bq];
+            cx = fma(zx[r], e.x, fma(zy[r], e.y, cx));
+            cy = fma(zy[r], e.x, fma(-zx[r], e.y, cy));
+        }
+    }
+    const int64_t f = (int64_t)j + (int64_t)bq * B;
+    const T sc = (T)1 / ((T)R * (T)B);
+    const V v = {cx * sc, cy * sc};
+    T e2 = 0;
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        if (r < R) {
+            const V e = W[r * L + bq];
+            const T ex = zx[r] - (T)B * (v.x * e.x - v.y * e.y);
+            const T ey = zy[r] - (T)B * (v.x * e.y + v.y * e.x);
+            e2 += ex * ex + ey * ey;
+        }
+    }
+    if (below(e2, thr[d].T1f, thr[d].T1)) record_candidate<T>(ctr, w, round, b, f, v);
+}
+
 // D2, ML locate for non-zero bin j of stage d, by a group of G lanes (G a power of two
 // <= 32, groups aligned within the warp; every lane of the warp calls this in lockstep).
 // Groups without a bin of their own pass valid = false and some other bin of the same
@@ -244,29 +278,155 @@ __device__ void locate_ml_group(const DecodeArgs& a, int32_t* ctr, const DecodeW
         }
     }
     if (!valid || li != 0) return;
-    T cx = 0, cy = 0;
+    ml_fit<T, RM>(ctr, w, W, L, B, R, zx, zy, j, bq, d, b, round, thr);
+}
+
+// D2 on the tensor cores (FP32, ML, the first round): the scores of up to 8 NT bins of one
+// stage (bl[0 .. nb)) against all L candidates as the product A Z of the stage's fragment
+// tables (ml_tc_rp) with the bins' Z_r = Y_r conj(a_r(j)) -- n-tile u's column g is bin
+// 8 u + g, and lane slot t of k-tile i holds delay t + 4 i -- in m16n8k8 TF32 MMAs with both
+// operands split into high and low parts, three partial products kept, as the tensor-core
+// DFT axes (FP32-level scores); each A fragment serves the NT n-tiles.  Lane (g, t) keeps the
+// best of candidates 8 mt + g for bins 2 t and 2 t + 1 of each n-tile; the eight lanes sharing
+// t reduce them (lowest q on ties).  The fit of bin 8 u + g then runs on lanes (g, 0..3),
+// which hold its Z_{t + 4 i}: v = sum_r Z_r conj(W[r][bq]) / (R B) and the residual, each a
+// sum of per-lane parts.  Every lane of the warp calls this in lockstep.
+template <int NZ, int NT>
+__device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                                          const float2* Y, const float2* wtab, int32_t wtab_base,
+                                          int round, const int* bl, int nb, const Thr* thr)
+{
+    using V = float2;
+    constexpr int RP = 4 * NZ, KT = NZ;
+    const PlanDesc& pd = a.pd;
+    const int lane = (int)(threadIdx.x & 31), g = lane >> 2, t = lane & 3;
+    const int d = stage_of(pd, bl[0]);
+    const StageDesc& st = pd.st[d];
+    const int R = pd.R, B = st.B, L = st.L;
+    float zx[NT][NZ], zy[NT][NZ];      // Z_{t + 4 i} of bin 8 u + g
+    uint32_t bh[NT][KT][2], bo[NT][KT][2];  // its B fragments: high and low parts
 #pragma unroll
-    for (int r = 0; r < RM; ++r) {
-        if (r < R) {
-            const V e = W[r * L + bq];
-            cx = fma(zx[r], e.x, fma(zy[r], e.y, cx));
-            cy = fma(zy[r], e.x, fma(-zx[r], e.y, cy));
+    for (int u = 0; u < NT; ++u) {
+        const int i8 = 8 * u + g;
+        const int bg = bl[i8 < nb ? i8 : 0];
+        const int jg = __ldg(a.pbin + bg);
+        const V* Yg = Y + st.y_off + (bg - st.bin_base);
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) {
+            const int r = t + 4 * i;
+            zx[u][i] = 0.0f;
+            zy[u][i] = 0.0f;
+            if (r < R && i8 < nb) {
+                const V y = __ldcg(Yg + (int64_t)r * B);
+                const V aj = delay_phasor<float>(a, jg, st.tau[r]);
+                zx[u][i] = y.x * aj.x + y.y * aj.y;
+                zy[u][i] = y.y * aj.x - y.x * aj.y;
+            }
+        }
+        // k-tile kt: rows 8 kt + t (slot 0) and 8 kt + t + 4 (slot 1) of [Re Z; Im Z]
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 8 * kt + 4 * h;
+                const float v = k < RP ? zx[u][(k % RP) >> 2] : zy[u][(k % RP) >> 2];
+                tf32_split_bits(__float_as_uint(v), &bh[u][kt][h], &bo[u][kt][h]);
+            }
+    }
+    const uint4* fr = a.mltc + (size_t)st.mltc_off * 64 + lane;
+    const int MT = (L + 7) >> 3;
+    float best[NT][2];
+    int bq[NT][2];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        best[u][0] = best[u][1] = -1.0f;
+        bq[u][0] = bq[u][1] = 0;
+    }
+    for (int mt = 0; mt < MT; ++mt) {
+        float c[NT][4], e[NT][4];
+#pragma unroll
+        for (int u = 0; u < NT; ++u)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) c[u][x] = e[u][x] = 0.0f;
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt) {
+            const uint4 ah = __ldg(fr + (mt * KT + kt) * 64), al = __ldg(fr + (mt * KT + kt) * 64 + 32);
+#pragma unroll
+            for (int u = 0; u < NT; ++u) {
+                mma_tf32(e[u], al, bh[u][kt][0], bh[u][kt][1]);
+                mma_tf32(e[u], ah, bo[u][kt][0], bo[u][kt][1]);
+                mma_tf32(c[u], ah, bh[u][kt][0], bh[u][kt][1]);
+            }
+        }
+        // rows g / g + 8: Re / Im c of candidate 8 mt + g; columns 2 t, 2 t + 1: the bins
+        const int q = 8 * mt + g;
+        if (q < L) {
+#pragma unroll
+            for (int u = 0; u < NT; ++u)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float cx = c[u][h] + e[u][h], cy = c[u][2 + h] + e[u][2 + h];
+                    const float sc = cx * cx + cy * cy;
+                    if (sc > best[u][h]) {
+                        best[u][h] = sc;
+                        bq[u][h] = q;
+                    }
+                }
         }
     }
-    const int64_t f = (int64_t)j + (int64_t)bq * B;
-    const T sc = (T)1 / ((T)R * (T)B);
-    const V v = {cx * sc, cy * sc};
-    T e2 = 0;
 #pragma unroll
-    for (int r = 0; r < RM; ++r) {
-        if (r < R) {
-            const V e = W[r * L + bq];
-            const T ex = zx[r] - (T)B * (v.x * e.x - v.y * e.y);
-            const T ey = zy[r] - (T)B * (v.x * e.y + v.y * e.x);
-            e2 += ex * ex + ey * ey;
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best[u][h], o);
+                const int oq = __shfl_xor_sync(0xffffffffu, bq[u][h], o);
+                if (ob > best[u][h] || (ob == best[u][h] && oq < bq[u][h])) {
+                    best[u][h] = ob;
+                    bq[u][h] = oq;
+                }
+            }
+    // the fit of bin 8 u + g on lanes (g, 0..3); its best candidate is held by lane g / 2
+    const V* W = wtab + (st.wtab_off - wtab_base);
+    const float scl = 1.0f / ((float)R * (float)B);
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        const int i8 = 8 * u + g;
+        const int q0 = __shfl_sync(0xffffffffu, bq[u][0], g >> 1);
+        const int q1 = __shfl_sync(0xffffffffu, bq[u][1], g >> 1);
+        const int qb = (g & 1) ? q1 : q0;
+        float cx = 0.0f, cy = 0.0f;
+        V wr[NZ];
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) {
+            const int r = t + 4 * i;
+            wr[i] = r < R ? W[r * L + qb] : V{0.0f, 0.0f};
+            cx = fma(zx[u][i], wr[i].x, fma(zy[u][i], wr[i].y, cx));
+            cy = fma(zy[u][i], wr[i].x, fma(-zx[u][i], wr[i].y, cy));
+        }
+        cx += __shfl_xor_sync(0xffffffffu, cx, 1);
+        cy += __shfl_xor_sync(0xffffffffu, cy, 1);
+        cx += __shfl_xor_sync(0xffffffffu, cx, 2);
+        cy += __shfl_xor_sync(0xffffffffu, cy, 2);
+        const V v = {cx * scl, cy * scl};
+        float e2 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) {
+            if (t + 4 * i < R) {
+                const float ex = zx[u][i] - (float)B * (v.x * wr[i].x - v.y * wr[i].y);
+                const float ey = zy[u][i] - (float)B * (v.x * wr[i].y + v.y * wr[i].x);
+                e2 += ex * ex + ey * ey;
+            }
+        }
+        e2 += __shfl_xor_sync(0xffffffffu, e2, 1);
+        e2 += __shfl_xor_sync(0xffffffffu, e2, 2);
+        if (t == 0 && i8 < nb && below(e2, thr[d].T1f, thr[d].T1)) {
+            const int b = bl[i8];
+            const int64_t f = (int64_t)__ldg(a.pbin + b) + (int64_t)qb * B;
+            record_candidate<float>(ctr, w, round, b, f, v);
         }
     }
-    if (below(e2, thr[d].T1f, thr[d].T1)) record_candidate<T>(ctr, w, round, b, f, v);
 }
 
 // Lanes per bin for the ML search of n bins with at most Lmax candidates by nt threads:
@@ -721,8 +881,8 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
 {
     using V = typename C2<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_nz[kClassifyTile];
-    __shared__ int s_cnt;
+    __shared__ int s_nz[kClassifyTile];  // non-zero bins: the first stage's from the front,
+    __shared__ int s_cnt, s_hi;          // the second's from the back (tiles within two stages)
     const PlanDesc& pd = a.pd;
     const int tiles = (pd.sumB + kClassifyTile - 1) / kClassifyTile;
     const int sig = blockIdx.x / tiles;
@@ -754,9 +914,12 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
     __shared__ Thr s_thr[kMaxStages];
     if (threadIdx.x == 0) {
         s_cnt = 0;
+        s_hi = 0;
         signal_thresholds(a, sig, s_thr);
     }
     __syncthreads();
+    const int dlo = stage_of(pd, b0), dhi = stage_of(pd, b1 - 1);
+    const int bsplit = dhi == dlo + 1 ? pd.st[dhi].bin_base : b1;
     // D1: the zero-ton test of every bin, NB bins per thread with all their loads in flight
     // (a compile-time delay count for the common R)
     constexpr int NB = 4;
@@ -784,7 +947,10 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
             // candidate word is written only with a single-ton state
             __stcg(w.state + bu, (uint8_t)(z[u] ? 1 : 0));
             if (!z[u]) {
-                s_nz[atomicAdd(&s_cnt, 1)] = bu;
+                if (bu < bsplit)
+                    s_nz[atomicAdd(&s_cnt, 1)] = bu;
+                else
+                    s_nz[kClassifyTile - 1 - atomicAdd(&s_hi, 1)] = bu;
                 if (pd.peel_atomic)
                     __stcg(w.dirty + bu, 0u);
                 else
@@ -793,19 +959,43 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
         }
     }
     __syncthreads();
-    const int n_nz = s_cnt;
+    const int n_lo = s_cnt, n_hi = s_hi, n_nz = n_lo + n_hi;
+    const int* nz_hi = s_nz + kClassifyTile - n_hi;
+    auto nz_at = [&](int i) { return i < n_lo ? s_nz[i] : nz_hi[i - n_lo]; };
+    bool tc_done = false;
     if (pd.locate == 1) {
+        if constexpr (sizeof(T) == 4) {
+            if (a.mltc && a.lanes == 0 && dhi - dlo <= 1 && pd.R <= 16) {
+                // the tensor-core search: warps take groups of 8 bins of one stage
+                constexpr int NB = 16;  // bins per warp task (two n-tiles)
+                const int t_lo = (n_lo + NB - 1) / NB, t_all = t_lo + (n_hi + NB - 1) / NB;
+                const int nw = (int)(blockDim.x >> 5);
+                for (int k = (int)(threadIdx.x >> 5); k < t_all; k += nw) {
+                    const int* bl = k < t_lo ? s_nz + NB * k : nz_hi + NB * (k - t_lo);
+                    const int nb = min(NB, k < t_lo ? n_lo - NB * k : n_hi - NB * (k - t_lo));
+                    switch ((pd.R + 3) >> 2) {
+                        case 1: locate_ml_tc<1, 2>(a, w.ctr, w, Y, wtab, wtab_base, 1, bl, nb, s_thr); break;
+                        case 2: locate_ml_tc<2, 2>(a, w.ctr, w, Y, wtab, wtab_base, 1, bl, nb, s_thr); break;
+                        case 3: locate_ml_tc<3, 2>(a, w.ctr, w, Y, wtab, wtab_base, 1, bl, nb, s_thr); break;
+                        default: locate_ml_tc<4, 2>(a, w.ctr, w, Y, wtab, wtab_base, 1, bl, nb, s_thr); break;
+                    }
+                }
+                tc_done = true;
+            }
+        }
+    }
+    if (pd.locate == 1 && !tc_done) {
         int Lmax = 0;
         for (int d = 0; d < pd.D; ++d) Lmax = max(Lmax, pd.st[d].L);
         const int G = a.lanes > 0 ? a.lanes : ml_group_size(n_nz, Lmax, pd.R, blockDim.x);
         const int per = blockDim.x / G;
         for (int k = 0; k < (n_nz + per - 1) / per; ++k) {
             const int i = k * per + threadIdx.x / G;
-            locate_ml<T>(a, w.ctr, w, Y, wtab, wtab_base, 1, s_nz[i < n_nz ? i : 0], i < n_nz, G, s_thr);
+            locate_ml<T>(a, w.ctr, w, Y, wtab, wtab_base, 1, nz_at(i < n_nz ? i : 0), i < n_nz, G, s_thr);
         }
-    } else {
+    } else if (pd.locate != 1) {
         for (int i = threadIdx.x; i < n_nz; i += blockDim.x)
-            locate_phase_thread<T>(a, w.ctr, w, Y, 1, s_nz[i], s_thr);
+            locate_phase_thread<T>(a, w.ctr, w, Y, 1, nz_at(i), s_thr);
     }
     if (threadIdx.x == 0) {
         atomicAdd(w.ctr + kCtrResolved, b1 - b0 - n_nz);  // the zero-tons

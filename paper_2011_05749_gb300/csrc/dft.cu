@@ -445,15 +445,6 @@ __device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo)
     lo = __float_as_uint(v - __uint_as_float(hi)) & 0xffffe000u;
 }
 
-// d += a b for one 16 x 8 x 8 tile: a row-major (4 registers), b column-major (2), FP32 d
-__device__ __forceinline__ void mma_tf32(float* d, uint4 a, uint32_t b0, uint32_t b1)
-{
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
-}
-
 // WPG warps per column group of 8 sub-DFTs (an n-tile of their real parts and one of their
 // imaginary parts), each for MR of the row tiles, so each data fragment is loaded and split
 // once per warp and a thread ends up holding C and S, real and imaginary, of the same

@@ -39,6 +39,7 @@ struct DecodeArgs {
     const int32_t* pbin;  // position -> bin j, per stage at bin_base
     const int32_t* bpos;  // bin j -> position
     const void* roots;    // the plan's twiddle table: ML phasor tables at st[d].wtab_off
+    const uint4* mltc;    // ML tensor-core fragment tables (st[d].mltc_off), or nullptr
     void* bins;           // complex, n_sig * y_per_sig, modified in place
 };
 

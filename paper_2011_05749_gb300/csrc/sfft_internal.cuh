@@ -60,7 +60,7 @@ struct StageDesc {
     int32_t root_off;        // offset of the L roots of unity (cos, sin)(2 pi t / L)
     float invL;              // 1 / L
     int32_t wtab_off;        // offset of the [R][L] table W[r][q] = (cos, sin)(2 pi (q tauL_r mod L) / L)
-    int32_t pad2;
+    int32_t mltc_off;        // first fragment tile of the stage in the ML tensor-core table (-1 none)
     double T0, T1;           // thresholds on sum_r |Y_r|^2 and on the single-tone residual
     float T0f, T1f;          // the same in FP32 (the FP32 path compares in FP32)
     double T0a, T1a, Tb;     // T0 = T0a sigma^2 + Tb, T1 = T1a sigma^2 + Tb (estimated sigma^2)
@@ -162,6 +162,16 @@ __host__ __device__ __forceinline__ void tf32_split_bits(uint32_t v, uint32_t* h
     *lo = r.u & 0xffffe000u;
 }
 #ifdef __CUDACC__
+// d += a b for one 16 x 8 x 8 TF32 tile: a row-major (4 registers), b column-major (2),
+// FP32 d
+__device__ __forceinline__ void mma_tf32(float* d, uint4 a, uint32_t b0, uint32_t b1)
+{
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
 // Word w of the fragment table of a tensor-core odd axis: the cosine or sine of
 // 2 pi (n k mod P) / P (FP64, rounded to FP32), for output k and input n of the fragment
 // slot, zero outside k, n <= (P - 1) / 2; its TF32 high or low part.
@@ -189,6 +199,20 @@ __host__ __device__ __forceinline__ int32_t axis_tw_residue(int P, int pow2, int
     const int n = i / kp + 1, k = i % kp + 1;
     return k > pairs ? 0 : (int32_t)(((int64_t)n * k) % P);
 }
+
+// The first round's ML candidate search on the tensor cores (FP32 plans, R <= 16).  For a
+// stage's L candidates q and R delays the scores are |c_q|^2 with
+//   c_q = sum_r Z_r conj(W[r][q]),  Re c_q = sum_r (Re Z_r cos + Im Z_r sin),
+//                                   Im c_q = sum_r (Im Z_r cos - Re Z_r sin),
+// (cos, sin) of 2 pi (q tauL_r mod L) / L: one real product A Z of the 16-row m-tile mt of A
+// (row i < 8: Re c of candidate 8 mt + i; row 8 + i: its Im c) with the K = 2 RP rows of Z
+// (k < RP: Re Z_k, else Im Z_{k - RP}; RP = R rounded up to a multiple of 4, so each of the
+// KT = RP / 4 k-tiles of 8 rows holds Z_{t + 4 i} in lane slot t).  A's m16n8k8 TF32
+// fragments come pre-split: fragment tile (mt, kt) of a stage is 64 uint4, the high parts
+// (lane l at + l) then the low parts (+ 32 + l), each uint4 the lane's (a0, a1, a2, a3) =
+// A[g][k], A[g + 8][k], A[g][k + 4], A[g + 8][k + 4] with g = l / 4, k = 8 kt + l % 4.
+__host__ __device__ __forceinline__ int ml_tc_rp(int R) { return (R + 3) & ~3; }
+__host__ __device__ __forceinline__ int ml_tc_tiles(int L, int R) { return ((L + 7) >> 3) * (ml_tc_rp(R) >> 2); }
 
 // Decode workspace of one signal slot (all arrays sumB entries unless stated).
 struct DecodeWs {

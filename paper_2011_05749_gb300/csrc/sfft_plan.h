@@ -29,6 +29,7 @@ struct sfft_plan_s {
     int32_t* d_pbin = nullptr;  // position -> bin j
     int32_t* d_bpos = nullptr;  // bin j -> position
     void* d_tw = nullptr;       // twiddles of every axis
+    void* d_mltc = nullptr;     // the ML search's tensor-core fragment tables (or none)
     // workspace for max_batch signals
     void* d_bins = nullptr;
     void* d_scratch = nullptr;
