@@ -119,17 +119,24 @@ __device__ __forceinline__ typename C2<T>::t delay_phasor(const DecodeArgs& a, i
     return V{fma(hi.x, lo.x, -(hi.y * lo.y)), fma(hi.x, lo.y, hi.y * lo.x)};
 }
 
+// bin b's single-ton f, v: its state and candidate word, and entry k of the round's list
 template <typename T>
-__device__ __forceinline__ void record_candidate(int32_t* ctr, const DecodeWs& w, int round, int b,
-                                                 int64_t f, typename C2<T>::t v)
+__device__ __forceinline__ void record_at(const DecodeWs& w, int round, int b, int64_t f,
+                                          typename C2<T>::t v, int k)
 {
     using V = typename C2<T>::t;
     __stcg(w.state + b, (uint8_t)2);
     __stcg((long long*)w.cand + b, (long long)(((int64_t)round << 40) | f));
-    const int k = atomicAdd(ctr + kCtrRoundBase + 3 * round + 2, 1);
     __stcg(w.cbin + k, b);
     __stcg((long long*)w.cf + k, (long long)f);
     reinterpret_cast<V*>(w.cv)[k] = v;
+}
+
+template <typename T>
+__device__ __forceinline__ void record_candidate(int32_t* ctr, const DecodeWs& w, int round, int b,
+                                                 int64_t f, typename C2<T>::t v)
+{
+    record_at<T>(w, round, b, f, v, atomicAdd(ctr + kCtrRoundBase + 3 * round + 2, 1));
     atomicAdd(ctr + kCtrResolved, 1);
 }
 
@@ -305,24 +312,34 @@ __device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, con
     const int R = pd.R, B = st.B, L = st.L;
     float zx[NT][NZ], zy[NT][NZ];      // Z_{t + 4 i} of bin 8 u + g
     uint32_t bh[NT][KT][2], bo[NT][KT][2];  // its B fragments: high and low parts
+    {
+        // every load of the Z_r in flight at once: bins, then their samples and phasors
+        int jg[NT];
+        V y[NT][NZ];
 #pragma unroll
-    for (int u = 0; u < NT; ++u) {
-        const int i8 = 8 * u + g;
-        const int bg = bl[i8 < nb ? i8 : 0];
-        const int jg = __ldg(a.pbin + bg);
-        const V* Yg = Y + st.y_off + (bg - st.bin_base);
+        for (int u = 0; u < NT; ++u) {
+            const int i8 = 8 * u + g;
+            const int bg = bl[i8 < nb ? i8 : 0];
+            jg[u] = __ldg(a.pbin + bg);
+            const V* Yg = Y + st.y_off + (bg - st.bin_base);
 #pragma unroll
-        for (int i = 0; i < NZ; ++i) {
-            const int r = t + 4 * i;
-            zx[u][i] = 0.0f;
-            zy[u][i] = 0.0f;
-            if (r < R && i8 < nb) {
-                const V y = __ldcg(Yg + (int64_t)r * B);
-                const V aj = delay_phasor<float>(a, jg, st.tau[r]);
-                zx[u][i] = y.x * aj.x + y.y * aj.y;
-                zy[u][i] = y.y * aj.x - y.x * aj.y;
+            for (int i = 0; i < NZ; ++i) {
+                const int r = t + 4 * i;
+                y[u][i] = r < R && i8 < nb ? __ldcg(Yg + (int64_t)r * B) : V{0.0f, 0.0f};
             }
         }
+#pragma unroll
+        for (int u = 0; u < NT; ++u)
+#pragma unroll
+            for (int i = 0; i < NZ; ++i) {
+                const int r = t + 4 * i;
+                const V aj = delay_phasor<float>(a, jg[u], st.tau[r < R ? r : 0]);
+                zx[u][i] = y[u][i].x * aj.x + y[u][i].y * aj.y;
+                zy[u][i] = y[u][i].y * aj.x - y[u][i].x * aj.y;
+            }
+    }
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
         // k-tile kt: rows 8 kt + t (slot 0) and 8 kt + t + 4 (slot 1) of [Re Z; Im Z]
 #pragma unroll
         for (int kt = 0; kt < KT; ++kt)
@@ -343,18 +360,19 @@ __device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, con
         bq[u][0] = bq[u][1] = 0;
     }
     for (int mt = 0; mt < MT; ++mt) {
-        float c[NT][4], e[NT][4];
+        // the three partial products in separate accumulators: chains of KT MMAs
+        float c[NT][4], e[NT][4], f[NT][4];
 #pragma unroll
         for (int u = 0; u < NT; ++u)
 #pragma unroll
-            for (int x = 0; x < 4; ++x) c[u][x] = e[u][x] = 0.0f;
+            for (int x = 0; x < 4; ++x) c[u][x] = e[u][x] = f[u][x] = 0.0f;
 #pragma unroll
         for (int kt = 0; kt < KT; ++kt) {
             const uint4 ah = __ldg(fr + (mt * KT + kt) * 64), al = __ldg(fr + (mt * KT + kt) * 64 + 32);
 #pragma unroll
             for (int u = 0; u < NT; ++u) {
                 mma_tf32(e[u], al, bh[u][kt][0], bh[u][kt][1]);
-                mma_tf32(e[u], ah, bo[u][kt][0], bo[u][kt][1]);
+                mma_tf32(f[u], ah, bo[u][kt][0], bo[u][kt][1]);
                 mma_tf32(c[u], ah, bh[u][kt][0], bh[u][kt][1]);
             }
         }
@@ -365,7 +383,8 @@ __device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, con
             for (int u = 0; u < NT; ++u)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float cx = c[u][h] + e[u][h], cy = c[u][2 + h] + e[u][2 + h];
+                    const float cx = c[u][h] + (e[u][h] + f[u][h]);
+                    const float cy = c[u][2 + h] + (e[u][2 + h] + f[u][2 + h]);
                     const float sc = cx * cx + cy * cy;
                     if (sc > best[u][h]) {
                         best[u][h] = sc;
@@ -390,6 +409,9 @@ __device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, con
     // the fit of bin 8 u + g on lanes (g, 0..3); its best candidate is held by lane g / 2
     const V* W = wtab + (st.wtab_off - wtab_base);
     const float scl = 1.0f / ((float)R * (float)B);
+    bool ok[NT];
+    V vv[NT];
+    int qq[NT];
 #pragma unroll
     for (int u = 0; u < NT; ++u) {
         const int i8 = 8 * u + g;
@@ -421,11 +443,34 @@ __device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, con
         }
         e2 += __shfl_xor_sync(0xffffffffu, e2, 1);
         e2 += __shfl_xor_sync(0xffffffffu, e2, 2);
-        if (t == 0 && i8 < nb && below(e2, thr[d].T1f, thr[d].T1)) {
-            const int b = bl[i8];
-            const int64_t f = (int64_t)__ldg(a.pbin + b) + (int64_t)qb * B;
-            record_candidate<float>(ctr, w, round, b, f, v);
+        ok[u] = t == 0 && i8 < nb && below(e2, thr[d].T1f, thr[d].T1);
+        vv[u] = v;
+        qq[u] = qb;
+    }
+    // the warp's single-tons: one list reservation for all of them
+    unsigned m[NT];
+    int n_rec = 0;
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        m[u] = __ballot_sync(0xffffffffu, ok[u]);
+        n_rec += __popc(m[u]);
+    }
+    if (n_rec == 0) return;
+    int base = 0;
+    if (lane == 0) {
+        base = atomicAdd(ctr + kCtrRoundBase + 3 * round + 2, n_rec);
+        atomicAdd(ctr + kCtrResolved, n_rec);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const unsigned below_me = (1u << lane) - 1u;
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        if (ok[u]) {
+            const int b = bl[8 * u + g];
+            const int64_t f = (int64_t)__ldg(a.pbin + b) + (int64_t)qq[u] * B;
+            record_at<float>(w, round, b, f, vv[u], base + __popc(m[u] & below_me));
         }
+        base += __popc(m[u]);
     }
 }
 
