@@ -224,6 +224,24 @@ def test_execute_rffast_124950(sfft, oracle_mod, prec, snr):
     assert_matches_oracle(idx, val, info, ref, prec)
 
 
+@pytest.mark.parametrize("lanes", [0, 2, 32])
+@pytest.mark.parametrize("name,seed", [("rffast_2097024", 41), ("rffast_124950", 42)])
+def test_ml_search_paths_match_oracle(sfft, oracle_mod, name, seed, lanes):
+    """The first round's ML candidate search two ways: on the tensor cores (classify_lanes =
+    0, the default for FP32 plans: split-TF32 scores of 16 bins per warp against the stage's
+    candidate matrix) and on the FMA pipes with 2 or 32 lanes per bin.  R = 8 (K-tiles of
+    exactly 8 delays) and R = 6 (padded to 8), 20 dB: each gives the oracle's support,
+    values, rounds and identifications."""
+    p = synth.config_problem(name, seed=seed)
+    kw = dict(precision="fp32", locate="ml", noise_var=p.noise_var)
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x.astype(np.complex64).astype(np.complex128))
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    plan, idx, val, info = run_plan(sfft, p, classify_lanes=lanes, **kw)
+    assert_matches_oracle(idx, val, info, ref, "fp32")
+    np.testing.assert_array_equal(idx, p.support)
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_execute_rffast_full_size_2097024(sfft, oracle_mod, prec):
     """The benchmark workload (N = 127*128*129, R = 8, K = 1000, U[1,10], 20 dB) on the
