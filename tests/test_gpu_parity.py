@@ -139,6 +139,25 @@ def test_bucketize_fma_only_matches_oracle(sfft, oracle_mod, N, f, R):
         assert rel_l2(g, r) <= TOL["fp32"], rel_l2(g, r)
 
 
+@pytest.mark.parametrize("N,f,R,tile", [(2097024, (127, 128, 129), 2, 4096),
+                                         (2097024, (127, 128, 129), 2, 8192),
+                                         (551286, (81, 82, 83), 3, 2048)])
+def test_two_pass_tiles_match_oracle(sfft, oracle_mod, N, f, R, tile):
+    """FP32 stages forced into two passes by a B-tile (max_tile, an autotuner axis): the
+    outer axes from x into scratch, the inner ones from scratch to the bins, every odd axis
+    on the FMA pipes (127, 43; 83, 81, 41).  Every bin within 1e-5 of the oracle per stage
+    and delay."""
+    rng = np.random.default_rng(N + tile)
+    x = (rng.standard_normal(N) + 1j * rng.standard_normal(N)).astype(np.complex64)
+    delays = synth.draw_delays(N, len(f), R, rng)
+    Y = oracle_mod.bucketize(N, f, delays, x.astype(np.complex128))
+    plan = sfft.Plan(N, 4, f, delays, precision="fp32", max_tile=tile)
+    bins = plan.bucketize(to_dev(x, np.complex64)).cpu().numpy()
+    plan.close()
+    for g, r in zip(split_bins(bins, N, f, R), split_bins(Y, N, f, R)):
+        assert rel_l2(g, r) <= TOL["fp32"], rel_l2(g, r)
+
+
 @pytest.mark.parametrize("N,f", [(16776960, (255, 256, 257)), (134217216, (511, 512, 513))])
 def test_bucketize_large_sampled(sfft, oracle_mod, N, f):
     """Two-pass stages (B up to 262656, factors 257 / 2^9 * 3^3 * 19): sampled bins against
