@@ -261,6 +261,23 @@ def test_ml_search_paths_match_oracle(sfft, oracle_mod, name, seed, lanes):
     plan.close()
 
 
+@pytest.mark.parametrize("R", [4, 5, 10, 12, 16])
+def test_ml_tensor_core_search_delay_counts(sfft, oracle_mod, R):
+    """The tensor-core ML search for delay counts that fill one to four k-tiles of 4 delays,
+    exactly (4, 12, 16) or with padding (5, 10): N = 49*50*51, K = 120 at 25 dB, random
+    delays.  The oracle's support, values, rounds and identifications, as with the FMA
+    search (classify_lanes = 4)."""
+    p = synth.make_problem(124950, (49, 50, 51), 120, seed=60 + R, R=R, delays="random",
+                           mag=(1.0, 10.0), snr_db=25.0)
+    kw = dict(precision="fp32", locate="ml", noise_var=p.noise_var)
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x.astype(np.complex64).astype(np.complex128))
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    for lanes in (0, 4):
+        plan, idx, val, info = run_plan(sfft, p, classify_lanes=lanes, **kw)
+        assert_matches_oracle(idx, val, info, ref, "fp32")
+        plan.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_execute_rffast_full_size_2097024(sfft, oracle_mod, prec):
     """The benchmark workload (N = 127*128*129, R = 8, K = 1000, U[1,10], 20 dB) on the
