@@ -671,7 +671,7 @@ static cudaError_t bucketize_pass(const sfft_plan_s* p, const BucketArgs& a, int
                                   cudaStream_t st)
 {
     if (pass == 0 && p->stream_ok && !a.x_sys)
-        return launch_bucketize_stream(a, p->num_sms, 512, (size_t)p->max_smem & ~(size_t)15,
+        return launch_bucketize_stream(a, p->num_sms, 512, ((size_t)p->max_smem - 1024) & ~(size_t)15,
                                        (int)(p->smem1 / 8), st);
     return launch_bucketize(a, p->prec, p->xdouble, pass == 0 ? p->threads1 : p->threads2,
                             pass == 0 ? p->smem1 : p->smem2, st);

@@ -430,20 +430,17 @@ __device__ __forceinline__ void axis_dft_odd_dispatch(typename C2<T>::t* s,
 //   C[k][c] = sum_n cos(2 pi n k / P) A[n][c],   A[n] = x_0 (n = 0), a_n (n >= 1)
 //   S[k][c] = sum_n sin(2 pi n k / P) Bs[n][c],  Bs[n] = 0 (n = 0), b_n (n >= 1)
 // over the real columns c (the real and imaginary parts of every sub-DFT); then X_0 = C_0,
-// X_k = C_k - i S_k and X_{P-k} = C_k + i S_k.  Each product runs as m16n8k8 TF32 MMAs with
-// both operands split into TF32 high and low parts, keeping the three largest partial
-// products (hi hi + hi lo + lo hi), the error-corrected TF32 scheme of Ootomo and Yokota
-// (2022): the dropped terms are about 2^-20 of the product, so the result keeps FP32-level
-// accuracy.  The cosine and sine matrices come pre-split in fragment order (the axis'
-// twiddle table in global memory, see tc_twiddle_word, read through the read-only cache);
-// the data come straight from the tile in shared memory, so nothing is staged beside the
-// resident tile.
-
-__device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo)
-{
-    hi = __float_as_uint(v) & 0xffffe000u;
-    lo = __float_as_uint(v - __uint_as_float(hi)) & 0xffffe000u;
-}
+// X_k = C_k - i S_k and X_{P-k} = C_k + i S_k.  Each product runs as m16n8k16 FP16 MMAs
+// with FP32 accumulation and both operands split into FP16 high and low parts, keeping the
+// three largest partial products (hi hi + hi lo + lo hi) -- the split-operand scheme of
+// Ootomo and Yokota (2022) with FP16 parts: FP16 has TF32's 11-bit significand, so the
+// dropped terms are again about 2^-22 of the product and the result keeps FP32-level
+// accuracy, while an FP16 MMA covers 16 inputs where a TF32 one covers 8.  FP16's range is
+// kept by a power-of-two scale per axis call (the tile's largest component mapped into
+// [2^13, 2^14), undone exactly on the accumulators).  The cosine and sine matrices come
+// pre-split in fragment order (the axis' twiddle table in global memory, see
+// tc_twiddle_word, read through the read-only cache); the data come straight from the tile
+// in shared memory, so nothing is staged beside the resident tile.
 
 // WPG warps per column group of 8 sub-DFTs (an n-tile of their real parts and one of their
 // imaginary parts), each for MR of the row tiles, so each data fragment is loaded and split
@@ -455,10 +452,11 @@ __device__ __forceinline__ void tf32_split(float v, uint32_t& hi, uint32_t& lo)
 // banks when the columns are an odd number of elements apart (LS = 1, column stride P) or
 // adjacent (odd LS).
 template <int MR, int WPG>
-__device__ __noinline__ void odd_dft_tc(float2* s, const uint4* frag, int P, int LS, int TS)
+__device__ __noinline__ void odd_dft_tc(float2* s, const uint4* frag, int P, int LS, int TS,
+                                        float sc, float isc)
 {
     const int M = TS / P, pairs = (P - 1) >> 1;
-    const int KT = tc_ktiles(P);
+    const int KK = tc_ktiles(P) >> 1;
     const int NG = (M + 7) >> 3;
     const int W = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
     const int GPC = W / WPG;                 // groups per chunk
@@ -484,57 +482,58 @@ __device__ __noinline__ void odd_dft_tc(float2* s, const uint4* frag, int P, int
                 const int hi = fdivmod(cc, LS, invLS, &lo);
                 src = lo + hi * LS * P;
             }
-            for (int kt = 0; kt < KT; ++kt) {
-                // (a_n, b_n) = (x_n + x_{P-n}, x_n - x_{P-n}) formed as the fragments are
-                // loaded (a_0 = x_0, b_0 = 0); slot t + 4 holds a row n >= 16
-                const int n0 = tc_row(kt, t), n1 = tc_row(kt, t + 4);
-                float2 a0 = {0.0f, 0.0f}, a1 = a0, b0 = a0, b1 = a0;
-                if (src >= 0) {
-                    if (n0 <= pairs) {
-                        const float2 u = s[src + n0 * LS];
-                        if (n0 == 0) {
-                            a0 = u;
-                        } else {
-                            const float2 v = s[src + (P - n0) * LS];
-                            a0 = float2{u.x + v.x, u.y + v.y};
-                            b0 = float2{u.x - v.x, u.y - v.y};
+            for (int kk = 0; kk < KK; ++kk) {
+                // (a_n, b_n) = (x_n + x_{P-n}, x_n - x_{P-n}), scaled, formed as the fragments
+                // are loaded (a_0 = x_0, b_0 = 0): slot 2 t + j of the k-tile is row
+                // tc_row(2 kk + j, t), slot 2 t + 8 + j row tc_row(2 kk + j, t + 4)
+                float2 av[2][2], bv[2][2];  // [t or t + 4][j]
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int n = tc_row(2 * kk + j, t + 4 * p);
+                        float2 a = {0.0f, 0.0f}, b = a;
+                        if (src >= 0 && n <= pairs) {
+                            const float2 u = s[src + n * LS];
+                            if (n == 0) {
+                                a = u;
+                            } else {
+                                const float2 v = s[src + (P - n) * LS];
+                                a = float2{u.x + v.x, u.y + v.y};
+                                b = float2{u.x - v.x, u.y - v.y};
+                            }
                         }
+                        av[p][j] = float2{a.x * sc, a.y * sc};
+                        bv[p][j] = float2{b.x * sc, b.y * sc};
                     }
-                    if (n1 <= pairs) {
-                        const float2 u = s[src + n1 * LS], v = s[src + (P - n1) * LS];
-                        a1 = float2{u.x + v.x, u.y + v.y};
-                        b1 = float2{u.x - v.x, u.y - v.y};
-                    }
-                }
                 uint32_t arh[2], arl[2], aih[2], ail[2], brh[2], brl[2], bih[2], bil[2];
-                tf32_split(a0.x, arh[0], arl[0]);
-                tf32_split(a1.x, arh[1], arl[1]);
-                tf32_split(a0.y, aih[0], ail[0]);
-                tf32_split(a1.y, aih[1], ail[1]);
-                tf32_split(b0.x, brh[0], brl[0]);
-                tf32_split(b1.x, brh[1], brl[1]);
-                tf32_split(b0.y, bih[0], bil[0]);
-                tf32_split(b1.y, bih[1], bil[1]);
-                const uint4* fk = frag + ((size_t)m0 * KT + kt) * 128 + lane;
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    f16_split2(av[p][0].x, av[p][1].x, arh[p], arl[p]);
+                    f16_split2(av[p][0].y, av[p][1].y, aih[p], ail[p]);
+                    f16_split2(bv[p][0].x, bv[p][1].x, brh[p], brl[p]);
+                    f16_split2(bv[p][0].y, bv[p][1].y, bih[p], bil[p]);
+                }
+                const uint4* fk = frag + ((size_t)m0 * KK + kk) * 128 + lane;
 #pragma unroll
                 for (int m = 0; m < MR; ++m) {
-                    const uint4* fm = fk + (size_t)m * KT * 128;
+                    const uint4* fm = fk + (size_t)m * KK * 128;
                     const uint4 ch = __ldg(fm), cl = __ldg(fm + 32);
                     const uint4 sh = __ldg(fm + 64), sl = __ldg(fm + 96);
                     // the three partial products of the four accumulators, interleaved so
                     // that no MMA waits on the one before it; small terms first
-                    mma_tf32(acc[m][0], cl, arh[0], arh[1]);
-                    mma_tf32(acc[m][1], cl, aih[0], aih[1]);
-                    mma_tf32(acc[m][2], sl, brh[0], brh[1]);
-                    mma_tf32(acc[m][3], sl, bih[0], bih[1]);
-                    mma_tf32(acc[m][0], ch, arl[0], arl[1]);
-                    mma_tf32(acc[m][1], ch, ail[0], ail[1]);
-                    mma_tf32(acc[m][2], sh, brl[0], brl[1]);
-                    mma_tf32(acc[m][3], sh, bil[0], bil[1]);
-                    mma_tf32(acc[m][0], ch, arh[0], arh[1]);
-                    mma_tf32(acc[m][1], ch, aih[0], aih[1]);
-                    mma_tf32(acc[m][2], sh, brh[0], brh[1]);
-                    mma_tf32(acc[m][3], sh, bih[0], bih[1]);
+                    mma_f16(acc[m][0], cl, arh[0], arh[1]);
+                    mma_f16(acc[m][1], cl, aih[0], aih[1]);
+                    mma_f16(acc[m][2], sl, brh[0], brh[1]);
+                    mma_f16(acc[m][3], sl, bih[0], bih[1]);
+                    mma_f16(acc[m][0], ch, arl[0], arl[1]);
+                    mma_f16(acc[m][1], ch, ail[0], ail[1]);
+                    mma_f16(acc[m][2], sh, brl[0], brl[1]);
+                    mma_f16(acc[m][3], sh, bil[0], bil[1]);
+                    mma_f16(acc[m][0], ch, arh[0], arh[1]);
+                    mma_f16(acc[m][1], ch, aih[0], aih[1]);
+                    mma_f16(acc[m][2], sh, brh[0], brh[1]);
+                    mma_f16(acc[m][3], sh, bih[0], bih[1]);
                 }
             }
         }
@@ -556,8 +555,8 @@ __device__ __noinline__ void odd_dft_tc(float2* s, const uint4* frag, int P, int
                     for (int r = 0; r < 2; ++r) {
                         const int k = (m0 + m) * 16 + g + 8 * r, e = 2 * r + hc;
                         if (k > pairs) continue;
-                        const float cr = acc[m][0][e], ci = acc[m][1][e];
-                        const float sr = acc[m][2][e], si = acc[m][3][e];
+                        const float cr = acc[m][0][e] * isc, ci = acc[m][1][e] * isc;
+                        const float sr = acc[m][2][e] * isc, si = acc[m][3][e] * isc;
                         if (k == 0) {
                             s[base] = float2{cr, ci};
                         } else {
@@ -577,11 +576,29 @@ __device__ __noinline__ void odd_dft_tc(float2* s, const uint4* frag, int P, int
 __device__ __forceinline__ void odd_axis_tc(float2* s, const float2* tw, int P, int LS, int TS)
 {
     const uint4* frag = reinterpret_cast<const uint4*>(tw);
+    // the tile's largest component, for the FP16 operands' scale
+    __shared__ float red[32];
+    float mx = 0.0f;
+    for (int i = threadIdx.x; i < TS; i += blockDim.x) {
+        const float2 v = s[i];
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.0f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mx = fmaxf(mx, red[i]);
+    __syncthreads();  // red is free again
+    // largest component into [2^13, 2^14): a_n = x_n + x_{P-n} stays below 2^15 (tiles of
+    // only tiny values, below 2^-100, get the scale of 2^-100: their FP16 parts underflow)
+    const int e = mx > 0.0f ? max(ilogbf(mx), -100) : 0;
+    const float sc = ldexpf(1.0f, 13 - e), isc = ldexpf(1.0f, e - 13);
     switch (tc_mtiles(P)) {
-        case 1: odd_dft_tc<1, 1>(s, frag, P, LS, TS); break;
-        case 2: odd_dft_tc<2, 1>(s, frag, P, LS, TS); break;
-        case 3: odd_dft_tc<3, 1>(s, frag, P, LS, TS); break;
-        default: odd_dft_tc<2, 2>(s, frag, P, LS, TS); break;
+        case 1: odd_dft_tc<1, 1>(s, frag, P, LS, TS, sc, isc); break;
+        case 2: odd_dft_tc<2, 1>(s, frag, P, LS, TS, sc, isc); break;
+        case 3: odd_dft_tc<3, 1>(s, frag, P, LS, TS, sc, isc); break;
+        default: odd_dft_tc<2, 2>(s, frag, P, LS, TS, sc, isc); break;
     }
 }
 
@@ -1251,8 +1268,12 @@ cudaError_t set_bucketize_smem_limit(int max_smem)
                          (const void*)bucketize_stream_kernel<false>,
                          (const void*)bucketize_stream_kernel<true>};
     for (const void* fn : fns) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        // the opt-in limit covers static and dynamic shared memory together
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -7,6 +7,7 @@
 //   scratch   same shape as bins, used between the two passes of a two-pass DFT.
 //   decode    per-bin state and lists, see DecodeWs.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -112,18 +113,22 @@ __host__ __device__ __forceinline__ int odd_row_len(int P)
 }
 // Odd axes with 17 <= P <= 127 of FP32 stages done in one pass (the whole stage in one
 // tile) run their DFTs on the tensor cores instead (two real matrix products with the
-// cosine and sine matrices, m16n8k8 TF32 MMAs with operands split into TF32 high and low
+// cosine and sine matrices, m16n8k16 FP16 MMAs with operands split into FP16 high and low
 // parts); the layout marks them AxisDesc::tc.  Their table holds the MMAs' A fragments,
-// already split: for row tile mt (16 outputs k), k-tile kt (8 inputs n) and quarter q
+// already split: for row tile mt (16 outputs k), k-tile kk (16 inputs n) and quarter q
 // (cos hi, cos lo, sin hi, sin lo), lane l's four fragment words sit at word
-// ((mt KT + kt) 4 + q) 128 + 4 l, as in tc_twiddle_word.  odd_tc: whether P qualifies.
+// ((mt KK + kk) 4 + q) 128 + 4 l, as in tc_twiddle_word.  odd_tc: whether P qualifies.
 __host__ __device__ __forceinline__ bool odd_tc(int P, int fp32)
 {
     return fp32 && (P & 1) && P >= 17 && P <= 127;
 }
 __host__ __device__ __forceinline__ int tc_mtiles(int P) { return ((P + 1) / 2 + 15) >> 4; }
+// groups of 8 input rows (padded to blocks of 32); a k-tile of the MMAs holds two of them
 __host__ __device__ __forceinline__ int tc_ktiles(int P) { return (((P + 1) / 2 + 31) >> 5) << 2; }
-// input row n of fragment slot i (0..7) of k-tile kt: blocks of 32 rows, every fourth row
+// input row n of slot i (0..7) of 8-row group kt: blocks of 32 rows, every fourth row.
+// k-tile kk's slot 2 t + j is row tc_row(2 kk + j, t), its slot 2 t + 8 + j is row
+// tc_row(2 kk + j, t + 4) (t = 0..3, j = 0, 1): the rows a lane holds, 4 apart within a
+// block, put the 16 lanes of a half-warp in distinct shared-memory banks.
 __host__ __device__ __forceinline__ int tc_row(int kt, int i)
 {
     return (kt & 3) + ((kt >> 2) << 5) + (i << 2);
@@ -132,7 +137,7 @@ __host__ __device__ __forceinline__ int tc_row(int kt, int i)
 __host__ __device__ __forceinline__ int axis_tw_count(int P, int pow2, int tc)
 {
     if (P <= 1) return 0;
-    if (tc) return tc_mtiles(P) * tc_ktiles(P) * 256;  // 8-byte entries
+    if (tc) return tc_mtiles(P) * (tc_ktiles(P) >> 1) * 256;  // 8-byte entries
     return pow2 ? (P >> 1) : ((P - 1) >> 1) * odd_row_len(P);
 }
 // Entries of the axis' table that the bucketization copies into shared memory.  Tables with
@@ -172,23 +177,51 @@ __device__ __forceinline__ void mma_tf32(float* d, uint4 a, uint32_t b0, uint32_
         : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
-// Word w of the fragment table of a tensor-core odd axis: the cosine or sine of
-// 2 pi (n k mod P) / P (FP64, rounded to FP32), for output k and input n of the fragment
-// slot, zero outside k, n <= (P - 1) / 2; its TF32 high or low part.
+// d += a b for one 16 x 8 x 16 FP16 tile: a row-major (4 registers of two halves), b
+// column-major (2), FP32 d
+__device__ __forceinline__ void mma_f16(float* d, uint4 a, uint32_t b0, uint32_t b1)
+{
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+// (hi, lo) of v0 and v1 as packed half pairs (v0 in the low half): hi = v rounded to FP16,
+// lo = the remainder rounded to FP16, so |v - hi - lo| <= 2^-22 |v| while the values stay in
+// FP16's normal range
+__device__ __forceinline__ void f16_split2(float v0, float v1, uint32_t& hi, uint32_t& lo)
+{
+    const __half2 h = __floats2half2_rn(v0, v1);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Word w of the fragment table of a tensor-core odd axis: two halves (columns 2 c' and
+// 2 c' + 1 of the m16n8k16 A fragment register c) of the cosine or sine of
+// 2 pi (n k mod P) / P (FP64, rounded to FP32), for output row k and the input rows n of
+// those slots, zero outside k, n <= (P - 1) / 2; their FP16 high or low parts.
 __device__ __forceinline__ uint32_t tc_twiddle_word(int P, int w)
 {
-    const int KT = tc_ktiles(P), pairs = (P - 1) >> 1;
+    const int KK = tc_ktiles(P) >> 1, pairs = (P - 1) >> 1;
     const int blk = w >> 7, lane = (w >> 2) & 31, c = w & 3;
     const int q = blk & 3, tile = blk >> 2;
-    const int mt = tile / KT, kt = tile - mt * KT;
+    const int mt = tile / KK, kk = tile - mt * KK;
     const int k = mt * 16 + (lane >> 2) + (c & 1) * 8;
-    const int n = tc_row(kt, (lane & 3) + (c >> 1) * 4);
-    if (k > pairs || n > pairs) return 0u;
-    double sv, cv;
-    sincospi(2.0 * (double)((n * k) % P) / (double)P, &sv, &cv);
-    const float v = (float)(q < 2 ? cv : sv);
+    float v[2];
+    for (int j = 0; j < 2; ++j) {
+        const int n = tc_row(2 * kk + j, (lane & 3) + (c >> 1) * 4);
+        v[j] = 0.0f;
+        if (k <= pairs && n <= pairs) {
+            double sv, cv;
+            sincospi(2.0 * (double)((n * k) % P) / (double)P, &sv, &cv);
+            v[j] = (float)(q < 2 ? cv : sv);
+        }
+    }
     uint32_t hi, lo;
-    tf32_split_bits(__float_as_uint(v), &hi, &lo);
+    f16_split2(v[0], v[1], hi, lo);
     return (q & 1) ? lo : hi;
 }
 #endif

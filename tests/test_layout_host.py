@@ -79,15 +79,15 @@ def test_two_pass_stages_keep_fma_axes(probe, B):
 @pytest.mark.parametrize("B,allow", [(16383, 1), (16383, 0), (16512, 1), (2499, 1)])
 def test_twiddle_offsets_and_sizes(probe, B, allow):
     """Axes' twiddles are laid out back to back from 0, each block even-sized (16-byte
-    aligned in FP32); a tensor-core axis holds mtiles * ktiles fragment tiles of 2 KB
-    (256 entries of 8 bytes)."""
+    aligned in FP32); a tensor-core axis holds mtiles * ktiles / 2 fragment tiles of 2 KB
+    (256 entries of 8 bytes: m16n8k16 tiles of 16 inputs, two 8-row groups each)."""
     lay = probe(B, allow_tc=allow)
     off = 0
     for ax in lay["axes"]:
         assert ax["tw_off"] == off and off % 2 == 0
         P = ax["P"]
         if ax["tc"]:
-            n = mtiles(P) * ktiles(P) * 256
+            n = mtiles(P) * (ktiles(P) // 2) * 256
         elif ax["pow2"]:
             n = P // 2
         else:
