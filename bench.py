@@ -553,7 +553,7 @@ def measure_noise_auto(sfft, batch=64, steps=20, warmup=3):
 
 def measure_dft_paths(sfft, batch=256, steps=20, warmup=3):
     """The R-FFAST workload's DFTs on the two paths the library has: the default (the 43- and
-    127-point direct DFTs on the tensor cores as 3-term split TF32 products) and a
+    127-point direct DFTs on the tensor cores as 3-term split FP16 products) and a
     dft_fma_only plan (every axis on the FMA pipes).  Same signals, same schedule; reports
     signals/s, the bucketization's ms per step and L0/L2 against the truth for each."""
     import torch

@@ -141,8 +141,8 @@ typedef struct {
     int32_t dft_fma_only;     /* 1 = every DFT axis on the FMA pipes.  0 (default) = in FP32
                                  stages done in one pass, the odd axes with 17 <= P <= 127 (direct
                                  P-point DFTs: a cosine and a sine matrix applied to every
-                                 sub-DFT) run on the tensor cores as 3-term split TF32 products,
-                                 with FP32-level accuracy */
+                                 sub-DFT) run on the tensor cores as 3-term split FP16 products
+                                 with FP32 accumulation, FP32-level accuracy */
     int32_t peel_atomic;      /* peeling subtraction (Sec. 3.2 subproblem 3, Eq. 20).  0 (default):
                                  every accepted frequency's subtraction is queued on the bins it
                                  aliases into and applied in increasing order of frequency, each

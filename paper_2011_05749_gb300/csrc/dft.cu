@@ -9,7 +9,8 @@
 // is one pass straight from x to the bins; otherwise the outer axes run first (from x into
 // scratch) and the inner axes second (scratch to bins).  The direct odd-axis DFTs are dense
 // contractions (a cosine and a sine matrix applied to every sub-DFT): in FP32 stages those
-// with 17 <= P <= 127 run on the tensor cores (3-term split TF32 MMAs, FP32-level accuracy),
+// with 17 <= P <= 127 run on the tensor cores (3-term split FP16 MMAs with FP32
+// accumulation, FP32-level accuracy),
 // the rest on the FMA pipes.
 #include <cuda_runtime.h>
 #include <stdint.h>
