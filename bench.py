@@ -6,8 +6,8 @@ experiments (Sec. 5.1): N = 127*128*129 = 2,097,024 complex64 samples, three sta
 B_d = 16512, 16383, 16256, eight delays per stage (0, 1 and six uniform draws), K = 1000
 coefficients with |xhat| ~ U[1, 10] and uniform phase, complex white Gaussian noise at
 20 dB SNR.  Every step recovers all S signals through the library's batched path (gather
-+ prime-factor DFTs, peeling decode, compaction).  The S inputs (4.3 GB at S = 256) are
-resident in HBM and larger than L2, so no L2 flush is needed between steps.
++ prime-factor DFTs, peeling decode, compaction).  The S inputs (8.6 GB at the default
+S = 512) are resident in HBM and larger than L2, so no L2 flush is needed between steps.
 
 Printed: one JSON line (rank 0) with signals/s, per-signal latency (p50/p99), accuracy
 against the plain FP64 path, the plain FP64 path's own signals/s, the dominant kernel's
@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--batch", type=int, default=256, help="signals per step per GPU")
+    ap.add_argument("--batch", type=int, default=512, help="signals per step per GPU")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
