@@ -917,11 +917,12 @@ __device__ __forceinline__ void signal_thresholds(const DecodeArgs& a, int sig, 
 }
 
 // Round 1: classify every bin.  One CTA per tile of kClassifyTile bins of one signal.
-// FP32: four CTAs per SM (64 registers, a few spills) hide the ML search's latency better
-// than two (decode 0.67 against 0.77 ms per 256 signals of N = 127 * 128 * 129); five or six
-// spill too much.
+// FP32: three CTAs per SM (85 registers).  With the tensor-core search, decode takes 0.462 ms
+// per 256 signals of N = 127 * 128 * 129 against 0.468 with four CTAs (64 registers) and
+// 0.490 with two; with the FMA search four had been best (0.67 against 0.77 with two), and
+// five or six spill too much.
 template <typename T>
-__global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 3 : 2)
     classify_kernel(const __grid_constant__ DecodeArgs a)
 {
     using V = typename C2<T>::t;
