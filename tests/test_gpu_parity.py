@@ -122,6 +122,28 @@ def test_bucketize_overlapped_gather_matches_oracle(sfft, oracle_mod, fma_only):
         assert rel_l2(g, r) <= TOL["fp32"], rel_l2(g, r)
 
 
+@pytest.mark.parametrize("scale", [1e30, 1e-25, 0.0])
+def test_tensor_core_axes_scale_extremes(sfft, oracle_mod, scale):
+    """The FP16-split odd axes scale each axis call's operands by a power of two from the
+    tile's largest component: signals of magnitude 1e30 and 1e-25 give the oracle's bins
+    within 1e-5 per stage and delay, and an all-zero signal gives all-zero bins (N =
+    127*128*129, tensor-core 43- and 127-point axes)."""
+    N, f, R = 2097024, (127, 128, 129), 2
+    rng = np.random.default_rng(99)
+    x = ((rng.standard_normal(N) + 1j * rng.standard_normal(N)) * scale).astype(np.complex64)
+    delays = synth.draw_delays(N, 3, R, rng)
+    plan = sfft.Plan(N, 4, f, delays, precision="fp32")
+    bins = plan.bucketize(to_dev(x, np.complex64)).cpu().numpy()
+    plan.close()
+    assert np.all(np.isfinite(bins))
+    if scale == 0.0:
+        assert not np.any(bins)
+        return
+    Y = oracle_mod.bucketize(N, f, delays, x.astype(np.complex128))
+    for g, r in zip(split_bins(bins, N, f, R), split_bins(Y, N, f, R)):
+        assert rel_l2(g, r) <= TOL["fp32"], rel_l2(g, r)
+
+
 @pytest.mark.parametrize("N,f,R", [(2097024, (127, 128, 129), 2), (551286, (81, 82, 83), 3)])
 def test_bucketize_fma_only_matches_oracle(sfft, oracle_mod, N, f, R):
     """dft_fma_only plans keep every odd axis on the FMA pipes (no tensor-core axes): the
