@@ -146,14 +146,15 @@ __device__ void axis_dft_odd(typename C2<T>::t* s, const typename C2<T>::t* twm,
 // block), so the tile makes ceil(log2P / 3) trips through shared memory.
 // tw[t] = (cos, sin)(2 pi t / P), t < P / 2; the butterfly of the stage with half-size H
 // multiplies by W_P^{(p mod H) P / (2 H)}.
-// nst < log2P runs only the first nst stages (the caller does the rest).
+// nst < log2P runs only the first nst stages (the caller does the rest); lh0 > 0 starts at
+// stage lh0 (the first lh0 done already).
 template <typename T>
 __device__ void axis_fft_pow2(typename C2<T>::t* s, const typename C2<T>::t* tw, int P,
-                              int log2P, int LS, int TS, int nst)
+                              int log2P, int LS, int TS, int nst, int lh0 = 0)
 {
     using V = typename C2<T>::t;
     const int M = TS / P;
-    for (int lh = 0; lh < nst;) {
+    for (int lh = lh0; lh < nst;) {
         const int c = min(3, nst - lh);
         const int G8 = 1 << c;
         const int h = 1 << lh;
@@ -821,7 +822,72 @@ __global__ void __launch_bounds__(512, 1) bucketize_kernel(const __grid_constant
     // a host signal read in place takes the register loads of the general path below (no
     // asynchronous copies from host memory)
     const bool host_src = a.x_sys && ps.src_gather;
+    int pow2_done = 0;  // radix-2 stages of the outermost axis done in the gather
     if constexpr (sizeof(XS) == sizeof(T)) {
+        // a whole-stage tile whose outermost axis is a power of two (stored bit-reversed):
+        // each work item gathers the 2^c samples of one radix-8 group of that axis into
+        // registers and runs the axis' first c radix-2 stages on them before its single
+        // store, which saves the axis a trip through shared memory (c <= 3; the rest of the
+        // axis runs in axis_fft_pow2 from stage c on, the last stage in the store)
+        const int ao = st.n_axes - 1;
+        if (ps.src_gather && Tb == 1 && Ta == 1 && !host_src && a0 == 0 && a1 == st.n_axes &&
+            ps.dst_bins && st.ax[ao].pow2 && st.ax[ao].log2P >= 2) {
+            const AxisDesc& A = st.ax[ao];
+            const int P = A.P, S = A.S, lg = A.log2P;
+            const int c = min(3, lg - 1), G8 = 1 << c;
+            const int nw = S * (P >> c);
+            const float invS = 1.0f / (float)S;
+            const V* twp = reinterpret_cast<const V*>(a.tw) + A.tw_off;
+            const V* xv = reinterpret_cast<const V*>(x);
+            constexpr int UI = 2;  // work items per trip: their 16 loads in flight at once
+            for (int w0 = threadIdx.x; w0 < nw; w0 += UI * blockDim.x) {
+                V v[UI][8];
+                int pos[UI];
+                bool ok[UI];
+#pragma unroll
+                for (int k = 0; k < UI; ++k) {
+                    int w = w0 + k * blockDim.x;
+                    ok[k] = w < nw;
+                    if (!ok[k]) w = w0;
+                    int m;
+                    const int blk = fdivmod(w, S, invS, &m);
+                    pos[k] = m + blk * G8 * S;
+                    int src[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) src[i] = i < G8 ? __ldg(nidx + pos[k] + i * S) : 0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (i >= G8) continue;
+                        int xi = src[i] * L + tau;
+                        xi = xi >= N ? xi - N : xi;
+                        v[k][i] = __ldg(xv + xi);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < UI; ++k)
+#pragma unroll
+                    for (int sg = 0; sg < 3; ++sg) {
+                        if (sg >= c) break;
+                        const int hs = 1 << sg;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            if (i >= G8 || (i & hs)) continue;
+                            const V wv = __ldg(twp + ((i & (hs - 1)) << (lg - 1 - sg)));
+                            const V u = v[k][i], xx = v[k][i + hs];
+                            const V xt = {fma(xx.x, wv.x, xx.y * wv.y), fma(xx.y, wv.x, -(xx.x * wv.y))};
+                            v[k][i] = V{u.x + xt.x, u.y + xt.y};
+                            v[k][i + hs] = V{u.x - xt.x, u.y - xt.y};
+                        }
+                    }
+#pragma unroll
+                for (int k = 0; k < UI; ++k)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < G8 && ok[k]) s[pos[k] + i * S] = v[k][i];
+            }
+            pow2_done = c;
+            goto loaded;
+        }
         if (ps.src_gather && Tb == 1 && Ta == 1 && !host_src) {
             // whole-stage tile straight from x: sample indices from the table, then
             // asynchronous 8/16-byte copies into shared memory, all in flight at once
@@ -944,7 +1010,7 @@ loaded:
                 a2 = ax;
                 tw2 = tws + off;
             }
-            axis_fft_pow2<T>(s, tws + off, A.P, A.log2P, LS, TS, defer ? A.log2P - 1 : A.log2P);
+            axis_fft_pow2<T>(s, tws + off, A.P, A.log2P, LS, TS, defer ? A.log2P - 1 : A.log2P, pow2_done);
         } else if (A.P > 1) {
             if (A.P <= 9) {
                 if (whole && a3 < 0) {

@@ -104,7 +104,9 @@ def test_bucketize_overlapped_gather_matches_oracle(sfft, oracle_mod, fma_only):
     """The benchmark's bucketization shape (N = 127*128*129, 8 delays, FP32), whose whole-stage
     tiles fill more than half of shared memory: the persistent kernel that overlaps the next
     tile's gather with the current tile's DFTs gives the oracle's bins within 1e-5 per stage
-    and delay, and the same bits as one CTA per tile."""
+    and delay, as one CTA per tile does.  With tensor-core odd axes (run last by both) the
+    two give the same bits; on the FMA pipes the per-tile kernel runs the 128-point axis'
+    first radix-8 pass inside its gather, before the 43-point axis, so the rounding differs."""
     N, f, R = 2097024, (127, 128, 129), 8
     rng = np.random.default_rng(808)
     x = (rng.standard_normal(N) + 1j * rng.standard_normal(N)).astype(np.complex64)
@@ -116,10 +118,12 @@ def test_bucketize_overlapped_gather_matches_oracle(sfft, oracle_mod, fma_only):
     b_off = off.bucketize(xd).cpu().numpy()
     on.close()
     off.close()
-    np.testing.assert_array_equal(b_on.view(np.uint8), b_off.view(np.uint8))
+    if not fma_only:
+        np.testing.assert_array_equal(b_on.view(np.uint8), b_off.view(np.uint8))
     Y = oracle_mod.bucketize(N, f, delays, x.astype(np.complex128))
-    for g, r in zip(split_bins(b_on, N, f, R), split_bins(Y, N, f, R)):
-        assert rel_l2(g, r) <= TOL["fp32"], rel_l2(g, r)
+    for b in (b_on, b_off):
+        for g, r in zip(split_bins(b, N, f, R), split_bins(Y, N, f, R)):
+            assert rel_l2(g, r) <= TOL["fp32"], rel_l2(g, r)
 
 
 @pytest.mark.parametrize("scale", [1e30, 1e-25, 0.0])
