@@ -16,6 +16,7 @@
 #include "launch.h"
 #include "sfft.h"
 #include "sfft_internal.cuh"
+#include "ml_table.h"
 #include "pfa_layout.h"
 #include "sfft_plan.h"
 
@@ -417,27 +418,13 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         s.mltc_off = -1;
         if (!ml_tc) continue;
         s.mltc_off = (int32_t)(h_mltc.size() / 256);
-        const int L = s.L, RP = ml_tc_rp(n_delays), KT = RP / 4, MT = (L + 7) / 8;
-        const double two_pi = 6.283185307179586476925286766559;
+        const int L = s.L, KT = ml_tc_rp(n_delays) / 4, MT = (L + 7) / 8;
         for (int mt = 0; mt < MT; ++mt)
             for (int kt = 0; kt < KT; ++kt)
                 for (int h = 0; h < 2; ++h)
                     for (int l = 0; l < 32; ++l)
-                        for (int e = 0; e < 4; ++e) {
-                            const int row = (l >> 2) + (e & 1) * 8, k = kt * 8 + (l & 3) + (e >> 1) * 4;
-                            const int q = mt * 8 + (row & 7), im = row >> 3;
-                            const int part = k / RP, r = k % RP;
-                            float v = 0.0f;
-                            if (q < L && r < n_delays) {
-                                const double th = two_pi * (double)(((int64_t)q * s.tauL[r]) % L) / (double)L;
-                                const double cv = cos(th), sv = sin(th);
-                                v = (float)(im == 0 ? (part == 0 ? cv : sv) : (part == 0 ? -sv : cv));
-                            }
-                            uint32_t bits, hi, lo;
-                            memcpy(&bits, &v, 4);
-                            tf32_split_bits(bits, &hi, &lo);
-                            h_mltc.push_back(h == 0 ? hi : lo);
-                        }
+                        for (int e = 0; e < 4; ++e)
+                            h_mltc.push_back(ml_tc_word(L, n_delays, s.tauL, mt, kt, h, l, e));
     }
     // ML candidate phasors per stage: W[r][q] = e^{2 pi i (q tauL_r mod L) / L}, a row of L
     // candidates per delay
