@@ -166,6 +166,14 @@ typedef struct {
                                  scaling by N / 2 pi in FP32; bit 1 = no snap, f = the integer
                                  nearest the estimate.  Modes 1-3 exist to measure what the FP64
                                  angle and the snap buy; they are not meant for use */
+    int32_t ml_tc_tf32;       /* the first peeling round's ML search on the tensor cores (FP32
+                                 plans, classify_lanes = 0, n_delays <= 16): the scores of a
+                                 bin's L candidates as the product of the stage's candidate
+                                 matrix with the bin's Z_r.  0 (default) = m16n8k16 FP16 MMAs, both
+                                 operands split into high and low FP16 parts (three partial
+                                 products, FP32 accumulation) after a power-of-two scale per
+                                 bin; 1 = m16n8k8 TF32 MMAs with split operands, twice the
+                                 MMAs.  Both give FP32-level scores */
 } sfft_opts;
 
 /* Fill *opts with the defaults above. */

@@ -54,7 +54,8 @@ class Opts(ctypes.Structure):
                 ("noise_auto", ctypes.c_int32), ("host_gather", ctypes.c_int32),
                 ("oneshot_method", ctypes.c_int32), ("dft_fma_only", ctypes.c_int32),
                 ("peel_atomic", ctypes.c_int32), ("overlap_gather", ctypes.c_int32),
-                ("classify_lanes", ctypes.c_int32), ("arg_mode", ctypes.c_int32)]
+                ("classify_lanes", ctypes.c_int32), ("arg_mode", ctypes.c_int32),
+                ("ml_tc_tf32", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

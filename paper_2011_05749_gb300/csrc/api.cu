@@ -236,6 +236,7 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
     if (o.classify_lanes < 0 || o.classify_lanes > 32 || (o.classify_lanes & (o.classify_lanes - 1)))
         return SFFT_EINVAL;
     if (o.arg_mode < 0 || o.arg_mode > 3) return SFFT_EINVAL;
+    if (o.ml_tc_tf32 != 0 && o.ml_tc_tf32 != 1) return SFFT_EINVAL;
     DevInfo di;
     int rc = device_info(&di);
     if (rc) return rc;
@@ -410,7 +411,9 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         tw_t.push_back((int32_t)((h << pd.ph_shift) % N));
     }
     // the first round's ML search on the tensor cores (FP32 peeling plans, R <= 16): per
-    // stage the split fragments of A (ml_tc_rp), from the same phasors in FP64 rounded to FP32
+    // stage the split fragments of A, from the same phasors in FP64 rounded to FP32, in the
+    // split-FP16 layout (ml_tc16_word) or, with ml_tc_tf32, the split-TF32 one (ml_tc_word);
+    // fragment tiles of 256 words either way
     std::vector<uint32_t> h_mltc;
     const bool ml_tc = p->prec == 1 && o.locate == SFFT_LOCATE_ML && pd.mode == 0 && n_delays <= 16;
     for (int d = 0; d < n_stages; ++d) {
@@ -418,13 +421,15 @@ extern "C" int sfft_plan_create(sfft_plan_t* out, int64_t N, int32_t K, int32_t 
         s.mltc_off = -1;
         if (!ml_tc) continue;
         s.mltc_off = (int32_t)(h_mltc.size() / 256);
-        const int L = s.L, KT = ml_tc_rp(n_delays) / 4, MT = (L + 7) / 8;
+        const int L = s.L, MT = (L + 7) / 8;
+        const int KT = o.ml_tc_tf32 ? ml_tc_rp(n_delays) / 4 : ml_tc16_ktiles(n_delays);
         for (int mt = 0; mt < MT; ++mt)
             for (int kt = 0; kt < KT; ++kt)
                 for (int h = 0; h < 2; ++h)
                     for (int l = 0; l < 32; ++l)
                         for (int e = 0; e < 4; ++e)
-                            h_mltc.push_back(ml_tc_word(L, n_delays, s.tauL, mt, kt, h, l, e));
+                            h_mltc.push_back(o.ml_tc_tf32 ? ml_tc_word(L, n_delays, s.tauL, mt, kt, h, l, e)
+                                                          : ml_tc16_word(L, n_delays, s.tauL, mt, kt, h, l, e));
     }
     // ML candidate phasors per stage: W[r][q] = e^{2 pi i (q tauL_r mod L) / L}, a row of L
     // candidates per delay
@@ -724,6 +729,7 @@ int run_chunk(sfft_plan_s* p, int n, const void* x0, const void* const* d_xs,
     da.wtab_smem = (size_t)p->wtab_elems * p->esz <= 160 * 1024 ? 1 : 0;
     da.dt_method = p->opts.oneshot_method == 0 ? 2 : p->opts.oneshot_method;
     da.lanes = p->opts.classify_lanes;
+    da.ml_tf32 = p->opts.ml_tc_tf32;
     const int threads = 512;
     const int total = p->num_sms * p->decode_occ;
     // later rounds touch O(K) bins: about one CTA per 256 expected single-tons

@@ -474,6 +474,217 @@ __device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, con
     }
 }
 
+// The same search with m16n8k16 FP16 MMAs (the plan's default; ml_tc_tf32 = 0 selects the
+// one above): a k-tile holds 8 delays, so the candidate matrix of R <= 8 delays is one
+// k-tile and each (candidate tile, n-tile) takes three MMAs where the TF32 search takes six,
+// with half the fragment loads.  Lane (g, t) holds Z of delays 8 kk + 2 t + j (j = 0, 1) of
+// bin 8 u + g: with the stage's FP16 table (ml_tc16_word) column k' of k-tile kk multiplies
+// Re Z_{8 kk + k'} (k' < 8) or Im Z_{8 kk + k' - 8}, and the m16n8k16 B fragment of lane
+// (g, t) is rows 2 t, 2 t + 1 (register 0) and 2 t + 8, 2 t + 9 (register 1) of column g.
+// FP16's range is kept by a power-of-two scale per bin (its largest Z component mapped
+// into [2^13, 2^14), as the tensor-core DFT axes do per tile): a bin's candidates share the
+// scale, so its argmax is that of the unscaled scores.  Both operands are split into high
+// and low FP16 parts and three partial products kept (FP32-level scores).  With one k-tile
+// the next candidate tile's fragments are loaded while the current one's MMAs run.  Argmax,
+// fit and records as in locate_ml_tc.
+template <int KK, int NT>
+__device__ __noinline__ void locate_ml_tc16(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                                            const float2* Y, const float2* wtab, int32_t wtab_base,
+                                            int round, const int* bl, int nb, const Thr* thr)
+{
+    using V = float2;
+    constexpr int NZ = 2 * KK;  // Z per lane and bin: slot i is delay 8 (i / 2) + 2 t + i % 2
+    const PlanDesc& pd = a.pd;
+    const int lane = (int)(threadIdx.x & 31), g = lane >> 2, t = lane & 3;
+    const int d = stage_of(pd, bl[0]);
+    const StageDesc& st = pd.st[d];
+    const int R = pd.R, B = st.B, L = st.L;
+    auto delay_of = [&](int i) { return 8 * (i >> 1) + 2 * t + (i & 1); };
+    float zx[NT][NZ], zy[NT][NZ];
+    uint32_t bh[NT][KK][2], bo[NT][KK][2];  // B fragments: high and low parts
+    {
+        int jg[NT];
+        V y[NT][NZ];
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            const int i8 = 8 * u + g;
+            const int bg = bl[i8 < nb ? i8 : 0];
+            jg[u] = __ldg(a.pbin + bg);
+            const V* Yg = Y + st.y_off + (bg - st.bin_base);
+#pragma unroll
+            for (int i = 0; i < NZ; ++i) {
+                const int r = delay_of(i);
+                y[u][i] = r < R && i8 < nb ? __ldcg(Yg + (int64_t)r * B) : V{0.0f, 0.0f};
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < NT; ++u)
+#pragma unroll
+            for (int i = 0; i < NZ; ++i) {
+                const int r = delay_of(i);
+                const V aj = delay_phasor<float>(a, jg[u], st.tau[r < R ? r : 0]);
+                zx[u][i] = y[u][i].x * aj.x + y[u][i].y * aj.y;
+                zy[u][i] = y[u][i].y * aj.x - y[u][i].x * aj.y;
+            }
+    }
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        // the bin's scale: its largest component over the four lanes that hold its Z
+        float mx = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) mx = fmaxf(mx, fmaxf(fabsf(zx[u][i]), fabsf(zy[u][i])));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+        const float sc = ldexpf(1.0f, 13 - (mx > 0.0f ? max(ilogbf(mx), -100) : 0));
+#pragma unroll
+        for (int kk = 0; kk < KK; ++kk) {
+            f16_split2(zx[u][2 * kk] * sc, zx[u][2 * kk + 1] * sc, bh[u][kk][0], bo[u][kk][0]);
+            f16_split2(zy[u][2 * kk] * sc, zy[u][2 * kk + 1] * sc, bh[u][kk][1], bo[u][kk][1]);
+        }
+    }
+    const uint4* fr = a.mltc + (size_t)st.mltc_off * 64 + lane;
+    const int MT = (L + 7) >> 3;
+    float best[NT][2];
+    int bq[NT][2];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        best[u][0] = best[u][1] = -1.0f;
+        bq[u][0] = bq[u][1] = 0;
+    }
+    // with one k-tile the registers allow the next candidate tile's fragments in flight
+    constexpr bool kAhead = KK == 1;
+    uint4 nh[KK], nl[KK];
+    if constexpr (kAhead) {
+        nh[0] = __ldg(fr);
+        nl[0] = __ldg(fr + 32);
+    }
+    for (int mt = 0; mt < MT; ++mt) {
+        uint4 ah[KK], al[KK];
+        if constexpr (kAhead) {
+            ah[0] = nh[0];
+            al[0] = nl[0];
+            // the next tile's fragments (the last tile's again at the end: in bounds, unused)
+            const int mn = min(mt + 1, MT - 1);
+            nh[0] = __ldg(fr + mn * 64);
+            nl[0] = __ldg(fr + mn * 64 + 32);
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < KK; ++kk) {
+                ah[kk] = __ldg(fr + (mt * KK + kk) * 64);
+                al[kk] = __ldg(fr + (mt * KK + kk) * 64 + 32);
+            }
+        }
+        float c[NT][4], e[NT][4], f[NT][4];
+#pragma unroll
+        for (int u = 0; u < NT; ++u)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) c[u][x] = e[u][x] = f[u][x] = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < KK; ++kk)
+#pragma unroll
+            for (int u = 0; u < NT; ++u) {
+                mma_f16(e[u], al[kk], bh[u][kk][0], bh[u][kk][1]);
+                mma_f16(f[u], ah[kk], bo[u][kk][0], bo[u][kk][1]);
+                mma_f16(c[u], ah[kk], bh[u][kk][0], bh[u][kk][1]);
+            }
+        // rows g / g + 8: Re / Im c of candidate 8 mt + g; columns 2 t, 2 t + 1: the bins
+        const int q = 8 * mt + g;
+        if (q < L) {
+#pragma unroll
+            for (int u = 0; u < NT; ++u)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float cx = c[u][h] + (e[u][h] + f[u][h]);
+                    const float cy = c[u][2 + h] + (e[u][2 + h] + f[u][2 + h]);
+                    const float sc = cx * cx + cy * cy;
+                    if (sc > best[u][h]) {
+                        best[u][h] = sc;
+                        bq[u][h] = q;
+                    }
+                }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best[u][h], o);
+                const int oq = __shfl_xor_sync(0xffffffffu, bq[u][h], o);
+                if (ob > best[u][h] || (ob == best[u][h] && oq < bq[u][h])) {
+                    best[u][h] = ob;
+                    bq[u][h] = oq;
+                }
+            }
+    // the fit of bin 8 u + g on lanes (g, 0..3); its best candidate is held by lane g / 2
+    const V* W = wtab + (st.wtab_off - wtab_base);
+    const float scl = 1.0f / ((float)R * (float)B);
+    bool ok[NT];
+    V vv[NT];
+    int qq[NT];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        const int i8 = 8 * u + g;
+        const int q0 = __shfl_sync(0xffffffffu, bq[u][0], g >> 1);
+        const int q1 = __shfl_sync(0xffffffffu, bq[u][1], g >> 1);
+        const int qb = (g & 1) ? q1 : q0;
+        float cx = 0.0f, cy = 0.0f;
+        V wr[NZ];
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) {
+            const int r = delay_of(i);
+            wr[i] = r < R ? W[r * L + qb] : V{0.0f, 0.0f};
+            cx = fma(zx[u][i], wr[i].x, fma(zy[u][i], wr[i].y, cx));
+            cy = fma(zy[u][i], wr[i].x, fma(-zx[u][i], wr[i].y, cy));
+        }
+        cx += __shfl_xor_sync(0xffffffffu, cx, 1);
+        cy += __shfl_xor_sync(0xffffffffu, cy, 1);
+        cx += __shfl_xor_sync(0xffffffffu, cx, 2);
+        cy += __shfl_xor_sync(0xffffffffu, cy, 2);
+        const V v = {cx * scl, cy * scl};
+        float e2 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) {
+            if (delay_of(i) < R) {
+                const float ex = zx[u][i] - (float)B * (v.x * wr[i].x - v.y * wr[i].y);
+                const float ey = zy[u][i] - (float)B * (v.x * wr[i].y + v.y * wr[i].x);
+                e2 += ex * ex + ey * ey;
+            }
+        }
+        e2 += __shfl_xor_sync(0xffffffffu, e2, 1);
+        e2 += __shfl_xor_sync(0xffffffffu, e2, 2);
+        ok[u] = t == 0 && i8 < nb && below(e2, thr[d].T1f, thr[d].T1);
+        vv[u] = v;
+        qq[u] = qb;
+    }
+    // the warp's single-tons: one list reservation for all of them
+    unsigned m[NT];
+    int n_rec = 0;
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        m[u] = __ballot_sync(0xffffffffu, ok[u]);
+        n_rec += __popc(m[u]);
+    }
+    if (n_rec == 0) return;
+    int base = 0;
+    if (lane == 0) {
+        base = atomicAdd(ctr + kCtrRoundBase + 3 * round + 2, n_rec);
+        atomicAdd(ctr + kCtrResolved, n_rec);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const unsigned below_me = (1u << lane) - 1u;
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        if (ok[u]) {
+            const int b = bl[8 * u + g];
+            const int64_t f = (int64_t)__ldg(a.pbin + b) + (int64_t)qq[u] * B;
+            record_at<float>(w, round, b, f, vv[u], base + __popc(m[u] & below_me));
+        }
+        base += __popc(m[u]);
+    }
+}
+
 // Lanes per bin for the ML search of n bins with at most Lmax candidates by nt threads:
 // the G that minimises (bins per lane) x (work per bin and lane), where a bin costs every
 // lane of its group ~4 R FMAs per candidate it scans, forming Z (shared when G >= R) and
@@ -1019,6 +1230,13 @@ __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 3 : 2)
                 for (int k = (int)(threadIdx.x >> 5); k < t_all; k += nw) {
                     const int* bl = k < t_lo ? s_nz + NB * k : nz_hi + NB * (k - t_lo);
                     const int nb = min(NB, k < t_lo ? n_lo - NB * k : n_hi - NB * (k - t_lo));
+                    if (!a.ml_tf32) {
+                        if (pd.R <= 8)
+                            locate_ml_tc16<1, 2>(a, w.ctr, w, Y, wtab, wtab_base, 1, bl, nb, s_thr);
+                        else
+                            locate_ml_tc16<2, 2>(a, w.ctr, w, Y, wtab, wtab_base, 1, bl, nb, s_thr);
+                        continue;
+                    }
                     switch ((pd.R + 3) >> 2) {
                         case 1: locate_ml_tc<1, 2>(a, w.ctr, w, Y, wtab, wtab_base, 1, bl, nb, s_thr); break;
                         case 2: locate_ml_tc<2, 2>(a, w.ctr, w, Y, wtab, wtab_base, 1, bl, nb, s_thr); break;

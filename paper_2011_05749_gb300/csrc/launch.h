@@ -36,6 +36,7 @@ struct DecodeArgs {
     int32_t wtab_smem;    // 1: classify stages them in shared memory
     int32_t dt_method;    // one-shot Step 2: 1 polynomial roots, 2 enumeration, 3 matrix pencil
     int32_t lanes;        // classify: lanes per bin of the ML search (0 = chosen per tile)
+    int32_t ml_tf32;      // classify's tensor-core ML search: 1 = split TF32 (m16n8k8), 0 = split FP16 (m16n8k16)
     const int32_t* pbin;  // position -> bin j, per stage at bin_base
     const int32_t* bpos;  // bin j -> position
     const void* roots;    // the plan's twiddle table: ML phasor tables at st[d].wtab_off

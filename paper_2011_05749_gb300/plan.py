@@ -27,7 +27,7 @@ class Plan:
                  decoder: str = "peel", a_m: int = 3, kay_m: int = 2, noise_auto: bool = False,
                  host_gather: bool = False, dft_fma_only: bool = False, dt_method: int = 2,
                  peel_atomic: bool = False, overlap_gather: bool = False,
-                 classify_lanes: int = 0, arg_mode: int = 0):
+                 classify_lanes: int = 0, arg_mode: int = 0, ml_tc_tf32: bool = False):
         lib = load()
         f = np.ascontiguousarray(f, dtype=np.int64)
         delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int64).reshape(f.size, -1))
@@ -44,6 +44,7 @@ class Plan:
         o.overlap_gather = 1 if overlap_gather else 0
         o.classify_lanes = classify_lanes
         o.arg_mode = arg_mode
+        o.ml_tc_tf32 = 1 if ml_tc_tf32 else 0
         o.oneshot_method = dt_method
         o.max_rounds = max_rounds
         o.max_batch = max_batch

@@ -43,6 +43,7 @@ def split_bins(Y, N, f, R):
 def oracle_opts(oracle_mod, plan_kw, p):
     prec = plan_kw.get("precision", "fp32")
     return oracle_mod.OracleOpts(noise_var=plan_kw.get("noise_var", 0.0),
+                                 a_min=plan_kw.get("a_min", 1.0),
                                  eta=1e-6 if prec == "fp64" else 3e-3,
                                  locate=0 if plan_kw.get("locate", "ml") == "arg" else 1)
 
@@ -269,39 +270,62 @@ def test_execute_rffast_124950(sfft, oracle_mod, prec, snr):
     assert_matches_oracle(idx, val, info, ref, prec)
 
 
-@pytest.mark.parametrize("lanes", [0, 2, 32])
+@pytest.mark.parametrize("lanes,tf32", [(0, False), (0, True), (2, False), (32, False)])
 @pytest.mark.parametrize("name,seed", [("rffast_2097024", 41), ("rffast_124950", 42)])
-def test_ml_search_paths_match_oracle(sfft, oracle_mod, name, seed, lanes):
-    """The first round's ML candidate search two ways: on the tensor cores (classify_lanes =
-    0, the default for FP32 plans: split-TF32 scores of 16 bins per warp against the stage's
-    candidate matrix) and on the FMA pipes with 2 or 32 lanes per bin.  R = 8 (K-tiles of
-    exactly 8 delays) and R = 6 (padded to 8), 20 dB: each gives the oracle's support,
+def test_ml_search_paths_match_oracle(sfft, oracle_mod, name, seed, lanes, tf32):
+    """The first round's ML candidate search three ways: on the tensor cores (classify_lanes
+    = 0, the default for FP32 plans: scores of 16 bins per warp against the stage's
+    candidate matrix) as split-FP16 m16n8k16 MMAs (the default) or split-TF32 m16n8k8 MMAs
+    (ml_tc_tf32), and on the FMA pipes with 2 or 32 lanes per bin.  R = 8 (one FP16 k-tile,
+    two TF32 k-tiles, exactly) and R = 6 (padded), 20 dB: each gives the oracle's support,
     values, rounds and identifications."""
     p = synth.config_problem(name, seed=seed)
     kw = dict(precision="fp32", locate="ml", noise_var=p.noise_var)
     Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x.astype(np.complex64).astype(np.complex128))
     ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
-    plan, idx, val, info = run_plan(sfft, p, classify_lanes=lanes, **kw)
+    plan, idx, val, info = run_plan(sfft, p, classify_lanes=lanes, ml_tc_tf32=tf32, **kw)
     assert_matches_oracle(idx, val, info, ref, "fp32")
     np.testing.assert_array_equal(idx, p.support)
     plan.close()
 
 
-@pytest.mark.parametrize("R", [4, 5, 10, 12, 16])
+@pytest.mark.parametrize("R", [4, 5, 9, 10, 12, 16])
 def test_ml_tensor_core_search_delay_counts(sfft, oracle_mod, R):
-    """The tensor-core ML search for delay counts that fill one to four k-tiles of 4 delays,
-    exactly (4, 12, 16) or with padding (5, 10): N = 49*50*51, K = 120 at 25 dB, random
-    delays.  The oracle's support, values, rounds and identifications, as with the FMA
-    search (classify_lanes = 4)."""
+    """The tensor-core ML searches for delay counts that fill one or two FP16 k-tiles of 8
+    delays and one to four TF32 k-tiles of 4, exactly (TF32: 4, 12, 16; FP16: 16) or with
+    padding (5, 9, 10): N = 49*50*51, K = 120 at 25 dB, random delays.  The oracle's support,
+    values, rounds and identifications, as with the FMA search (classify_lanes = 4)."""
     p = synth.make_problem(124950, (49, 50, 51), 120, seed=60 + R, R=R, delays="random",
                            mag=(1.0, 10.0), snr_db=25.0)
     kw = dict(precision="fp32", locate="ml", noise_var=p.noise_var)
     Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x.astype(np.complex64).astype(np.complex128))
     ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
-    for lanes in (0, 4):
-        plan, idx, val, info = run_plan(sfft, p, classify_lanes=lanes, **kw)
+    for lanes, tf32 in ((0, False), (0, True), (4, False)):
+        plan, idx, val, info = run_plan(sfft, p, classify_lanes=lanes, ml_tc_tf32=tf32, **kw)
         assert_matches_oracle(idx, val, info, ref, "fp32")
         plan.close()
+
+
+@pytest.mark.parametrize("tf32", [False, True])
+def test_ml_tensor_core_search_wide_magnitudes(sfft, oracle_mod, tf32):
+    """Coefficient magnitudes spread over three decades (log-uniform in [0.1, 100], a_min =
+    0.1, exactly sparse, N = 49*50*51, K = 150, R = 8 random delays): the FP16 search scales
+    each bin by its own power of two, so weak and strong bins in one warp task are located
+    alike; both tensor-core searches give the oracle's support, values, rounds and
+    identifications."""
+    rng = np.random.default_rng(4242)
+    N, f, K = 124950, (49, 50, 51), 150
+    support = np.sort(rng.choice(N, size=K, replace=False)).astype(np.int64)
+    values = 10.0 ** rng.uniform(-1.0, 2.0, K) * np.exp(2j * np.pi * rng.uniform(size=K))
+    p = synth.make_problem(N, f, K, seed=4243, R=8, delays="random", support=support,
+                           values=values)
+    kw = dict(precision="fp32", locate="ml", noise_var=0.0, a_min=0.1)
+    Y = oracle_mod.bucketize(p.N, p.f, p.delays, p.x.astype(np.complex64).astype(np.complex128))
+    ref = oracle_mod.decode(p.N, p.f, p.delays, Y, p.K, oracle_opts(oracle_mod, kw, p))
+    plan, idx, val, info = run_plan(sfft, p, ml_tc_tf32=tf32, **kw)
+    assert_matches_oracle(idx, val, info, ref, "fp32")
+    np.testing.assert_array_equal(idx, support)
+    plan.close()
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
