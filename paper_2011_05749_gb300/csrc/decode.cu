@@ -290,109 +290,97 @@ __device__ void locate_ml_group(const DecodeArgs& a, int32_t* ctr, const DecodeW
 
 // D2 on the tensor cores (FP32, ML, the first round): the scores of up to 8 NT bins of one
 // stage (bl[0 .. nb)) against all L candidates as the product A Z of the stage's fragment
-// tables (ml_tc_rp) with the bins' Z_r = Y_r conj(a_r(j)) -- n-tile u's column g is bin
-// 8 u + g, and lane slot t of k-tile i holds delay t + 4 i -- in m16n8k8 TF32 MMAs with both
-// operands split into high and low parts, three partial products kept, as the tensor-core
-// DFT axes (FP32-level scores); each A fragment serves the NT n-tiles.  Lane (g, t) keeps the
-// best of candidates 8 mt + g for bins 2 t and 2 t + 1 of each n-tile; the eight lanes sharing
-// t reduce them (lowest q on ties).  The fit of bin 8 u + g then runs on lanes (g, 0..3),
-// which hold its Z_{t + 4 i}: v = sum_r Z_r conj(W[r][bq]) / (R B) and the residual, each a
-// sum of per-lane parts.  Every lane of the warp calls this in lockstep.
-template <int NZ, int NT>
-__device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
-                                          const float2* Y, const float2* wtab, int32_t wtab_base,
-                                          int round, const int* bl, int nb, const Thr* thr)
+// table (the candidate matrix, split into high and low parts) with the bins' [Re Z; Im Z],
+// Z_r = Y_r conj(a_r(j)) -- n-tile u's column g is bin 8 u + g -- keeping three partial
+// products (hi hi + hi lo + lo hi, FP32-level scores) as the tensor-core DFT axes do.
+// Two forms, which differ only in the MMA shape and so in which delays a lane holds:
+//   split TF32 (locate_ml_tc, ml_tc_tf32 = 1): m16n8k8 MMAs, the table of ml_tc_word, lane
+//     slot i holds delay t + 4 i (k-tiles of 4 delays);
+//   split FP16 (locate_ml_tc16, the default): m16n8k16 MMAs, the table of ml_tc16_word, lane
+//     slot i holds delay 8 (i / 2) + 2 t + i % 2 (k-tiles of 8 delays, so R <= 8 is one
+//     k-tile and a candidate tile takes half the MMAs and fragment loads), with a
+//     power-of-two scale per bin -- its largest Z component mapped into [2^13, 2^14) -- which
+//     all of its candidates share, so its argmax is that of the unscaled scores.
+// Each A fragment serves the NT n-tiles.  Lane (g, t) keeps the best of candidates 8 mt + g
+// for bins 2 t and 2 t + 1 of each n-tile; the eight lanes sharing t reduce them (lowest q
+// on ties).  The fit of bin 8 u + g then runs on lanes (g, 0..3), which hold its Z:
+// v = sum_r Z_r conj(W[r][bq]) / (R B) and the residual, each a sum of per-lane parts.
+// Every lane of the warp calls these in lockstep.
+template <bool F16>
+__device__ __forceinline__ int ml_tc_delay(int i, int t)
+{
+    return F16 ? 8 * (i >> 1) + 2 * t + (i & 1) : t + 4 * i;
+}
+
+// Z of bin 8 u + g at the lane's delays: every load in flight at once (bins, then their
+// samples and phasors)
+template <int NZ, int NT, bool F16>
+__device__ __forceinline__ void ml_tc_form_z(const DecodeArgs& a, const StageDesc& st, const float2* Y,
+                                             const int* bl, int nb, float (&zx)[NT][NZ], float (&zy)[NT][NZ])
 {
     using V = float2;
-    constexpr int RP = 4 * NZ, KT = NZ;
-    const PlanDesc& pd = a.pd;
     const int lane = (int)(threadIdx.x & 31), g = lane >> 2, t = lane & 3;
-    const int d = stage_of(pd, bl[0]);
-    const StageDesc& st = pd.st[d];
-    const int R = pd.R, B = st.B, L = st.L;
-    float zx[NT][NZ], zy[NT][NZ];      // Z_{t + 4 i} of bin 8 u + g
-    uint32_t bh[NT][KT][2], bo[NT][KT][2];  // its B fragments: high and low parts
-    {
-        // every load of the Z_r in flight at once: bins, then their samples and phasors
-        int jg[NT];
-        V y[NT][NZ];
-#pragma unroll
-        for (int u = 0; u < NT; ++u) {
-            const int i8 = 8 * u + g;
-            const int bg = bl[i8 < nb ? i8 : 0];
-            jg[u] = __ldg(a.pbin + bg);
-            const V* Yg = Y + st.y_off + (bg - st.bin_base);
-#pragma unroll
-            for (int i = 0; i < NZ; ++i) {
-                const int r = t + 4 * i;
-                y[u][i] = r < R && i8 < nb ? __ldcg(Yg + (int64_t)r * B) : V{0.0f, 0.0f};
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < NT; ++u)
-#pragma unroll
-            for (int i = 0; i < NZ; ++i) {
-                const int r = t + 4 * i;
-                const V aj = delay_phasor<float>(a, jg[u], st.tau[r < R ? r : 0]);
-                zx[u][i] = y[u][i].x * aj.x + y[u][i].y * aj.y;
-                zy[u][i] = y[u][i].y * aj.x - y[u][i].x * aj.y;
-            }
-    }
+    const int R = a.pd.R, B = st.B;
+    int jg[NT];
+    V y[NT][NZ];
 #pragma unroll
     for (int u = 0; u < NT; ++u) {
-        // k-tile kt: rows 8 kt + t (slot 0) and 8 kt + t + 4 (slot 1) of [Re Z; Im Z]
+        const int i8 = 8 * u + g;
+        const int bg = bl[i8 < nb ? i8 : 0];
+        jg[u] = __ldg(a.pbin + bg);
+        const V* Yg = Y + st.y_off + (bg - st.bin_base);
 #pragma unroll
-        for (int kt = 0; kt < KT; ++kt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = 8 * kt + 4 * h;
-                const float v = k < RP ? zx[u][(k % RP) >> 2] : zy[u][(k % RP) >> 2];
-                tf32_split_bits(__float_as_uint(v), &bh[u][kt][h], &bo[u][kt][h]);
-            }
-    }
-    const uint4* fr = a.mltc + (size_t)st.mltc_off * 64 + lane;
-    const int MT = (L + 7) >> 3;
-    float best[NT][2];
-    int bq[NT][2];
-#pragma unroll
-    for (int u = 0; u < NT; ++u) {
-        best[u][0] = best[u][1] = -1.0f;
-        bq[u][0] = bq[u][1] = 0;
-    }
-    for (int mt = 0; mt < MT; ++mt) {
-        // the three partial products in separate accumulators: chains of KT MMAs
-        float c[NT][4], e[NT][4], f[NT][4];
-#pragma unroll
-        for (int u = 0; u < NT; ++u)
-#pragma unroll
-            for (int x = 0; x < 4; ++x) c[u][x] = e[u][x] = f[u][x] = 0.0f;
-#pragma unroll
-        for (int kt = 0; kt < KT; ++kt) {
-            const uint4 ah = __ldg(fr + (mt * KT + kt) * 64), al = __ldg(fr + (mt * KT + kt) * 64 + 32);
-#pragma unroll
-            for (int u = 0; u < NT; ++u) {
-                mma_tf32(e[u], al, bh[u][kt][0], bh[u][kt][1]);
-                mma_tf32(f[u], ah, bo[u][kt][0], bo[u][kt][1]);
-                mma_tf32(c[u], ah, bh[u][kt][0], bh[u][kt][1]);
-            }
-        }
-        // rows g / g + 8: Re / Im c of candidate 8 mt + g; columns 2 t, 2 t + 1: the bins
-        const int q = 8 * mt + g;
-        if (q < L) {
-#pragma unroll
-            for (int u = 0; u < NT; ++u)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float cx = c[u][h] + (e[u][h] + f[u][h]);
-                    const float cy = c[u][2 + h] + (e[u][2 + h] + f[u][2 + h]);
-                    const float sc = cx * cx + cy * cy;
-                    if (sc > best[u][h]) {
-                        best[u][h] = sc;
-                        bq[u][h] = q;
-                    }
-                }
+        for (int i = 0; i < NZ; ++i) {
+            const int r = ml_tc_delay<F16>(i, t);
+            y[u][i] = r < R && i8 < nb ? __ldcg(Yg + (int64_t)r * B) : V{0.0f, 0.0f};
         }
     }
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) {
+            const int r = ml_tc_delay<F16>(i, t);
+            const V aj = delay_phasor<float>(a, jg[u], st.tau[r < R ? r : 0]);
+            zx[u][i] = y[u][i].x * aj.x + y[u][i].y * aj.y;
+            zy[u][i] = y[u][i].y * aj.x - y[u][i].x * aj.y;
+        }
+}
+
+// One candidate tile's accumulators into the lane's running best: rows g / g + 8 are Re / Im
+// c of candidate q = 8 mt + g; columns 2 t, 2 t + 1 the bins
+template <int NT>
+__device__ __forceinline__ void ml_tc_score(const float (&c)[NT][4], const float (&e)[NT][4],
+                                            const float (&f)[NT][4], int q, int L,
+                                            float (&best)[NT][2], int (&bq)[NT][2])
+{
+    if (q >= L) return;
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float cx = c[u][h] + (e[u][h] + f[u][h]);
+            const float cy = c[u][2 + h] + (e[u][2 + h] + f[u][2 + h]);
+            const float sc = cx * cx + cy * cy;
+            if (sc > best[u][h]) {
+                best[u][h] = sc;
+                bq[u][h] = q;
+            }
+        }
+}
+
+// The argmax over the lanes sharing t, the fit of each bin on the four lanes that hold its
+// Z, and the warp's single-tons recorded with one list reservation
+template <int NZ, int NT, bool F16>
+__device__ __forceinline__ void ml_tc_finish(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                                             const float2* wtab, int32_t wtab_base, int round,
+                                             const int* bl, int nb, const Thr* thr, int d,
+                                             const StageDesc& st, const float (&zx)[NT][NZ],
+                                             const float (&zy)[NT][NZ], float (&best)[NT][2],
+                                             int (&bq)[NT][2])
+{
+    using V = float2;
+    const int lane = (int)(threadIdx.x & 31), g = lane >> 2, t = lane & 3;
+    const int R = a.pd.R, B = st.B, L = st.L;
 #pragma unroll
     for (int u = 0; u < NT; ++u)
 #pragma unroll
@@ -422,7 +410,7 @@ __device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, con
         V wr[NZ];
 #pragma unroll
         for (int i = 0; i < NZ; ++i) {
-            const int r = t + 4 * i;
+            const int r = ml_tc_delay<F16>(i, t);
             wr[i] = r < R ? W[r * L + qb] : V{0.0f, 0.0f};
             cx = fma(zx[u][i], wr[i].x, fma(zy[u][i], wr[i].y, cx));
             cy = fma(zy[u][i], wr[i].x, fma(-zx[u][i], wr[i].y, cy));
@@ -435,7 +423,7 @@ __device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, con
         float e2 = 0.0f;
 #pragma unroll
         for (int i = 0; i < NZ; ++i) {
-            if (t + 4 * i < R) {
+            if (ml_tc_delay<F16>(i, t) < R) {
                 const float ex = zx[u][i] - (float)B * (v.x * wr[i].x - v.y * wr[i].y);
                 const float ey = zy[u][i] - (float)B * (v.x * wr[i].y + v.y * wr[i].x);
                 e2 += ex * ex + ey * ey;
@@ -474,59 +462,77 @@ __device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, con
     }
 }
 
-// The same search with m16n8k16 FP16 MMAs (the plan's default; ml_tc_tf32 = 0 selects the
-// one above): a k-tile holds 8 delays, so the candidate matrix of R <= 8 delays is one
-// k-tile and each (candidate tile, n-tile) takes three MMAs where the TF32 search takes six,
-// with half the fragment loads.  Lane (g, t) holds Z of delays 8 kk + 2 t + j (j = 0, 1) of
-// bin 8 u + g: with the stage's FP16 table (ml_tc16_word) column k' of k-tile kk multiplies
-// Re Z_{8 kk + k'} (k' < 8) or Im Z_{8 kk + k' - 8}, and the m16n8k16 B fragment of lane
-// (g, t) is rows 2 t, 2 t + 1 (register 0) and 2 t + 8, 2 t + 9 (register 1) of column g.
-// FP16's range is kept by a power-of-two scale per bin (its largest Z component mapped
-// into [2^13, 2^14), as the tensor-core DFT axes do per tile): a bin's candidates share the
-// scale, so its argmax is that of the unscaled scores.  Both operands are split into high
-// and low FP16 parts and three partial products kept (FP32-level scores).  With one k-tile
-// the next candidate tile's fragments are loaded while the current one's MMAs run.  Argmax,
-// fit and records as in locate_ml_tc.
+// Split TF32: NZ = RP / 4 k-tiles of 8 rows (RP = ml_tc_rp(R)); k-tile kt's rows are
+// 8 kt + t (slot 0) and 8 kt + t + 4 (slot 1) of [Re Z; Im Z] (row k < RP: Re Z_k, else
+// Im Z_{k - RP}); the partial products in separate accumulators, chains of KT MMAs
+template <int NZ, int NT>
+__device__ __noinline__ void locate_ml_tc(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
+                                          const float2* Y, const float2* wtab, int32_t wtab_base,
+                                          int round, const int* bl, int nb, const Thr* thr)
+{
+    constexpr int RP = 4 * NZ, KT = NZ;
+    const int lane = (int)(threadIdx.x & 31);
+    const int d = stage_of(a.pd, bl[0]);
+    const StageDesc& st = a.pd.st[d];
+    float zx[NT][NZ], zy[NT][NZ];          // Z_{t + 4 i} of bin 8 u + g
+    uint32_t bh[NT][KT][2], bo[NT][KT][2];  // its B fragments: high and low parts
+    ml_tc_form_z<NZ, NT, false>(a, st, Y, bl, nb, zx, zy);
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 8 * kt + 4 * h;
+                const float v = k < RP ? zx[u][(k % RP) >> 2] : zy[u][(k % RP) >> 2];
+                tf32_split_bits(__float_as_uint(v), &bh[u][kt][h], &bo[u][kt][h]);
+            }
+    const uint4* fr = a.mltc + (size_t)st.mltc_off * 64 + lane;
+    const int MT = (st.L + 7) >> 3;
+    float best[NT][2];
+    int bq[NT][2];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        best[u][0] = best[u][1] = -1.0f;
+        bq[u][0] = bq[u][1] = 0;
+    }
+    for (int mt = 0; mt < MT; ++mt) {
+        float c[NT][4], e[NT][4], f[NT][4];
+#pragma unroll
+        for (int u = 0; u < NT; ++u)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) c[u][x] = e[u][x] = f[u][x] = 0.0f;
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt) {
+            const uint4 ah = __ldg(fr + (mt * KT + kt) * 64), al = __ldg(fr + (mt * KT + kt) * 64 + 32);
+#pragma unroll
+            for (int u = 0; u < NT; ++u) {
+                mma_tf32(e[u], al, bh[u][kt][0], bh[u][kt][1]);
+                mma_tf32(f[u], ah, bo[u][kt][0], bo[u][kt][1]);
+                mma_tf32(c[u], ah, bh[u][kt][0], bh[u][kt][1]);
+            }
+        }
+        ml_tc_score<NT>(c, e, f, 8 * mt + (lane >> 2), st.L, best, bq);
+    }
+    ml_tc_finish<NZ, NT, false>(a, ctr, w, wtab, wtab_base, round, bl, nb, thr, d, st, zx, zy, best, bq);
+}
+
+// Split FP16: KK k-tiles of 16 rows; lane (g, t)'s B fragment of k-tile kk is rows 2 t,
+// 2 t + 1 (register 0: Re Z_{8 kk + 2 t + j}) and 2 t + 8, 2 t + 9 (register 1: the Im
+// parts) of column g.  With one k-tile the next candidate tile's fragments are loaded while
+// the current one's MMAs run.
 template <int KK, int NT>
 __device__ __noinline__ void locate_ml_tc16(const DecodeArgs& a, int32_t* ctr, const DecodeWs& w,
                                             const float2* Y, const float2* wtab, int32_t wtab_base,
                                             int round, const int* bl, int nb, const Thr* thr)
 {
-    using V = float2;
-    constexpr int NZ = 2 * KK;  // Z per lane and bin: slot i is delay 8 (i / 2) + 2 t + i % 2
-    const PlanDesc& pd = a.pd;
-    const int lane = (int)(threadIdx.x & 31), g = lane >> 2, t = lane & 3;
-    const int d = stage_of(pd, bl[0]);
-    const StageDesc& st = pd.st[d];
-    const int R = pd.R, B = st.B, L = st.L;
-    auto delay_of = [&](int i) { return 8 * (i >> 1) + 2 * t + (i & 1); };
+    constexpr int NZ = 2 * KK;  // Z per lane and bin
+    const int lane = (int)(threadIdx.x & 31);
+    const int d = stage_of(a.pd, bl[0]);
+    const StageDesc& st = a.pd.st[d];
     float zx[NT][NZ], zy[NT][NZ];
     uint32_t bh[NT][KK][2], bo[NT][KK][2];  // B fragments: high and low parts
-    {
-        int jg[NT];
-        V y[NT][NZ];
-#pragma unroll
-        for (int u = 0; u < NT; ++u) {
-            const int i8 = 8 * u + g;
-            const int bg = bl[i8 < nb ? i8 : 0];
-            jg[u] = __ldg(a.pbin + bg);
-            const V* Yg = Y + st.y_off + (bg - st.bin_base);
-#pragma unroll
-            for (int i = 0; i < NZ; ++i) {
-                const int r = delay_of(i);
-                y[u][i] = r < R && i8 < nb ? __ldcg(Yg + (int64_t)r * B) : V{0.0f, 0.0f};
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < NT; ++u)
-#pragma unroll
-            for (int i = 0; i < NZ; ++i) {
-                const int r = delay_of(i);
-                const V aj = delay_phasor<float>(a, jg[u], st.tau[r < R ? r : 0]);
-                zx[u][i] = y[u][i].x * aj.x + y[u][i].y * aj.y;
-                zy[u][i] = y[u][i].y * aj.x - y[u][i].x * aj.y;
-            }
-    }
+    ml_tc_form_z<NZ, NT, true>(a, st, Y, bl, nb, zx, zy);
 #pragma unroll
     for (int u = 0; u < NT; ++u) {
         // the bin's scale: its largest component over the four lanes that hold its Z
@@ -543,7 +549,7 @@ __device__ __noinline__ void locate_ml_tc16(const DecodeArgs& a, int32_t* ctr, c
         }
     }
     const uint4* fr = a.mltc + (size_t)st.mltc_off * 64 + lane;
-    const int MT = (L + 7) >> 3;
+    const int MT = (st.L + 7) >> 3;
     float best[NT][2];
     int bq[NT][2];
 #pragma unroll
@@ -587,102 +593,9 @@ __device__ __noinline__ void locate_ml_tc16(const DecodeArgs& a, int32_t* ctr, c
                 mma_f16(f[u], ah[kk], bo[u][kk][0], bo[u][kk][1]);
                 mma_f16(c[u], ah[kk], bh[u][kk][0], bh[u][kk][1]);
             }
-        // rows g / g + 8: Re / Im c of candidate 8 mt + g; columns 2 t, 2 t + 1: the bins
-        const int q = 8 * mt + g;
-        if (q < L) {
-#pragma unroll
-            for (int u = 0; u < NT; ++u)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float cx = c[u][h] + (e[u][h] + f[u][h]);
-                    const float cy = c[u][2 + h] + (e[u][2 + h] + f[u][2 + h]);
-                    const float sc = cx * cx + cy * cy;
-                    if (sc > best[u][h]) {
-                        best[u][h] = sc;
-                        bq[u][h] = q;
-                    }
-                }
-        }
+        ml_tc_score<NT>(c, e, f, 8 * mt + (lane >> 2), st.L, best, bq);
     }
-#pragma unroll
-    for (int u = 0; u < NT; ++u)
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int o = 4; o < 32; o <<= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best[u][h], o);
-                const int oq = __shfl_xor_sync(0xffffffffu, bq[u][h], o);
-                if (ob > best[u][h] || (ob == best[u][h] && oq < bq[u][h])) {
-                    best[u][h] = ob;
-                    bq[u][h] = oq;
-                }
-            }
-    // the fit of bin 8 u + g on lanes (g, 0..3); its best candidate is held by lane g / 2
-    const V* W = wtab + (st.wtab_off - wtab_base);
-    const float scl = 1.0f / ((float)R * (float)B);
-    bool ok[NT];
-    V vv[NT];
-    int qq[NT];
-#pragma unroll
-    for (int u = 0; u < NT; ++u) {
-        const int i8 = 8 * u + g;
-        const int q0 = __shfl_sync(0xffffffffu, bq[u][0], g >> 1);
-        const int q1 = __shfl_sync(0xffffffffu, bq[u][1], g >> 1);
-        const int qb = (g & 1) ? q1 : q0;
-        float cx = 0.0f, cy = 0.0f;
-        V wr[NZ];
-#pragma unroll
-        for (int i = 0; i < NZ; ++i) {
-            const int r = delay_of(i);
-            wr[i] = r < R ? W[r * L + qb] : V{0.0f, 0.0f};
-            cx = fma(zx[u][i], wr[i].x, fma(zy[u][i], wr[i].y, cx));
-            cy = fma(zy[u][i], wr[i].x, fma(-zx[u][i], wr[i].y, cy));
-        }
-        cx += __shfl_xor_sync(0xffffffffu, cx, 1);
-        cy += __shfl_xor_sync(0xffffffffu, cy, 1);
-        cx += __shfl_xor_sync(0xffffffffu, cx, 2);
-        cy += __shfl_xor_sync(0xffffffffu, cy, 2);
-        const V v = {cx * scl, cy * scl};
-        float e2 = 0.0f;
-#pragma unroll
-        for (int i = 0; i < NZ; ++i) {
-            if (delay_of(i) < R) {
-                const float ex = zx[u][i] - (float)B * (v.x * wr[i].x - v.y * wr[i].y);
-                const float ey = zy[u][i] - (float)B * (v.x * wr[i].y + v.y * wr[i].x);
-                e2 += ex * ex + ey * ey;
-            }
-        }
-        e2 += __shfl_xor_sync(0xffffffffu, e2, 1);
-        e2 += __shfl_xor_sync(0xffffffffu, e2, 2);
-        ok[u] = t == 0 && i8 < nb && below(e2, thr[d].T1f, thr[d].T1);
-        vv[u] = v;
-        qq[u] = qb;
-    }
-    // the warp's single-tons: one list reservation for all of them
-    unsigned m[NT];
-    int n_rec = 0;
-#pragma unroll
-    for (int u = 0; u < NT; ++u) {
-        m[u] = __ballot_sync(0xffffffffu, ok[u]);
-        n_rec += __popc(m[u]);
-    }
-    if (n_rec == 0) return;
-    int base = 0;
-    if (lane == 0) {
-        base = atomicAdd(ctr + kCtrRoundBase + 3 * round + 2, n_rec);
-        atomicAdd(ctr + kCtrResolved, n_rec);
-    }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    const unsigned below_me = (1u << lane) - 1u;
-#pragma unroll
-    for (int u = 0; u < NT; ++u) {
-        if (ok[u]) {
-            const int b = bl[8 * u + g];
-            const int64_t f = (int64_t)__ldg(a.pbin + b) + (int64_t)qq[u] * B;
-            record_at<float>(w, round, b, f, vv[u], base + __popc(m[u] & below_me));
-        }
-        base += __popc(m[u]);
-    }
+    ml_tc_finish<NZ, NT, true>(a, ctr, w, wtab, wtab_base, round, bl, nb, thr, d, st, zx, zy, best, bq);
 }
 
 // Lanes per bin for the ML search of n bins with at most Lmax candidates by nt threads:
