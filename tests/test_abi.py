@@ -70,6 +70,34 @@ def test_opts_layout_and_defaults_without_gpu():
     assert (o.a_min, o.c0, o.c1) == (1.0, 4.0, 2.0)
     assert (o.decoder, o.oneshot_am, o.kay_m, o.noise_auto) == (_lib.DECODER_PEEL, 3, 2, 0)
     assert (o.host_gather, o.oneshot_method, o.dft_fma_only) == (0, 0, 0)
+    assert (o.peel_atomic, o.overlap_gather, o.classify_lanes, o.arg_mode, o.ml_tc_tf32) == (0, 0, 0, 0, 0)
+
+
+def test_schedule_option_ranges_checked_without_gpu():
+    """Out-of-range schedule and precision options fail with SFFT_EINVAL before any device
+    work: classify_lanes not a power of two up to 32, arg_mode outside 0..3, ml_tc_tf32
+    outside {0, 1}."""
+    import ctypes as ct
+    import numpy as np
+    from paper_2011_05749_gb300 import _lib
+    lib = _lib.load()
+    N, f = 124950, np.array([49, 50, 51], dtype=np.int64)
+    delays = np.ascontiguousarray(np.tile(np.arange(3, dtype=np.int64), (3, 1)))
+
+    def create(**kw):
+        o = _lib.Opts()
+        lib.sfft_opts_default(ct.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        h = ct.c_void_p()
+        return lib.sfft_plan_create(ct.byref(h), N, 10, 3, f.ctypes.data, delays.shape[1],
+                                    delays.ctypes.data, ct.byref(o))
+    inval = _lib.SFFT_EINVAL
+    assert create(classify_lanes=3) == inval
+    assert create(classify_lanes=64) == inval
+    assert create(arg_mode=4) == inval
+    assert create(ml_tc_tf32=2) == inval
+    assert create(ml_tc_tf32=-1) == inval
 
 
 def test_oneshot_plan_rules_checked_without_gpu():
