@@ -157,9 +157,12 @@ typedef struct {
                                  current one.  0 (default) = one CTA per tile: the scattered
                                  8-byte copies need L1 lines in flight, which the second tile
                                  region takes away (measured 2.4x slower on N = 127*128*129) */
-    int32_t classify_lanes;   /* lanes of a warp that search one bin's L candidates in the
-                                 first peeling round (ML locate): 1, 2, 4, 8, 16 or 32; 0
-                                 (default) = chosen per tile from its non-zero bins, L and R */
+    int32_t classify_lanes;   /* lanes of a warp that search one bin's L candidates on the FMA
+                                 pipes in the first peeling round (ML locate): 1, 2, 4, 8, 16
+                                 or 32.  0 (default) = the tensor-core search (ml_tc_tf32) in
+                                 FP32 plans with n_delays <= 16 when a classify tile's bins lie
+                                 in at most two stages; otherwise lanes chosen per tile from
+                                 its non-zero bins, L and R */
     int32_t arg_mode;         /* SFFT_LOCATE_ARG precision experiment (Sec. 3.2 subproblem 2):
                                  0 (default) = the angle of Y(1) conj(Y(0)) in FP64, snapped to
                                  the bin's candidate set {j + q B_d}; bit 0 = the angle and its
