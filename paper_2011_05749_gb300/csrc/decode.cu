@@ -1041,10 +1041,12 @@ __device__ __forceinline__ void signal_thresholds(const DecodeArgs& a, int sig, 
 }
 
 // Round 1: classify every bin.  One CTA per tile of kClassifyTile bins of one signal.
-// FP32: three CTAs per SM (85 registers).  With the tensor-core search, decode takes 0.462 ms
-// per 256 signals of N = 127 * 128 * 129 against 0.468 with four CTAs (64 registers) and
-// 0.490 with two; with the FMA search four had been best (0.67 against 0.77 with two), and
-// five or six spill too much.
+// FP32: three CTAs per SM (85 registers).  With the split-FP16 tensor-core search, decode
+// takes 0.411 ms per 256 signals of N = 127 * 128 * 129 against 0.427 with four CTAs (64
+// registers), and tiles of 2048 bins beat 1024 (0.482), 3072 (0.445) and 4096 (0.429); with
+// the split-TF32 search three CTAs also won (0.462 against 0.468 with four, 0.490 with two);
+// with the FMA search four had been best (0.67 against 0.77 with two), and five or six
+// spill too much.
 template <typename T>
 __global__ void __launch_bounds__(kClassifyThreads, sizeof(T) == 4 ? 3 : 2)
     classify_kernel(const __grid_constant__ DecodeArgs a)
