@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large single-signal measurement (N = 511*512*513)")
     ap.add_argument("--only", choices=["large", "sweep", "oneshot", "locate", "noise", "dsfft", "mix",
-                                       "serve", "dft"],
+                                       "serve", "dft", "ml"],
                     default=None,
                     help="run only that block (a short run for profiling) and print its JSON")
     ap.add_argument("--no-autotune", action="store_true",
@@ -551,11 +551,11 @@ def measure_noise_auto(sfft, batch=64, steps=20, warmup=3):
             "sigma2_estimate_over_true": {"min": min(ratio), "max": max(ratio)}}
 
 
-def measure_dft_paths(sfft, batch=256, steps=20, warmup=3):
-    """The R-FFAST workload's DFTs on the two paths the library has: the default (the 43- and
-    127-point direct DFTs on the tensor cores as 3-term split FP16 products) and a
-    dft_fma_only plan (every axis on the FMA pipes).  Same signals, same schedule; reports
-    signals/s, the bucketization's ms per step and L0/L2 against the truth for each."""
+def measure_plan_paths(sfft, variants, batch=256, steps=20, warmup=3):
+    """The R-FFAST workload through plans that differ in one option each (`variants`: pairs
+    of a name and the Plan keyword arguments), the same signals and schedule otherwise:
+    signals/s, the bucketization's and the decoder's ms per step and L0/L2 against the truth
+    for each."""
     import torch
     N, f, K = CFG["N"], CFG["f"], CFG["K"]
     delays = plan_delays(3)
@@ -564,9 +564,9 @@ def measure_dft_paths(sfft, batch=256, steps=20, warmup=3):
     dev = [torch.from_numpy(p.x.astype(np.complex64)).cuda() for p in probs]
     xs = torch.stack([dev[i % len(dev)] for i in range(batch)])
     out = {"workload": f"{WORKLOAD}, batches of {batch}"}
-    for name, fma in (("tensor_core_odd_axes", False), ("fma_only", True)):
+    for name, kw in variants:
         plan = sfft.Plan(N, K, f, delays, precision="fp32", locate="ml", noise_var=nv,
-                         max_batch=batch, dft_fma_only=fma)
+                         max_batch=batch, **kw)
         res = plan.empty_outputs("cuda", batch)
         for _ in range(warmup):
             plan.execute_many(xs, res)
@@ -586,9 +586,27 @@ def measure_dft_paths(sfft, batch=256, steps=20, warmup=3):
         plan.close()
         out[name] = {"signals_per_s": batch * 1e3 / ms, "ms_per_step": ms,
                      "bucketize_ms_per_step": prof["bucketize"]["ms"] / steps,
+                     "decode_ms_per_step": prof["decode"]["ms"] / steps,
                      "l0_vs_truth_total": int(sum(e[0] for e in errs)),
                      "rel_l2_vs_truth_max": max(e[1] for e in errs)}
     return out
+
+
+def measure_dft_paths(sfft, batch=256, steps=20, warmup=3):
+    """The R-FFAST workload's DFTs on the two paths the library has: the default (the 43- and
+    127-point direct DFTs on the tensor cores as 3-term split FP16 products) and a
+    dft_fma_only plan (every axis on the FMA pipes)."""
+    return measure_plan_paths(sfft, [("tensor_core_odd_axes", {}),
+                                     ("fma_only", {"dft_fma_only": True})], batch, steps, warmup)
+
+
+def measure_ml_paths(sfft, batch=256, steps=20, warmup=3):
+    """The first round's ML candidate search three ways on the same signals: on the tensor
+    cores as split-FP16 m16n8k16 MMAs (the default), as split-TF32 m16n8k8 MMAs
+    (ml_tc_tf32), and on the FMA pipes with two lanes per bin (classify_lanes = 2)."""
+    return measure_plan_paths(sfft, [("tensor_core_fp16", {}),
+                                     ("tensor_core_tf32", {"ml_tc_tf32": True}),
+                                     ("fma_lanes_2", {"classify_lanes": 2})], batch, steps, warmup)
 
 
 def measure_dsfft(sfft, batch=64, steps=5, warmup=1):
@@ -1022,6 +1040,11 @@ def run_gpu(args):
         dft_paths = measure_dft_paths(sfft)
     except Exception as exc:  # report, never fall back
         dft_paths = {"error": repr(exc)[:200]}
+    ml_paths = None
+    try:
+        ml_paths = measure_ml_paths(sfft)
+    except Exception as exc:  # report, never fall back
+        ml_paths = {"error": repr(exc)[:200]}
     dsfft = None
     try:
         dsfft = measure_dsfft(sfft)
@@ -1111,6 +1134,7 @@ def run_gpu(args):
         "locate_ml_vs_kay": locate_modes,
         "noise_auto": noise_auto,
         "dft_paths": dft_paths,
+        "ml_paths": ml_paths,
         "dsfft": dsfft,
         "batched_mix": mix,
         "serving_mix": serving_mix,
@@ -1149,6 +1173,8 @@ def run_only(args):
         out = measure_serving_mix(sfft, args.serve_rate, args.mix_seconds)
     elif args.only == "dft":
         out = measure_dft_paths(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
+    elif args.only == "ml":
+        out = measure_ml_paths(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     else:
         out = measure_oneshot(sfft, steps=max(1, args.steps), warmup=max(1, args.warmup))
     print(json.dumps(out, default=float), flush=True)
